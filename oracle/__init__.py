@@ -1,0 +1,151 @@
+"""CPU oracle for canonical hub labeling — TEST INFRASTRUCTURE ONLY.
+
+Plain restatement of the paper's definitions in C (``chl_oracle.c``), built with
+gcc on first use. Only ``tests/``, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the GPU library
+(``paper_1907_00140_gb300``) never does, and the two share no code.
+
+Functions follow the paper:
+  * ``build_labels``: the canonical labeling (Sec. 1), three independent ways:
+      ``"canonical"`` — the definition (h is a hub of v iff h is the
+      highest-ranked vertex of SP_{v,h}; Sec. 1, Lemma 1 in Sec. 3.1);
+      ``"plant"`` — Algorithm 3 (PLaNTDijkstra) with early termination;
+      ``"pll"`` — Algorithm 1 run sequentially in rank order (Sec. 3).
+  * ``query``: PPSD by linear merge of rank-sorted lists (Sec. 1, Sec. 5 QLSN).
+  * ``count_redundant``: labels that ``DQ_Clean`` (Algorithm 2) flags.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "chl_oracle.c")
+_LIB = os.path.join(_HERE, "libchloracle.so")
+_lock = threading.Lock()
+_lib = None
+
+METHODS = {"canonical": 0, "plant": 1, "pll": 2}
+
+
+def build(force: bool = False) -> str:
+    """Compile chl_oracle.c into liborc (in-tree) if missing or stale."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lpthread"],
+                       check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Labels(C.Structure):
+    _fields_ = [("offsets", C.POINTER(C.c_uint64)), ("hub", C.POINTER(C.c_uint32)),
+                ("dist", C.POINTER(C.c_uint32)), ("total", C.c_uint64), ("overflow", C.c_int)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+            lib.orc_build.argtypes = [u32, vp, vp, vp, vp, i32, vp, u64, i32, u64,
+                                      C.POINTER(_Labels), vp]
+            lib.orc_labels_free.argtypes = [C.POINTER(_Labels)]
+            lib.orc_query.argtypes = [u32, vp, vp, vp, vp, vp, u64, vp, i32]
+            lib.orc_count_redundant.argtypes = [u32, vp, vp, vp, vp]
+            lib.orc_count_redundant.restype = u64
+            _lib = lib
+    return _lib
+
+
+@dataclass
+class Labels:
+    """Per-vertex labels: L_v = (hub, dist)[offsets[v]:offsets[v+1]], hubs in
+    descending rank."""
+    offsets: np.ndarray  # uint64 [n+1]
+    hub: np.ndarray      # uint32 [T]
+    dist: np.ndarray     # uint32 [T]
+    overflow: bool = False
+
+    @property
+    def n(self) -> int:
+        return len(self.offsets) - 1
+
+    @property
+    def total(self) -> int:
+        return int(self.offsets[-1])
+
+    def of(self, v: int):
+        a, b = int(self.offsets[v]), int(self.offsets[v + 1])
+        return list(zip(self.hub[a:b].tolist(), self.dist[a:b].tolist()))
+
+
+def _u(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
+                 tie_seed: int = 0, with_stats: bool = False):
+    """Canonical labels of graph `g` (workloads.Graph or any object with n,
+    row_ptr, col, w) under ranking `rank`.
+
+    roots: None = every vertex in descending rank; else only labels with hub
+    in `roots` are produced (each tree is independent, Sec. 4.2).
+    tie_seed != 0 randomises the pop order of equal-distance vertices.
+    Returns Labels, or (Labels, stats[k,3] = settled, arcs scanned, labels per
+    root) when with_stats.
+    """
+    lib = _load()
+    n = int(g.n)
+    row, col, w = _u(g.row_ptr, np.uint64), _u(g.col, np.uint32), _u(g.w, np.uint32)
+    rank = _u(rank, np.uint32)
+    if roots is None:
+        rarr, nroots, rptr = None, n, None
+    else:
+        rarr = _u(roots, np.uint32)
+        nroots, rptr = len(rarr), rarr.ctypes.data
+    stats = np.zeros((nroots, 3), np.uint64) if with_stats else None
+    out = _Labels()
+    rc = lib.orc_build(n, row.ctypes.data, col.ctypes.data, w.ctypes.data, rank.ctypes.data,
+                       METHODS[method], rptr, nroots if rarr is not None else 0,
+                       int(threads), int(tie_seed), C.byref(out),
+                       stats.ctypes.data if stats is not None else None)
+    if rc != 0:
+        raise RuntimeError(f"orc_build failed: {rc}")
+    try:
+        T = int(out.total)
+        off = np.ctypeslib.as_array(out.offsets, shape=(n + 1,)).copy()
+        hub = np.ctypeslib.as_array(out.hub, shape=(T,)).copy() if T else np.zeros(0, np.uint32)
+        dist = np.ctypeslib.as_array(out.dist, shape=(T,)).copy() if T else np.zeros(0, np.uint32)
+        L = Labels(off, hub, dist, bool(out.overflow))
+    finally:
+        lib.orc_labels_free(C.byref(out))
+    return (L, stats) if with_stats else L
+
+
+def query(L: Labels, rank, pairs, threads: int = 1) -> np.ndarray:
+    """d(u,v) for each pair; UINT32_MAX where u and v share no hub."""
+    lib = _load()
+    pairs = _u(pairs, np.uint32).reshape(-1, 2)
+    out = np.empty(len(pairs), np.uint32)
+    rank = _u(rank, np.uint32)
+    rc = lib.orc_query(L.n, L.offsets.ctypes.data, L.hub.ctypes.data, L.dist.ctypes.data,
+                       rank.ctypes.data, pairs.ctypes.data, len(pairs), out.ctypes.data,
+                       int(threads))
+    if rc != 0:
+        raise ValueError(f"orc_query failed: {rc}")
+    return out
+
+
+def count_redundant(L: Labels, rank) -> int:
+    """Number of labels that DQ_Clean (Algorithm 2) would delete."""
+    lib = _load()
+    rank = _u(rank, np.uint32)
+    return int(lib.orc_count_redundant(L.n, L.offsets.ctypes.data, L.hub.ctypes.data,
+                                       L.dist.ctypes.data, rank.ctypes.data))
