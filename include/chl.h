@@ -1,0 +1,219 @@
+/*
+ * chl.h — C ABI of the GB300 canonical hub labeling library (libchl.so).
+ *
+ * Canonical hub labeling (CHL), Lakhotia et al., "Planting Trees for scalable
+ * and efficient Canonical Hub Labeling" (arXiv 1907.00140):
+ *
+ *   Given an undirected graph G(V,E,W) with positive integer edge weights and
+ *   a ranking function R (a total order on V, larger R = more important;
+ *   Sec. 1), the CHL holds a label (h, d(v,h)) in L_v exactly when h is the
+ *   highest-ranked vertex of SP_{v,h}, the set of vertices on all shortest
+ *   v-h paths (Sec. 1; Lemma 1 of Sec. 3.1). It is unique for a fixed R and
+ *   minimal (Sec. 1).
+ *
+ *   chl_build computes it the PLaNT way (Sec. 4.2, Algorithm 3): one
+ *   shortest-path tree per root h that carries, for every vertex, its
+ *   distance and the highest rank seen on any shortest path to it; a vertex
+ *   receives h as a hub when no higher-ranked vertex lies on any of its
+ *   shortest paths from h, and a tree stops once every pending vertex is
+ *   outranked (early termination, Sec. 4.2). Labels of each vertex are then
+ *   sorted by hub rank (Algorithm 2, sort step).
+ *
+ *   chl_query answers point-to-point shortest distance (PPSD) queries,
+ *   d(u,v) = min over common hubs h of d(u,h) + d(v,h) (Sec. 1), by merging
+ *   the two rank-sorted label lists (Sec. 5, querying with labels on a single
+ *   node).
+ *
+ * Conventions
+ *   - Every function returns a chl_status; no C++ exception crosses the ABI.
+ *     On failure chl_last_error() returns a message for the calling thread.
+ *   - Pointers marked "device or host" follow the chl_mem value passed with
+ *     them: CHL_MEM_DEVICE = CUDA device memory of the current device,
+ *     CHL_MEM_HOST = host memory (pinned is faster; pageable works). The
+ *     caller keeps ownership of every input and output buffer it passes.
+ *   - Work is ordered on the CUDA stream passed as `stream` (a cudaStream_t,
+ *     NULL = legacy default stream). A function returns once its results
+ *     are complete, unless stated otherwise.
+ *   - Distances are uint32; UINT32_MAX means "unreachable". Sums in queries
+ *     are taken in 64-bit and saturate at UINT32_MAX.
+ *   - The library runs every step on the GPU (sm_103a); it has no CPU
+ *     fallback.
+ */
+#ifndef CHL_H
+#define CHL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CHL_OK = 0,
+    CHL_EINVAL = 1,     /* malformed argument or input graph / rank */
+    CHL_ENOMEM = 2,     /* device or host allocation failed */
+    CHL_ECUDA = 3,      /* a CUDA call failed (message holds the CUDA error) */
+    CHL_ETIMEOUT = 4,   /* a bounded device wait ran out of iterations */
+    CHL_EOVERFLOW = 5   /* a distance reached UINT32_MAX, or a capacity was exceeded */
+} chl_status;
+
+typedef enum {
+    CHL_MEM_DEVICE = 0,
+    CHL_MEM_HOST = 1
+} chl_mem;
+
+/*
+ * Undirected weighted graph as a symmetric CSR (the paper's G(V,E,W), Sec. 2:
+ * positive edge weights; undirected per Table 1).
+ *   n          number of vertices, 1 <= n < 2^31
+ *   num_arcs   row_ptr[n] = 2|E| (every edge stored in both directions)
+ *   row_ptr    [n+1] uint64, row_ptr[0] = 0, non-decreasing
+ *   col        [num_arcs] uint32 < n; each row strictly increasing (no
+ *              duplicate arcs); self-loops are not allowed
+ *   w          [num_arcs] uint32 >= 1; the arc v->u and the arc u->v carry
+ *              the same weight
+ *   mem        where row_ptr, col and w live
+ * chl_build rejects (CHL_EINVAL) any violation, including an arc without its
+ * reverse.
+ */
+typedef struct {
+    uint32_t n;
+    uint64_t num_arcs;
+    const uint64_t *row_ptr;
+    const uint32_t *col;
+    const uint32_t *w;
+    chl_mem mem;
+} chl_csr;
+
+/* Labels produced by chl_build: opaque, library-owned, resident in device
+   memory until chl_labels_free. */
+typedef struct chl_labels chl_labels;
+
+/*
+ * Build options. Zero-initialise and set what you need; 0 means "choose
+ * automatically" (the autotuner).
+ *   root_begin, root_end   build only trees whose root has rank position p in
+ *                          [root_begin, root_end), p = n-1-R(root) (p = 0 is
+ *                          the most important vertex). root_end = 0 means n.
+ *                          Trees are independent (Sec. 4.2), so disjoint
+ *                          ranges partition the labels by hub.
+ *   threads_per_tree       CUDA threads cooperating on one tree (32..512,
+ *                          multiple of 32)
+ *   bucket_delta           distance width of one bucket of the tree search
+ *                          (>= 1)
+ *   window_buckets         buckets held in the near window (2..64)
+ *   slots                  trees in flight at once
+ *   mode                   0 = persistent batched launch (all roots claimed
+ *                          dynamically in rank order by one launch);
+ *                          1 = plain: one launch per root (one CTA of
+ *                          threads_per_tree threads, default 512, builds it)
+ *   label_capacity         initial size of the label buffer in labels; when
+ *                          a tree does not fit, the buffer doubles and the
+ *                          roots that did not fit are built again
+ */
+typedef struct {
+    uint32_t root_begin;
+    uint32_t root_end;
+    int32_t threads_per_tree;
+    int32_t bucket_delta;
+    int32_t window_buckets;
+    int32_t slots;
+    int32_t mode;
+    int32_t reserved;
+    uint64_t label_capacity;
+} chl_build_opts;
+
+/*
+ * Counters of a finished build (for throughput and exploration reports).
+ *   trees          trees built (roots in the requested range)
+ *   labels         total labels (hub, dist) emitted
+ *   expanded       vertex expansions, re-expansions included
+ *   arcs           arcs relaxed
+ *   trivial        trees that ended at the root (every neighbour outranks it)
+ *   build_ms       device time of the whole chl_build (CUDA events)
+ *   tree_ms        device time of the tree kernel alone
+ *   sort_ms        device time of label assembly (count, scan, scatter, sort)
+ *   launches       kernels launched by the build
+ */
+typedef struct {
+    uint64_t trees;
+    uint64_t labels;
+    uint64_t expanded;
+    uint64_t arcs;
+    uint64_t trivial;
+    double build_ms;
+    double tree_ms;
+    double sort_ms;
+    uint64_t launches;
+} chl_build_stats;
+
+/*
+ * chl_build — canonical hub labels of g under ranking `rank` (PLaNT,
+ * Sec. 4.2, Algorithm 3; early termination as in Sec. 4.2; label sort as in
+ * Algorithm 2).
+ *   g        input graph (see chl_csr); g->mem says where its arrays are
+ *   rank     [n] uint32 R(v), a permutation of [0,n); same memory kind as g
+ *   opts     NULL = defaults
+ *   stream   cudaStream_t to order the work on
+ *   out      receives the new labels object (owned by the caller, free with
+ *            chl_labels_free); *out is NULL on failure
+ * Errors: CHL_EINVAL (malformed graph, rank not a permutation, bad options),
+ * CHL_ENOMEM, CHL_ECUDA, CHL_EOVERFLOW (a shortest distance reaches
+ * UINT32_MAX, or one vertex holds more labels than the sorter supports).
+ */
+chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opts *opts,
+                     void *stream, chl_labels **out);
+
+/* n, total number of labels, and device bytes held by the object. */
+chl_status chl_labels_info(const chl_labels *L, uint32_t *n, uint64_t *total, uint64_t *bytes);
+
+/* Counters of the build that produced L (see chl_build_stats). */
+chl_status chl_labels_stats(const chl_labels *L, chl_build_stats *stats);
+
+/*
+ * Device views, valid until chl_labels_free(L):
+ *   offsets  [n+1] uint64; the labels of vertex v are entries
+ *            [offsets[v], offsets[v+1])
+ *   hub      [total] uint32 hub vertex id; within each vertex sorted by
+ *            R(hub) descending (most important first); the last entry of
+ *            L_v is v itself with distance 0
+ *   dist     [total] uint32 d(v, hub)
+ * Any output pointer may be NULL.
+ */
+chl_status chl_labels_view(const chl_labels *L, const uint64_t **offsets, const uint32_t **hub,
+                           const uint32_t **dist);
+
+/*
+ * Copy the labels into caller buffers (offsets [n+1], hub [total],
+ * dist [total]; any may be NULL) in memory of kind dst_mem, ordered on
+ * stream; returns after the copy completed.
+ */
+chl_status chl_labels_copy(const chl_labels *L, uint64_t *offsets, uint32_t *hub, uint32_t *dist,
+                           chl_mem dst_mem, void *stream);
+
+/*
+ * chl_query — PPSD queries (Sec. 1 cover property; Sec. 5 QLSN merge).
+ *   pairs    [q][2] uint32 vertex ids (u, v), device or host per `mem`
+ *   q        number of pairs (0 is allowed and does nothing)
+ *   out      [q] uint32, out[i] = d(u_i, v_i), UINT32_MAX if u_i and v_i are
+ *            disconnected; same memory kind as pairs
+ * Errors: CHL_EINVAL (NULL pointers, a vertex id >= n), CHL_ENOMEM,
+ * CHL_ECUDA.
+ */
+chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t *out,
+                     chl_mem mem, void *stream);
+
+/* Release the labels object (NULL is allowed). Synchronises its stream. */
+void chl_labels_free(chl_labels *L);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+const char *chl_last_error(void);
+
+/* Library version string. */
+const char *chl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CHL_H */

@@ -1,0 +1,95 @@
+"""Algorithmic work units of each benchmark workload, computed by the oracle.
+
+TEST/BENCH INFRASTRUCTURE: calls only ``oracle`` and ``workloads``.
+
+For the PLaNT build (Algorithm 3 with early termination, Sec. 4.2) the units
+are, summed over all roots h:
+  S = vertices settled (popped) by the tree of h,
+  A = arcs scanned by those vertices,
+  T = labels emitted (= total size of the canonical labeling).
+T is exact: sequential Algorithm 1 (pruned Dijkstra with rank queries, Sec. 3)
+builds the same labeling quickly. S and A are exact for small workloads and
+otherwise a stratified estimate: every one of the 64 most important roots,
+then rank-position strata of doubling width with `per_stratum` seeded roots
+each (mean x stratum size), with a standard error.
+
+Usage:  python oracle/work_units.py [workload ...]   (writes oracle/work_units.json)
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+_ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if _ROOT not in sys.path:
+    sys.path.insert(0, _ROOT)
+
+import oracle as O  # noqa: E402
+import workloads as W  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "work_units.json")
+
+
+def strata(n):
+    edges = [0, 64]
+    while edges[-1] < n:
+        edges.append(min(n, edges[-1] * 2))
+    return list(zip(edges[:-1], edges[1:]))
+
+
+def units(name, per_stratum=96, threads=None, exact_below=5000, seed=1):
+    threads = threads or os.cpu_count()
+    g, rank = W.load(name)
+    n = g.n
+    order = np.empty(n, np.uint32)
+    order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
+    t0 = time.time()
+    T = O.build_labels(g, rank, "pll").total
+    t_pll = time.time() - t0
+    rng = np.random.default_rng(seed)
+    S = A = 0.0
+    varS = varA = 0.0
+    sampled = 0
+    for lo, hi in strata(n):
+        size = hi - lo
+        if n <= exact_below or lo == 0 or size <= per_stratum:
+            pos = np.arange(lo, hi)
+        else:
+            pos = np.sort(rng.choice(np.arange(lo, hi), per_stratum, replace=False))
+        _, st = O.build_labels(g, rank, "plant", roots=order[pos], threads=threads, with_stats=True)
+        s, a = st[:, 0].astype(np.float64), st[:, 1].astype(np.float64)
+        k = len(pos)
+        sampled += k
+        S += s.mean() * size
+        A += a.mean() * size
+        if k < size and k > 1:
+            f = (1 - k / size) * size * size / k
+            varS += f * s.var(ddof=1)
+            varA += f * a.var(ddof=1)
+    return {
+        "n": int(n), "arcs": int(g.num_arcs), "T": int(T),
+        "S": float(S), "A": float(A), "S_stderr": float(varS ** 0.5), "A_stderr": float(varA ** 0.5),
+        "roots_sampled": int(sampled), "exact": bool(sampled == n),
+        "method": "T: sequential Algorithm 1; S, A: Algorithm 3 with early termination, "
+                  "stratified by rank position (all of the top 64, then doubling strata)",
+        "pll_seconds": round(t_pll, 1),
+    }
+
+
+def main(names):
+    data = {}
+    if os.path.exists(OUT):
+        data = json.load(open(OUT))
+    for name in names:
+        t = time.time()
+        data[name] = units(name)
+        data[name]["seconds"] = round(time.time() - t, 1)
+        print(name, json.dumps(data[name]), flush=True)
+        with open(OUT, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or ["ba2k", "rmat18", "grid512"])

@@ -1,0 +1,304 @@
+"""Python binding of libchl.so, the GB300 canonical hub labeling library.
+
+Thin marshalling over the C ABI declared in ``include/chl.h``: every function
+of that header is exposed under the same name with the same arguments
+(pointers as ints, ``void* stream`` as an int). Arrays may be numpy arrays
+(host memory, ``CHL_MEM_HOST``) or torch CUDA tensors (device memory,
+``CHL_MEM_DEVICE``); the helpers below only pass pointers and sizes. All
+computation happens inside libchl.so on the GPU; there is no CPU fallback, and
+calling into this module without a built library raises.
+
+Method: PLaNT (Lakhotia et al., arXiv 1907.00140, Sec. 4.2, Algorithm 3)
+builds one shortest-path tree per root in rank order and labels a vertex with
+the root exactly when no higher-ranked vertex lies on any of its shortest
+paths from the root; queries merge the two rank-sorted label lists (Sec. 5).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+__all__ = [
+    "build", "lib", "CHL_OK", "CHL_EINVAL", "CHL_ENOMEM", "CHL_ECUDA", "CHL_ETIMEOUT",
+    "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "ChlError", "chl_csr", "chl_build_opts",
+    "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
+    "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
+    "Labels", "build_labels", "query",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
+_SOURCES = ["chl_api.cu", "chl_graph.cu", "chl_tree.cu", "chl_labels.cu", "chl_query.cu"]
+LIB_PATH = os.path.join(_HERE, "libchl.so")
+ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+CHL_OK, CHL_EINVAL, CHL_ENOMEM, CHL_ECUDA, CHL_ETIMEOUT, CHL_EOVERFLOW = range(6)
+CHL_MEM_DEVICE, CHL_MEM_HOST = 0, 1
+_NAMES = {0: "CHL_OK", 1: "CHL_EINVAL", 2: "CHL_ENOMEM", 3: "CHL_ECUDA", 4: "CHL_ETIMEOUT",
+          5: "CHL_EOVERFLOW"}
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def _sources():
+    return [os.path.join(_CSRC, s) for s in _SOURCES]
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB_PATH):
+        return True
+    t = os.path.getmtime(LIB_PATH)
+    deps = _sources() + [os.path.join(_CSRC, "chl_common.cuh"), os.path.join(_INCLUDE, "chl.h")]
+    return any(os.path.getmtime(d) > t for d in deps)
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile libchl.so for sm_103a in-tree (nvcc, one translation unit per
+    source, compiled in parallel) if it is missing or older than its sources."""
+    if not force and not _stale():
+        return LIB_PATH
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH_FLAGS, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+           "-shared", "-t", "0", "-o", tmp, *_sources()]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
+    if verbose:
+        print(r.stdout + r.stderr)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+# ------------------------------------------------------------------ ABI structs
+class chl_csr(C.Structure):
+    _fields_ = [("n", C.c_uint32), ("num_arcs", C.c_uint64), ("row_ptr", C.c_void_p),
+                ("col", C.c_void_p), ("w", C.c_void_p), ("mem", C.c_int)]
+
+
+class chl_build_opts(C.Structure):
+    _fields_ = [("root_begin", C.c_uint32), ("root_end", C.c_uint32),
+                ("threads_per_tree", C.c_int32), ("bucket_delta", C.c_int32),
+                ("window_buckets", C.c_int32), ("slots", C.c_int32), ("mode", C.c_int32),
+                ("reserved", C.c_int32), ("label_capacity", C.c_uint64)]
+
+
+class chl_build_stats(C.Structure):
+    _fields_ = [("trees", C.c_uint64), ("labels", C.c_uint64), ("expanded", C.c_uint64),
+                ("arcs", C.c_uint64), ("trivial", C.c_uint64), ("build_ms", C.c_double),
+                ("tree_ms", C.c_double), ("sort_ms", C.c_double), ("launches", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """The loaded libchl.so (raises if it is not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is not built; call paper_1907_00140_gb300.build()")
+            L = C.CDLL(LIB_PATH)
+            vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+            L.chl_build.argtypes = [C.POINTER(chl_csr), vp, C.POINTER(chl_build_opts), vp,
+                                    C.POINTER(vp)]
+            L.chl_build.restype = i32
+            L.chl_labels_info.argtypes = [vp, C.POINTER(u32), C.POINTER(u64), C.POINTER(u64)]
+            L.chl_labels_info.restype = i32
+            L.chl_labels_stats.argtypes = [vp, C.POINTER(chl_build_stats)]
+            L.chl_labels_stats.restype = i32
+            L.chl_labels_view.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp)]
+            L.chl_labels_view.restype = i32
+            L.chl_labels_copy.argtypes = [vp, vp, vp, vp, i32, vp]
+            L.chl_labels_copy.restype = i32
+            L.chl_query.argtypes = [vp, vp, u64, vp, i32, vp]
+            L.chl_query.restype = i32
+            L.chl_labels_free.argtypes = [vp]
+            L.chl_labels_free.restype = None
+            L.chl_last_error.argtypes = []
+            L.chl_last_error.restype = C.c_char_p
+            L.chl_version.argtypes = []
+            L.chl_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+class ChlError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(st: int):
+    if st != CHL_OK:
+        raise ChlError(st, lib().chl_last_error().decode())
+
+
+# ------------------------------------------------------------------ raw ABI (same names)
+def chl_build(g: chl_csr, rank_ptr: int, opts: chl_build_opts | None, stream: int) -> int:
+    out = C.c_void_p()
+    _check(lib().chl_build(C.byref(g), rank_ptr, C.byref(opts) if opts is not None else None,
+                           stream, C.byref(out)))
+    return out.value
+
+
+def chl_labels_info(handle: int):
+    n, t, b = C.c_uint32(), C.c_uint64(), C.c_uint64()
+    _check(lib().chl_labels_info(handle, C.byref(n), C.byref(t), C.byref(b)))
+    return n.value, t.value, b.value
+
+
+def chl_labels_stats(handle: int) -> chl_build_stats:
+    s = chl_build_stats()
+    _check(lib().chl_labels_stats(handle, C.byref(s)))
+    return s
+
+
+def chl_labels_view(handle: int):
+    o, h, d = C.c_void_p(), C.c_void_p(), C.c_void_p()
+    _check(lib().chl_labels_view(handle, C.byref(o), C.byref(h), C.byref(d)))
+    return o.value, h.value, d.value
+
+
+def chl_labels_copy(handle: int, offsets: int, hub: int, dist: int, mem: int, stream: int):
+    _check(lib().chl_labels_copy(handle, offsets, hub, dist, mem, stream))
+
+
+def chl_query(handle: int, pairs: int, q: int, out: int, mem: int, stream: int):
+    _check(lib().chl_query(handle, pairs, q, out, mem, stream))
+
+
+def chl_labels_free(handle: int):
+    lib().chl_labels_free(handle)
+
+
+def chl_last_error() -> str:
+    return lib().chl_last_error().decode()
+
+
+def chl_version() -> str:
+    return lib().chl_version().decode()
+
+
+# ------------------------------------------------------------------ helpers
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _ptr_mem(x, dtype):
+    """(pointer, memory kind, keep-alive) for a numpy array or a torch CUDA tensor."""
+    if _is_torch(x):
+        import torch
+        want = {np.uint32: torch.int32, np.uint64: torch.int64}[dtype]
+        if not x.is_cuda:
+            x = x.contiguous().numpy().view(dtype)
+            return x.ctypes.data, CHL_MEM_HOST, x
+        if x.dtype not in (want, {np.uint32: torch.uint32, np.uint64: torch.uint64}[dtype]):
+            raise TypeError(f"tensor dtype {x.dtype} does not match {dtype.__name__}")
+        x = x.contiguous()
+        return x.data_ptr(), CHL_MEM_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, CHL_MEM_HOST, a
+
+
+def _current_stream() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+class Labels:
+    """Owner of a chl_labels handle (device-resident labels)."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        self.free()
+
+    def free(self):
+        if getattr(self, "handle", None):
+            chl_labels_free(self.handle)
+            self.handle = None
+
+    @property
+    def n(self) -> int:
+        return chl_labels_info(self.handle)[0]
+
+    @property
+    def total(self) -> int:
+        return chl_labels_info(self.handle)[1]
+
+    @property
+    def nbytes(self) -> int:
+        return chl_labels_info(self.handle)[2]
+
+    def stats(self) -> dict:
+        return chl_labels_stats(self.handle).as_dict()
+
+    def to_numpy(self, stream: int | None = None):
+        """(offsets uint64[n+1], hub uint32[T], dist uint32[T]) copied to host."""
+        n, T, _ = chl_labels_info(self.handle)
+        off = np.empty(n + 1, np.uint64)
+        hub = np.empty(T, np.uint32)
+        dist = np.empty(T, np.uint32)
+        chl_labels_copy(self.handle, off.ctypes.data, hub.ctypes.data if T else None,
+                        dist.ctypes.data if T else None, CHL_MEM_HOST,
+                        _current_stream() if stream is None else stream)
+        return off, hub, dist
+
+    def query(self, pairs, out=None, stream: int | None = None):
+        """Distances for pairs [q,2] (numpy -> numpy, CUDA tensor -> CUDA tensor)."""
+        p, mem, keep = _ptr_mem(pairs, np.uint32)
+        q = (keep.numel() if _is_torch(keep) else keep.size) // 2
+        if out is None:
+            if mem == CHL_MEM_DEVICE:
+                import torch
+                out = torch.empty(q, dtype=torch.int32, device=keep.device)
+            else:
+                out = np.empty(q, np.uint32)
+        op = out.data_ptr() if _is_torch(out) else out.ctypes.data
+        chl_query(self.handle, p, q, op, mem, _current_stream() if stream is None else stream)
+        return out
+
+
+def build_labels(g, rank, stream: int | None = None, **opts) -> Labels:
+    """Canonical hub labels of graph g (object with n, row_ptr, col, w; numpy
+    arrays or CUDA tensors) under rank R (permutation, larger = more important).
+    opts: fields of chl_build_opts (root_begin, root_end, threads_per_tree,
+    bucket_delta, window_buckets, slots, mode)."""
+    rp, mem, k1 = _ptr_mem(g.row_ptr, np.uint64)
+    cp, mem2, k2 = _ptr_mem(g.col, np.uint32)
+    wp, mem3, k3 = _ptr_mem(g.w, np.uint32)
+    rkp, mem4, k4 = _ptr_mem(rank, np.uint32)
+    if len({mem, mem2, mem3, mem4}) != 1:
+        raise ValueError("graph arrays and rank must all be host arrays or all CUDA tensors")
+    narcs = (k2.numel() if _is_torch(k2) else k2.size)
+    csr = chl_csr(int(g.n), int(narcs), rp, cp if narcs else None, wp if narcs else None, mem)
+    o = chl_build_opts()
+    for k, v in opts.items():
+        setattr(o, k, int(v))
+    h = chl_build(csr, rkp, o, _current_stream() if stream is None else stream)
+    return Labels(h)
+
+
+def query(labels: Labels, pairs, **kw):
+    return labels.query(pairs, **kw)

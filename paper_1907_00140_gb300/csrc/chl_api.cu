@@ -1,0 +1,479 @@
+// C ABI of libchl.so (declared in include/chl.h): argument checks, device
+// memory, the build driver (graph preparation, persistent tree launch with
+// retry on a full label buffer, label assembly) and the query entry point.
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "chl_common.cuh"
+
+struct chl_labels {
+    uint32_t n = 0;
+    uint64_t total = 0;
+    uint64_t *offsets = nullptr;
+    uint32_t *hub = nullptr;
+    uint32_t *hubpos = nullptr;
+    uint32_t *dist = nullptr;
+    uint64_t bytes = 0;
+    chl_build_stats stats{};
+    int device = 0;
+};
+
+namespace chl {
+
+static thread_local char g_err[512] = "";
+
+chl_status set_error(chl_status st, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
+                               int *launches);
+
+namespace {
+
+// device control block of one tree launch
+struct Control {
+    unsigned int next_root;
+    unsigned int failed_count;
+    int flags[2];
+    unsigned long long out_count;
+    unsigned long long stats[4];
+};
+
+struct Params {
+    int tpt;
+    uint32_t delta;
+    uint32_t nwin;
+    int slots;
+};
+
+// Defaults of the search parameters from graph statistics. Bucket width:
+// about a sixteenth of the mean weight keeps buckets narrow enough that early
+// termination overshoots little (the test runs at bucket granularity) while a
+// bucket still holds many vertices of a large tree.
+Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_t free_bytes) {
+    Params p;
+    p.tpt = o.threads_per_tree ? o.threads_per_tree : 128;
+    uint32_t d = o.bucket_delta > 0 ? uint32_t(o.bucket_delta) : uint32_t(g.w_mean / 16.0);
+    p.delta = d < 1 ? 1 : d;
+    p.nwin = o.window_buckets > 0 ? uint32_t(o.window_buckets) : 16;
+    int per_sm = plant_max_slots_per_sm(p.tpt);
+    if (per_sm < 1) per_sm = 1;
+    long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
+    // slot state: key 8 + three tags 12 + five lists 20 bytes per vertex
+    const double per_slot = 40.0 * double(g.n) + 64.0;
+    const double budget = 0.35 * double(free_bytes);
+    long long cap = (long long)(budget / per_slot);
+    if (o.slots <= 0 && slots > cap) slots = cap;
+    if (slots < 1) slots = 1;
+    p.slots = int(slots);
+    return p;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+}  // namespace
+}  // namespace chl
+
+using namespace chl;
+
+#define CUDA_TRY(x)                                                              \
+    do {                                                                         \
+        cudaError_t e__ = (x);                                                   \
+        if (e__ != cudaSuccess) {                                                \
+            st = (e__ == cudaErrorMemoryAllocation)                              \
+                     ? set_error(CHL_ENOMEM, "%s: %s", #x, cudaGetErrorString(e__)) \
+                     : set_error(CHL_ECUDA, "%s: %s", #x, cudaGetErrorString(e__)); \
+            goto done;                                                           \
+        }                                                                        \
+    } while (0)
+
+extern "C" const char *chl_last_error(void) { return g_err; }
+
+extern "C" const char *chl_version(void) { return "chl-gb300 0.1 (sm_103a)"; }
+
+extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opts *opts,
+                                void *stream, chl_labels **out) {
+    g_err[0] = 0;
+    if (!out) return set_error(CHL_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!g || !rank) return set_error(CHL_EINVAL, "graph or rank is NULL");
+    if (g->n == 0) return set_error(CHL_EINVAL, "graph has no vertices");
+    if (g->n >= 0x7FFFFFFFu) return set_error(CHL_EINVAL, "n must be < 2^31");
+    if (!g->row_ptr || (g->num_arcs && (!g->col || !g->w)))
+        return set_error(CHL_EINVAL, "graph arrays are NULL");
+    if (g->mem != CHL_MEM_DEVICE && g->mem != CHL_MEM_HOST)
+        return set_error(CHL_EINVAL, "unknown memory kind");
+    chl_build_opts o{};
+    if (opts) o = *opts;
+    const uint32_t n = g->n;
+    const uint32_t rb = o.root_begin, re = o.root_end ? o.root_end : n;
+    if (rb > re || re > n) return set_error(CHL_EINVAL, "root range [%u,%u) outside [0,%u)", rb, re, n);
+    if (o.threads_per_tree && (o.threads_per_tree % 32 || o.threads_per_tree < 32 || o.threads_per_tree > 512))
+        return set_error(CHL_EINVAL, "threads_per_tree must be 32..512 and a multiple of 32");
+    if (o.window_buckets && (o.window_buckets < 2 || o.window_buckets > 64))
+        return set_error(CHL_EINVAL, "window_buckets must be in [2,64]");
+    if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
+    if (o.bucket_delta < 0 || o.slots < 0) return set_error(CHL_EINVAL, "negative option");
+
+    cudaStream_t s = (cudaStream_t)stream;
+    chl_status st = CHL_OK;
+    int launches = 0;
+    int dev = 0, sms = 0;
+    size_t free_b = 0, total_b = 0;
+    const uint64_t m2 = g->num_arcs;
+    const uint64_t *d_row = g->row_ptr;
+    const uint32_t *d_col = g->col, *d_w = g->w, *d_rank = rank;
+    DevBuf b_row, b_col, b_w, b_rank, b_key, b_tags, b_lists, b_ctr, b_ctl, b_ov, b_oh, b_od,
+        b_fail, b_roots;
+    RankGraph rg;
+    Params P{};
+    Control hc{};
+    Control *ctl = nullptr;
+    LabelCSR csr;
+    uint64_t cap = 0;
+    uint64_t T = 0;
+    int too_long = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    float ms_total = 0, ms_tree = 0, ms_sort = 0;
+    chl_labels *L = nullptr;
+    unsigned long long agg[4] = {0, 0, 0, 0};
+    std::vector<uint32_t> pending;  // roots still to build (after a full buffer)
+    uint32_t claimed_upto = 0;
+    bool first = true;
+
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventRecord(ev[0], s));
+    b_row.s = b_col.s = b_w.s = b_rank.s = b_key.s = b_tags.s = b_lists.s = b_ctr.s = b_ctl.s = s;
+    b_ov.s = b_oh.s = b_od.s = b_fail.s = b_roots.s = s;
+
+    // inputs on the device
+    if (g->mem == CHL_MEM_HOST) {
+        CUDA_TRY(cudaMallocAsync(&b_row.p, (size_t(n) + 1) * 8, s));
+        CUDA_TRY(cudaMallocAsync(&b_col.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(cudaMallocAsync(&b_w.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(cudaMallocAsync(&b_rank.p, size_t(n) * 4, s));
+        CUDA_TRY(cudaMemcpyAsync(b_row.p, g->row_ptr, (size_t(n) + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (m2) {
+            CUDA_TRY(cudaMemcpyAsync(b_col.p, g->col, m2 * 4, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(b_w.p, g->w, m2 * 4, cudaMemcpyHostToDevice, s));
+        }
+        CUDA_TRY(cudaMemcpyAsync(b_rank.p, rank, size_t(n) * 4, cudaMemcpyHostToDevice, s));
+        d_row = (const uint64_t *)b_row.p;
+        d_col = (const uint32_t *)b_col.p;
+        d_w = (const uint32_t *)b_w.p;
+        d_rank = (const uint32_t *)b_rank.p;
+    }
+    {
+        uint64_t last = 0;
+        CUDA_TRY(cudaMemcpyAsync(&last, d_row + n, 8, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (last != m2) {
+            st = set_error(CHL_EINVAL, "row_ptr[n] = %llu differs from num_arcs = %llu",
+                           (unsigned long long)last, (unsigned long long)m2);
+            goto done;
+        }
+    }
+    st = prepare_graph(n, m2, d_row, d_col, d_w, d_rank, rg, s, &launches);
+    if (st != CHL_OK) goto done;
+
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    P = choose_params(rg, o, sms, free_b);
+    if (o.mode == 1) { P.slots = 1; P.tpt = o.threads_per_tree ? o.threads_per_tree : 512; }
+
+    // slot state
+    CUDA_TRY(cudaMallocAsync(&b_key.p, size_t(P.slots) * n * 8, s));
+    CUDA_TRY(cudaMemsetAsync(b_key.p, 0xFF, size_t(P.slots) * n * 8, s));
+    CUDA_TRY(cudaMallocAsync(&b_tags.p, size_t(P.slots) * n * 12, s));
+    CUDA_TRY(cudaMemsetAsync(b_tags.p, 0, size_t(P.slots) * n * 12, s));
+    CUDA_TRY(cudaMallocAsync(&b_lists.p, size_t(P.slots) * n * 20, s));
+    CUDA_TRY(cudaMallocAsync(&b_ctr.p, size_t(P.slots) * 16, s));
+    CUDA_TRY(cudaMemsetAsync(b_ctr.p, 0, size_t(P.slots) * 16, s));
+    CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
+    ctl = (Control *)b_ctl.p;
+    CUDA_TRY(cudaMallocAsync(&b_fail.p, size_t(re - rb + 1) * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_roots.p, size_t(re - rb + 1) * 4, s));
+
+    // label buffer: an estimate, grown (x2) when a tree does not fit
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    cap = o.label_capacity ? o.label_capacity : uint64_t(re - rb) * 64 + 1024;
+    if (!o.label_capacity) {
+        const uint64_t fit = uint64_t(0.25 * double(free_b)) / 12;
+        if (cap > fit) cap = fit;
+        if (cap < 1024) cap = 1024;
+    }
+    if (cap < 1) cap = 1;
+    CUDA_TRY(cudaMallocAsync(&b_ov.p, cap * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_oh.p, cap * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
+
+    CUDA_TRY(cudaEventRecord(ev[1], s));
+    for (int attempt = 0;; ++attempt) {
+        TreeLaunch tl{};
+        tl.n = n;
+        tl.row = rg.row;
+        tl.arc = rg.arc;
+        tl.vert_at = rg.vert_at;
+        tl.delta = P.delta;
+        tl.nwin = P.nwin;
+        tl.key = (uint64_t *)b_key.p;
+        tl.rtag = (uint32_t *)b_tags.p;
+        tl.wtag = tl.rtag + size_t(P.slots) * n;
+        tl.ftag = tl.wtag + size_t(P.slots) * n;
+        tl.lists = (uint32_t *)b_lists.p;
+        tl.slot_ctr = (uint32_t *)b_ctr.p;
+        tl.out_v = (uint32_t *)b_ov.p;
+        tl.out_h = (uint32_t *)b_oh.p;
+        tl.out_d = (uint32_t *)b_od.p;
+        tl.out_cap = cap;
+        tl.out_count = &ctl->out_count;
+        tl.next_root = &ctl->next_root;
+        tl.failed = (uint32_t *)b_fail.p;
+        tl.failed_count = &ctl->failed_count;
+        tl.flags = ctl->flags;
+        tl.stats = ctl->stats;
+        uint32_t count = 0;
+        if (first) {
+            tl.root_list = nullptr;
+            tl.root_begin = rb;
+            count = re - rb;
+        } else {
+            CUDA_TRY(cudaMemcpyAsync(b_roots.p, pending.data(), pending.size() * 4,
+                                     cudaMemcpyHostToDevice, s));
+            tl.root_list = (const uint32_t *)b_roots.p;
+            tl.root_begin = 0;
+            count = uint32_t(pending.size());
+        }
+        tl.root_count = count;
+        // reset the control block but keep the running output count
+        {
+            Control c0{};
+            c0.out_count = T;
+            CUDA_TRY(cudaMemcpyAsync(ctl, &c0, sizeof(Control), cudaMemcpyHostToDevice, s));
+        }
+        if (count) {
+            if (o.mode == 1) {
+                // plain form: one launch per root, one CTA per launch; the claim
+                // counter is reset so that launch i builds exactly root i
+                for (uint32_t i = 0; i < count; ++i) {
+                    TreeLaunch one = tl;
+                    if (one.root_list) one.root_list += i; else one.root_begin += i;
+                    one.root_count = 1;
+                    CUDA_TRY(cudaMemsetAsync(&ctl->next_root, 0, sizeof(unsigned int), s));
+                    CUDA_TRY(launch_plant_trees(one, P.tpt, 1, s));
+                    ++launches;
+                }
+            } else {
+                CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
+                ++launches;
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        for (int k = 0; k < 4; ++k) agg[k] += hc.stats[k];
+        if (hc.flags[0] == ERR_DIST_OVERFLOW) {
+            st = set_error(CHL_EOVERFLOW, "a shortest distance reaches UINT32_MAX");
+            goto done;
+        }
+        if (hc.flags[0] == ERR_ROUND_LIMIT) {
+            st = set_error(CHL_ETIMEOUT, "a tree exceeded its round limit");
+            goto done;
+        }
+        if (hc.flags[0] == ERR_RESERVE_LIMIT) {
+            st = set_error(CHL_ETIMEOUT, "label buffer reservation did not converge");
+            goto done;
+        }
+        T = hc.out_count;
+        if (!hc.flags[1]) break;  // every root of this attempt fit
+        // collect roots that failed or were never claimed, grow the buffer, go again
+        {
+            std::vector<uint32_t> failed(hc.failed_count);
+            if (hc.failed_count)
+                CUDA_TRY(cudaMemcpyAsync(failed.data(), b_fail.p, size_t(hc.failed_count) * 4,
+                                         cudaMemcpyDeviceToHost, s));
+            std::vector<uint32_t> prev = pending;
+            CUDA_TRY(cudaStreamSynchronize(s));
+            claimed_upto = hc.next_root < count ? hc.next_root : count;
+            if (o.mode == 1) {
+                // launches after the first failure claimed nothing: resume after it
+                claimed_upto = count;
+                if (!failed.empty()) {
+                    for (uint32_t i = 0; i < count; ++i)
+                        if ((first ? rb + i : prev[i]) == failed[0]) { claimed_upto = i + 1; break; }
+                }
+            }
+            pending = failed;
+            for (uint32_t i = claimed_upto; i < count; ++i)
+                pending.push_back(first ? rb + i : prev[i]);
+            first = false;
+            if (attempt > 40) {
+                st = set_error(CHL_ENOMEM, "label buffer cannot grow further");
+                goto done;
+            }
+            uint64_t ncap = cap * 2;
+            void *nv = nullptr, *nh = nullptr, *nd = nullptr;
+            CUDA_TRY(cudaMallocAsync(&nv, ncap * 4, s));
+            CUDA_TRY(cudaMallocAsync(&nh, ncap * 4, s));
+            CUDA_TRY(cudaMallocAsync(&nd, ncap * 4, s));
+            CUDA_TRY(cudaMemcpyAsync(nv, b_ov.p, T * 4, cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(nh, b_oh.p, T * 4, cudaMemcpyDeviceToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(nd, b_od.p, T * 4, cudaMemcpyDeviceToDevice, s));
+            cudaFreeAsync(b_ov.p, s);
+            cudaFreeAsync(b_oh.p, s);
+            cudaFreeAsync(b_od.p, s);
+            b_ov.p = nv;
+            b_oh.p = nh;
+            b_od.p = nd;
+            cap = ncap;
+        }
+    }
+    CUDA_TRY(cudaEventRecord(ev[2], s));
+    // slot state is no longer needed: release it before assembly
+    cudaFreeAsync(b_key.p, s); b_key.p = nullptr;
+    cudaFreeAsync(b_tags.p, s); b_tags.p = nullptr;
+    cudaFreeAsync(b_lists.p, s); b_lists.p = nullptr;
+
+    CUDA_TRY(assemble_labels(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
+                             (const uint32_t *)b_od.p, rg.vert_at, csr, &too_long, s, &launches));
+    if (too_long) {
+        st = set_error(CHL_EOVERFLOW, "a vertex holds more labels than the segment sorter supports");
+        goto done;
+    }
+    CUDA_TRY(cudaEventRecord(ev[3], s));
+    CUDA_TRY(cudaEventSynchronize(ev[3]));
+    cudaEventElapsedTime(&ms_total, ev[0], ev[3]);
+    cudaEventElapsedTime(&ms_tree, ev[1], ev[2]);
+    cudaEventElapsedTime(&ms_sort, ev[2], ev[3]);
+
+    L = new (std::nothrow) chl_labels;
+    if (!L) {
+        st = set_error(CHL_ENOMEM, "host allocation failed");
+        goto done;
+    }
+    L->n = n;
+    L->total = T;
+    L->offsets = csr.offsets;
+    L->hub = csr.hub;
+    L->hubpos = csr.hubpos;
+    L->dist = csr.dist;
+    L->bytes = (uint64_t(n) + 1) * 8 + T * 12;
+    L->device = dev;
+    L->stats.trees = agg[3];
+    L->stats.labels = T;
+    L->stats.expanded = agg[0];
+    L->stats.arcs = agg[1];
+    L->stats.trivial = agg[2];
+    L->stats.build_ms = ms_total;
+    L->stats.tree_ms = ms_tree;
+    L->stats.sort_ms = ms_sort;
+    L->stats.launches = uint64_t(launches);
+    csr = LabelCSR{};
+    *out = L;
+done:
+    if (csr.offsets) cudaFreeAsync(csr.offsets, s);
+    if (csr.hub) cudaFreeAsync(csr.hub, s);
+    if (csr.hubpos) cudaFreeAsync(csr.hubpos, s);
+    if (csr.dist) cudaFreeAsync(csr.dist, s);
+    free_graph(rg, s);
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    // DevBuf destructors release the rest on stream s
+    return st;
+}
+
+extern "C" chl_status chl_labels_info(const chl_labels *L, uint32_t *n, uint64_t *total,
+                                      uint64_t *bytes) {
+    if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    if (n) *n = L->n;
+    if (total) *total = L->total;
+    if (bytes) *bytes = L->bytes;
+    return CHL_OK;
+}
+
+extern "C" chl_status chl_labels_stats(const chl_labels *L, chl_build_stats *stats) {
+    if (!L || !stats) return set_error(CHL_EINVAL, "NULL argument");
+    *stats = L->stats;
+    return CHL_OK;
+}
+
+extern "C" chl_status chl_labels_view(const chl_labels *L, const uint64_t **offsets,
+                                      const uint32_t **hub, const uint32_t **dist) {
+    if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    if (offsets) *offsets = L->offsets;
+    if (hub) *hub = L->hub;
+    if (dist) *dist = L->dist;
+    return CHL_OK;
+}
+
+extern "C" chl_status chl_labels_copy(const chl_labels *L, uint64_t *offsets, uint32_t *hub,
+                                      uint32_t *dist, chl_mem dst_mem, void *stream) {
+    if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    if (dst_mem != CHL_MEM_DEVICE && dst_mem != CHL_MEM_HOST)
+        return set_error(CHL_EINVAL, "unknown memory kind");
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind k = dst_mem == CHL_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    chl_status st = CHL_OK;
+    if (offsets) CUDA_TRY(cudaMemcpyAsync(offsets, L->offsets, (size_t(L->n) + 1) * 8, k, s));
+    if (hub && L->total) CUDA_TRY(cudaMemcpyAsync(hub, L->hub, L->total * 4, k, s));
+    if (dist && L->total) CUDA_TRY(cudaMemcpyAsync(dist, L->dist, L->total * 4, k, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+done:
+    return st;
+}
+
+extern "C" chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint64_t q,
+                                uint32_t *out, chl_mem mem, void *stream) {
+    g_err[0] = 0;
+    if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    if (q == 0) return CHL_OK;
+    if (!pairs || !out) return set_error(CHL_EINVAL, "pairs or out is NULL");
+    if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
+    cudaStream_t s = (cudaStream_t)stream;
+    chl_status st = CHL_OK;
+    DevBuf b_p, b_o, b_bad;
+    b_p.s = b_o.s = b_bad.s = s;
+    const uint32_t *dp = pairs;
+    uint32_t *dout = out;
+    int hbad = 0;
+    CUDA_TRY(cudaMallocAsync(&b_bad.p, sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(b_bad.p, 0, sizeof(int), s));
+    if (mem == CHL_MEM_HOST) {
+        CUDA_TRY(cudaMallocAsync(&b_p.p, q * 8, s));
+        CUDA_TRY(cudaMallocAsync(&b_o.p, q * 4, s));
+        CUDA_TRY(cudaMemcpyAsync(b_p.p, pairs, q * 8, cudaMemcpyHostToDevice, s));
+        dp = (const uint32_t *)b_p.p;
+        dout = (uint32_t *)b_o.p;
+    }
+    CUDA_TRY(launch_query(L->n, L->offsets, L->hubpos, L->dist, dp, q, dout, (int *)b_bad.p, s));
+    if (mem == CHL_MEM_HOST) CUDA_TRY(cudaMemcpyAsync(out, dout, q * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&hbad, b_bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) st = set_error(CHL_EINVAL, "a query vertex id is >= n");
+done:
+    return st;
+}
+
+extern "C" void chl_labels_free(chl_labels *L) {
+    if (!L) return;
+    cudaFree(L->offsets);
+    cudaFree(L->hub);
+    cudaFree(L->hubpos);
+    cudaFree(L->dist);
+    delete L;
+}

@@ -1,0 +1,118 @@
+// Internal declarations shared by the translation units of libchl.so.
+// Nothing here is part of the public ABI (include/chl.h).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/chl.h"
+
+namespace chl {
+
+// ------------------------------------------------------------------ keys
+// A tree search key packs (distance, ancestor) into 64 bits:
+//   key = dist << 32 | anc
+// where vertices are renumbered by rank position (pos 0 = most important),
+// so the ancestor with the highest rank R is the one with the smallest id.
+// Under unsigned min a shorter distance wins, and at equal distance the
+// higher-ranked ancestor wins: the tie rule of Algorithm 3 (equal-distance
+// branch) and of the worked example in Sec. 4.2 (a[v5] = v1).
+// `anc` is the smallest pos over the vertices of the best known paths from
+// the root, excluding the vertex itself; a vertex v is "live" (would receive
+// the root h as a hub) iff min(anc, v) == h, i.e. anc == h and v >= h.
+constexpr uint64_t KEY_INF = ~0ull;
+__host__ __device__ inline uint64_t make_key(uint32_t dist, uint32_t anc) {
+    return (uint64_t(dist) << 32) | anc;
+}
+__host__ __device__ inline uint32_t key_dist(uint64_t k) { return uint32_t(k >> 32); }
+__host__ __device__ inline uint32_t key_anc(uint64_t k) { return uint32_t(k); }
+
+// ------------------------------------------------------------------ graph in rank order
+// The input graph renumbered by rank position: vertex p of this graph is the
+// vertex of rank position p (R = n-1-p) of the caller's graph.
+struct RankGraph {
+    uint32_t n = 0;
+    uint64_t m2 = 0;             // arcs
+    uint64_t *row = nullptr;     // [n+1]
+    uint2 *arc = nullptr;        // [m2] {neighbour pos, weight}
+    uint32_t *vert_at = nullptr; // [n] pos -> caller vertex id
+    uint32_t *pos_of = nullptr;  // [n] caller vertex id -> pos
+    uint32_t w_max = 0, w_min = 0;
+    double w_mean = 0.0;
+};
+
+// ------------------------------------------------------------------ tree kernel interface
+struct TreeLaunch {
+    // graph (rank order)
+    uint32_t n;
+    const uint64_t *row;
+    const uint2 *arc;
+    const uint32_t *vert_at;
+    // roots: pos ids root_list[i] (if non-null) or root_begin + i, i < root_count
+    const uint32_t *root_list;
+    uint32_t root_begin;
+    uint32_t root_count;
+    // search parameters
+    uint32_t delta;
+    uint32_t nwin;
+    // slot state: slot s owns [s*n, (s+1)*n) of each array
+    uint64_t *key;      // KEY_INF when idle
+    uint32_t *rtag, *wtag, *ftag;
+    uint32_t *lists;    // 5 lists per slot: cur, nxt, win, far, touched -> [slot][5][n]
+    uint32_t *slot_ctr; // [slot][4] persistent instance counters
+    // label output (structure of arrays)
+    uint32_t *out_v;    // caller vertex id of the labelled vertex
+    uint32_t *out_h;    // hub pos id
+    uint32_t *out_d;    // distance
+    unsigned long long out_cap;
+    unsigned long long *out_count;
+    // control
+    unsigned int *next_root;
+    uint32_t *failed;          // roots whose labels did not fit
+    unsigned int *failed_count;
+    int *flags;                // [0] error code, [1] output full
+    unsigned long long *stats; // [0] expanded [1] arcs [2] trivial [3] trees
+};
+
+enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2, ERR_RESERVE_LIMIT = 3 };
+
+// launches (defined in chl_tree.cu)
+cudaError_t launch_plant_trees(const TreeLaunch &p, int threads_per_tree, int slots,
+                               cudaStream_t s);
+int plant_max_slots_per_sm(int threads_per_tree);
+
+// label assembly (chl_labels.cu)
+struct LabelCSR {
+    uint64_t *offsets = nullptr; // [n+1] by caller vertex id
+    uint32_t *hub = nullptr;     // caller vertex id
+    uint32_t *hubpos = nullptr;  // rank position of hub (sorted ascending per vertex)
+    uint32_t *dist = nullptr;
+};
+// builds CSR from T label triples; returns error status via cudaError_t, sets
+// *too_long when a vertex holds more labels than the sorter handles
+cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const uint32_t *in_h,
+                            const uint32_t *in_d, const uint32_t *vert_at, LabelCSR &out,
+                            int *too_long, cudaStream_t s, int *launches);
+
+// queries (chl_query.cu)
+// bad is set to 1 when a pair holds a vertex id >= n (that answer is UINT32_MAX)
+cudaError_t launch_query(uint32_t n, const uint64_t *offsets, const uint32_t *hubpos,
+                         const uint32_t *dist, const uint32_t *pairs, uint64_t q, uint32_t *out,
+                         int *bad, cudaStream_t s);
+
+// exclusive prefix sum of n uint64 values (out may alias in); chl_graph.cu
+cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
+                               int *launches);
+
+// graph preparation (chl_graph.cu)
+// validates the caller CSR (device copy) and rank; builds the rank-ordered graph
+// returns CHL_OK / CHL_EINVAL (with message) / CHL_ECUDA / CHL_ENOMEM
+chl_status prepare_graph(uint32_t n, uint64_t m2, const uint64_t *row, const uint32_t *col,
+                         const uint32_t *w, const uint32_t *rank, RankGraph &g, cudaStream_t s,
+                         int *launches);
+void free_graph(RankGraph &g, cudaStream_t s);
+
+// errors (chl_api.cu)
+chl_status set_error(chl_status st, const char *fmt, ...);
+
+}  // namespace chl

@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads without a GPU and exports every function
+declared in include/chl.h; argument errors are reported before any GPU work."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1907_00140_gb300 as chl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "chl.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(chl_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    chl.build()
+    return chl.lib()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert {"chl_build", "chl_query", "chl_labels_free", "chl_last_error"} <= set(names)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_version(lib):
+    assert "sm_103a" in chl.chl_version()
+
+
+def test_null_arguments_are_einval(lib):
+    assert lib.chl_build(None, None, None, None, None) == chl.CHL_EINVAL
+    out = C.c_void_p()
+    assert lib.chl_build(None, None, None, None, C.byref(out)) == chl.CHL_EINVAL
+    assert "NULL" in chl.chl_last_error()
+    g = chl.chl_csr(0, 0, None, None, None, 0)
+    assert lib.chl_build(C.byref(g), C.c_void_p(1), None, None, C.byref(out)) == chl.CHL_EINVAL
+    assert out.value is None
+    assert lib.chl_query(None, None, 0, None, 0, None) == chl.CHL_EINVAL
+    assert lib.chl_labels_info(None, None, None, None) == chl.CHL_EINVAL
+    lib.chl_labels_free(None)
+
+
+def test_bad_options_are_einval(lib):
+    g = chl.chl_csr(4, 0, 1, None, None, chl.CHL_MEM_HOST)
+    out = C.c_void_p()
+    for field, val in [("threads_per_tree", 48), ("window_buckets", 1), ("mode", 3),
+                       ("root_end", 9), ("slots", -1)]:
+        o = chl.chl_build_opts()
+        setattr(o, field, val)
+        assert lib.chl_build(C.byref(g), C.c_void_p(1), C.byref(o), None, C.byref(out)) == chl.CHL_EINVAL, field
+
+
+def test_no_fallback_without_library(tmp_path, monkeypatch):
+    monkeypatch.setattr(chl, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(chl, "_lib", None)
+    with pytest.raises(RuntimeError):
+        chl.lib()

@@ -1,0 +1,81 @@
+"""Full-size parity on sampled outputs.
+
+Trees are independent (Sec. 4.2), so the labels whose hub is a sampled root
+can be checked one tree at a time against the oracle; the whole labeling is
+checked through the cover property (query = Dijkstra distance, Sec. 1) on
+sampled pairs and through invariants that hold at any size. The GPU build
+runs in the default launch configuration, the one the benchmark times.
+"""
+import numpy as np
+import pytest
+from scipy.sparse import csr_matrix
+from scipy.sparse.csgraph import dijkstra
+
+import oracle as O
+import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1907_00140_gb300 as chl  # noqa: E402
+from test_gpu_parity import DG, dev  # noqa: E402
+
+
+def sample_roots(n, seed):
+    """rank positions: the 64 most important, 256 uniform, the 256 least important"""
+    rng = np.random.default_rng(seed)
+    mid = rng.choice(np.arange(64, n - 256), 256, replace=False)
+    return np.unique(np.concatenate([np.arange(64), mid, np.arange(n - 256, n)]))
+
+
+def check_workload(name, seed):
+    g, rank = W.load(name)
+    n = g.n
+    L = chl.build_labels(DG(g), dev(rank))
+    off, hub, dist = L.to_numpy()
+    order = np.empty(n, np.uint32)
+    order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
+    # 1) sampled trees, bit-exact
+    roots = order[sample_roots(n, seed)]
+    ref = O.build_labels(g, rank, "plant", roots=roots, threads=16)
+    keep = np.isin(hub, roots)
+    vert = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))
+    sub_off = np.zeros(n + 1, np.uint64)
+    np.add.at(sub_off, vert[keep] + 1, 1)
+    sub_off = np.cumsum(sub_off).astype(np.uint64)
+    assert np.array_equal(sub_off, ref.offsets)
+    assert np.array_equal(hub[keep], ref.hub)
+    assert np.array_equal(dist[keep], ref.dist)
+    # 2) invariants at full size: self label last, hubs in descending rank, top hub first
+    lens = np.diff(off.astype(np.int64))
+    assert (lens >= 1).all()
+    last = off[1:].astype(np.int64) - 1
+    assert np.array_equal(hub[last], np.arange(n)) and (dist[last] == 0).all()
+    r = rank[hub].astype(np.int64)
+    inner = np.ones(len(hub), bool)
+    inner[last] = False
+    assert (r[:-1][inner[:-1]] > r[1:][inner[:-1]]).all()
+    assert (hub[off[:-1].astype(np.int64)] == order[0]).all()
+    # 3) cover: queries equal Dijkstra distances on sampled pairs
+    rng = np.random.default_rng(seed + 1)
+    src = rng.choice(n, 32, replace=False)
+    A = csr_matrix((g.w.astype(np.float64), g.col.astype(np.int64), g.row_ptr.astype(np.int64)),
+                   shape=(n, n))
+    D = dijkstra(A, indices=src)
+    tgt = rng.integers(0, n, size=(32, 2000))
+    pairs = np.stack([np.repeat(src, 2000), tgt.ravel()], 1).astype(np.uint32)
+    got = L.query(dev(pairs)).cpu().numpy().view(np.uint32)
+    want = D[np.repeat(np.arange(32), 2000), tgt.ravel()].astype(np.uint32)
+    assert np.array_equal(got, want)
+    return L
+
+
+def test_rmat18_sampled_parity():
+    check_workload("rmat18", 18)
+
+
+def test_grid512_sampled_parity():
+    check_workload("grid512", 512)
