@@ -107,6 +107,7 @@ typedef struct chl_labels chl_labels;
  *                          dynamically in rank order by one launch);
  *                          1 = plain: one launch per root (one CTA of
  *                          threads_per_tree threads, default 512, builds it)
+ *   flags                  reserved, must be 0
  *   label_capacity         initial size of the label buffer in labels; when
  *                          a tree does not fit, the buffer doubles and the
  *                          roots that did not fit are built again
@@ -119,9 +120,10 @@ typedef struct {
     int32_t window_buckets;
     int32_t slots;
     int32_t mode;
-    int32_t reserved;
+    int32_t flags;
     uint64_t label_capacity;
 } chl_build_opts;
+
 
 /*
  * Counters of a finished build (for throughput and exploration reports).

@@ -89,7 +89,7 @@ class chl_build_opts(C.Structure):
     _fields_ = [("root_begin", C.c_uint32), ("root_end", C.c_uint32),
                 ("threads_per_tree", C.c_int32), ("bucket_delta", C.c_int32),
                 ("window_buckets", C.c_int32), ("slots", C.c_int32), ("mode", C.c_int32),
-                ("reserved", C.c_int32), ("label_capacity", C.c_uint64)]
+                ("flags", C.c_int32), ("label_capacity", C.c_uint64)]
 
 
 class chl_build_stats(C.Structure):

@@ -129,6 +129,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         return set_error(CHL_EINVAL, "window_buckets must be in [2,64]");
     if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
     if (o.bucket_delta < 0 || o.slots < 0) return set_error(CHL_EINVAL, "negative option");
+    if (o.flags != 0) return set_error(CHL_EINVAL, "flags is reserved and must be 0");
 
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;
@@ -212,8 +213,11 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
 
     // label buffer: an estimate, grown (x2) when a tree does not fit
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    cap = o.label_capacity ? o.label_capacity : uint64_t(re - rb) * 64 + 1024;
-    if (!o.label_capacity) {
+    // label buffer: generous (up to 1024 labels per root within a quarter of the
+    // free memory); it doubles and the roots that did not fit are rebuilt
+    cap = o.label_capacity;
+    if (!cap) {
+        cap = uint64_t(re - rb) * 1024 + 1024;
         const uint64_t fit = uint64_t(0.25 * double(free_b)) / 12;
         if (cap > fit) cap = fit;
         if (cap < 1024) cap = 1024;

@@ -84,25 +84,44 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t *l
     if (pred) list[base + __popc(m & ((1u << lane) - 1))] = val;
 }
 
-// relax one arc (v -> a.x, weight a.y) of a vertex expanded with distance dv
-// and inclusive ancestor av = min(anc(v), v)
-__device__ __forceinline__ void relax(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t h,
-                                      uint32_t dv, uint32_t av, uint2 a,
-                                      unsigned long long &arcs) {
-    const uint32_t u = a.x;
+// Relaxation of one arc (v -> u, weight w) of a vertex expanded with distance
+// dv and inclusive ancestor av = min(anc(v), v), in two stages so that a lane
+// can have several key loads in flight:
+//   probe:  form the candidate key and load the target's key from L2 (keys
+//           only decrease, so a stale read never hides an improvement)
+//   commit: if the candidate is smaller, atomicMin; on improvement, record
+//           the vertex as touched and list it for the bucket it now falls in
+
+struct Probe {
+    uint64_t cand;
+    uint64_t seen;
+    uint32_t u;
+    bool live;  // still worth committing
+};
+
+__device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t dv,
+                                      uint32_t av, uint2 a, Probe &q) {
+    q.u = a.x;
     const uint64_t nd = uint64_t(dv) + a.y;
-    ++arcs;
     if (nd >= 0xFFFFFFFFull) {
         atomicExch(&p.flags[0], ERR_DIST_OVERFLOW);
         S.abort = 1;
+        q.live = false;
         return;
     }
-    const uint64_t cand = make_key(uint32_t(nd), av);
-    const uint64_t seen = __ldcg(&sl.key[u]);
-    if (cand >= seen) return;  // keys only decrease: a stale read never hides an improvement
-    const uint64_t old = atomicMin((unsigned long long *)&sl.key[u], (unsigned long long)cand);
-    if (cand >= old) return;
+    q.cand = make_key(uint32_t(nd), av);
+    q.seen = __ldcg(&sl.key[q.u]);
+    q.live = true;
+}
+
+__device__ __forceinline__ void commit(Shared &S, const Slot &sl, uint32_t h, uint32_t av,
+                                       const Probe &q) {
+    const uint32_t u = q.u;
+    if (q.cand >= q.seen) return;
+    const uint64_t old = atomicMin((unsigned long long *)&sl.key[u], (unsigned long long)q.cand);
+    if (q.cand >= old) return;
     if (old == KEY_INF) sl.touch[atomicAdd(&S.touch_n, 1u)] = u;
+    const uint64_t nd = key_dist(q.cand);
     if (nd < S.t_hi) {
         if (atomicExch(&sl.rtag[u], S.rid) != S.rid) {
             uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
@@ -115,6 +134,8 @@ __device__ __forceinline__ void relax(const TreeLaunch &p, Shared &S, const Slot
         if (av == h && u > h) S.far_live = 1;
     }
 }
+
+constexpr int UNROLL = 4;
 
 // expand every vertex of the current list once
 template <int TPB>
@@ -146,7 +167,27 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
             const uint32_t ba = __shfl_sync(FULL, av, src);
             const uint64_t brs = __shfl_sync(FULL, rs, src);
             const uint32_t bdeg = __shfl_sync(FULL, deg, src);
-            for (uint32_t j = lane; j < bdeg; j += 32) relax(p, S, sl, h, bd, ba, __ldg(&p.arc[brs + j]), arcs);
+            for (uint32_t j0 = 0; j0 < bdeg; j0 += 32 * UNROLL) {
+                Probe q[UNROLL];
+                uint2 a[UNROLL];
+#pragma unroll
+                for (int k = 0; k < UNROLL; ++k) {
+                    const uint32_t j = j0 + k * 32 + lane;
+                    if (j < bdeg) a[k] = __ldg(&p.arc[brs + j]);
+                }
+#pragma unroll
+                for (int k = 0; k < UNROLL; ++k) {
+                    const uint32_t j = j0 + k * 32 + lane;
+                    q[k].live = false;
+                    if (j < bdeg) {
+                        ++arcs;
+                        probe(p, S, sl, bd, ba, a[k], q[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < UNROLL; ++k)
+                    if (q[k].live) commit(S, sl, h, ba, q[k]);
+            }
         }
         // low-degree vertices: pack their arcs densely over the lanes
         const uint32_t ds = deg < LARGE_DEG ? deg : 0;
@@ -171,7 +212,12 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
             const uint32_t oa = __shfl_sync(FULL, av, o);
             const uint32_t oex = __shfl_sync(FULL, excl, o);
             const uint64_t ors = __shfl_sync(FULL, rs, o);
-            if (j < total) relax(p, S, sl, h, od, oa, __ldg(&p.arc[ors + (j - oex)]), arcs);
+            if (j < total) {
+                Probe q;
+                ++arcs;
+                probe(p, S, sl, od, oa, __ldg(&p.arc[ors + (j - oex)]), q);
+                if (q.live) commit(S, sl, h, oa, q);
+            }
         }
     }
 }
@@ -220,6 +266,9 @@ __device__ void list_pass(Shared &S, const Slot &sl, uint32_t h, uint32_t *list,
         warp_append(keep, u, list, &S.out_n);
         if (mode == 1) warp_append(move, u, dst, dst_count);
     }
+    // the tag resets above are plain stores, while tags are later updated by
+    // atomics performed in L2: publish them device-wide before the barrier
+    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) *count = S.out_n;
     mn = warp_min(mn);
@@ -304,7 +353,7 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
                 S.abort = 0;
                 sl.l0[0] = h;
                 sl.touch[0] = h;
-                sl.key[h] = make_key(0, h);
+                atomicExch((unsigned long long *)&sl.key[h], (unsigned long long)make_key(0, h));
             }
             __syncthreads();
             uint32_t rounds = 0;
@@ -382,6 +431,7 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
             if (S.abort) {
                 // reset and give up on this tree; the host reports the error
                 for (uint32_t i = threadIdx.x; i < S.touch_n; i += TPB) sl.key[sl.touch[i]] = KEY_INF;
+                __threadfence();
                 __syncthreads();
                 break;
             }
@@ -416,6 +466,9 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
             nlab = S.out_n;
             // reset exactly what this tree modified
             for (uint32_t i = threadIdx.x; i < nt; i += TPB) sl.key[sl.touch[i]] = KEY_INF;
+            // the next tree reads keys with L2 loads and L2 atomics: the plain
+            // reset stores must be visible there first, not only inside the CTA
+            __threadfence();
         }
 
         // ---- reserve an all-or-nothing output range and copy the labels out

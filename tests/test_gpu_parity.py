@@ -148,6 +148,18 @@ def test_root_ranges_partition_labels_by_hub(ba2k):
         assert_same(want, off, hub, dist)
 
 
+def test_repeated_single_slot_builds(ba2k):
+    """One CTA runs every tree back to back on the same slot state, with
+    narrow buckets (many rounds per bucket): the configuration most exposed to
+    ordering races between rounds, buckets and consecutive trees."""
+    g, rank, ref = ba2k
+    G, R = DG(g), dev(rank)
+    for _ in range(12):
+        L = chl.build_labels(G, R, slots=1, bucket_delta=3)
+        assert_same(ref, *L.to_numpy())
+        L.free()
+
+
 def test_deterministic(ba2k):
     g, rank, _ = ba2k
     a = gpu_labels(g, rank)[1:]
