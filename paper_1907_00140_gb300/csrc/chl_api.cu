@@ -68,8 +68,8 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     int per_sm = plant_max_slots_per_sm(p.tpt);
     if (per_sm < 1) per_sm = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
-    // slot state: key 8 + three tags 12 + five lists 20 bytes per vertex
-    const double per_slot = 40.0 * double(g.n) + 64.0;
+    // slot state per vertex: key 8 + three tags 12 + (4 + nwin) lists of 4 bytes
+    const double per_slot = (20.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
     const double budget = 0.35 * double(free_bytes);
     long long cap = (long long)(budget / per_slot);
     if (o.slots <= 0 && slots > cap) slots = cap;
@@ -203,7 +203,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     CUDA_TRY(cudaMemsetAsync(b_key.p, 0xFF, size_t(P.slots) * n * 8, s));
     CUDA_TRY(cudaMallocAsync(&b_tags.p, size_t(P.slots) * n * 12, s));
     CUDA_TRY(cudaMemsetAsync(b_tags.p, 0, size_t(P.slots) * n * 12, s));
-    CUDA_TRY(cudaMallocAsync(&b_lists.p, size_t(P.slots) * n * 20, s));
+    CUDA_TRY(cudaMallocAsync(&b_lists.p, size_t(P.slots) * n * 4 * (4 + P.nwin), s));
     CUDA_TRY(cudaMallocAsync(&b_ctr.p, size_t(P.slots) * 16, s));
     CUDA_TRY(cudaMemsetAsync(b_ctr.p, 0, size_t(P.slots) * 16, s));
     CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));

@@ -58,7 +58,7 @@ struct TreeLaunch {
     // slot state: slot s owns [s*n, (s+1)*n) of each array
     uint64_t *key;      // KEY_INF when idle
     uint32_t *rtag, *wtag, *ftag;
-    uint32_t *lists;    // 5 lists per slot: cur, nxt, win, far, touched -> [slot][5][n]
+    uint32_t *lists;    // per slot: round lists l0, l1, far, touched, then nwin bucket lists
     uint32_t *slot_ctr; // [slot][4] persistent instance counters
     // label output (structure of arrays)
     uint32_t *out_v;    // caller vertex id of the labelled vertex

@@ -5,33 +5,38 @@
 // the next root in rank order with a global atomic counter, the dynamic
 // root claiming of Sec. 3.1 (threads pop the most important remaining root).
 //
-// Per tree the search is a bucketed label-correcting Dijkstra (delta-stepping)
-// over packed keys dist<<32 | anc (see chl_common.cuh): a 64-bit atomicMin
-// keeps the shortest distance and, at equal distance, the highest-ranked
-// ancestor (Algorithm 3, equal-distance branch). Every vertex that is
-// expanded relaxes all its arcs, labelled or not: PLaNT does not prune trees
-// (Sec. 1, Sec. 4.2); a vertex outranked by its ancestor only gets no label.
+// Per tree the search is a bucketed label-correcting Dijkstra (delta-stepping,
+// bucket width delta) over packed keys dist<<32 | anc (see chl_common.cuh): a
+// 64-bit atomicMin keeps the shortest distance and, at equal distance, the
+// highest-ranked ancestor (Algorithm 3, equal-distance branch). Every vertex
+// that is expanded relaxes all its arcs, labelled or not: PLaNT does not
+// prune trees (Sec. 1, Sec. 4.2); a vertex outranked by its ancestor only gets
+// no label.
 //
-// Early termination (Sec. 4.2): the paper stops a tree when every vertex in
-// Dijkstra's queue is outranked (cnt = 0). Here the pending vertices are the
-// ones whose key lies in a later bucket; after a bucket converges, all keys
-// below its upper bound are final, and the tree stops once no pending vertex
-// is live. The test is exact at bucket granularity: the lists that hold
-// pending vertices are scanned (the far list only when a live key was ever
-// sent there).
+// Pending vertices (keys in later buckets) are held per bucket:
+//   sub[s]   one list per bucket of the current window of `nwin` buckets
+//            (bucket win_base + s); a vertex is listed once per bucket it
+//            enters (keys only decrease, so an earlier entry is then stale)
+//   far      vertices whose bucket lies beyond the window; when the window is
+//            used up it restarts at the nearest far bucket
+//   nxt      vertices improved inside the current bucket during a round
+// plus `touched`, every vertex that got a finite key (for emission and for
+// resetting only what the tree modified, footnote of Sec. 3.1).
 //
-// Pending vertices sit in four deduplicated lists per slot:
-//   cur  vertices of the current bucket to expand this round
-//   nxt  vertices of the current bucket improved during this round
-//   win  vertices in later buckets of the current window (nwin buckets)
-//   far  vertices beyond the window
-// plus `touched`, every vertex that got a finite key (for emission and
-// for resetting only what the tree modified, footnote of Sec. 3.1).
+// Early termination (Sec. 4.2). The paper stops when every vertex in
+// Dijkstra's queue is outranked; Algorithm 3 keeps the count `cnt` of queued
+// vertices whose ancestor is the root. Here `cnt` counts the live vertices
+// whose key lies beyond the current bucket: every successful atomicMin on a
+// key adds f(new) - f(old), f(K) = [K live and beyond the current bucket].
+// atomicMin serialises the updates of one key, so the sum telescopes to the
+// exact count whatever the order of the atomic adds; entering a bucket
+// subtracts its live vertices. After a bucket converges all keys below its
+// end are final, so the tree stops when cnt = 0: exact at bucket granularity.
 //
 // Labels: after a tree stops, every touched vertex whose key is live gets
 // (vertex, root, dist); the tree reserves its output range with one CAS
-// (the range is all-or-nothing, so a full buffer loses no partial tree), and
-// the host rebuilds failed roots after growing the buffer.
+// (all-or-nothing, so a full buffer loses no partial tree), and the host
+// rebuilds failed roots after growing the buffer.
 #include <cstdio>
 
 #include "chl_common.cuh"
@@ -43,28 +48,43 @@ constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t MAX_ROUNDS_PER_TREE = 1u << 26;
 constexpr uint32_t RESERVE_TRIES = 1u << 20;
 constexpr int LARGE_DEG = 32;
+constexpr uint32_t NWIN_MAX = 64;
+constexpr int UNROLL = 4;
+constexpr uint32_t CHUNK = 32 * UNROLL;  // arcs one warp relaxes per step
+constexpr uint32_t HUB_DEG = 4 * CHUNK;  // rows this long are shared by all warps
+constexpr uint32_t HUBQ = 128;           // queued hub rows per round
+constexpr uint32_t NONE = 0xFFFFFFFFu;
 
 struct Shared {
     uint32_t root;
-    uint32_t cur_n, nxt_n, win_n, far_n, touch_n;
-    uint32_t rid, wid, fid;
-    uint32_t sel;          // which of list 0/1 is cur
-    uint64_t t_hi, w_hi;   // bucket and window upper bounds (exclusive)
-    uint32_t min_d;
+    uint32_t cur_n, nxt_n, far_n, touch_n;
+    uint32_t rid, fid;
+    uint32_t sel;          // round lists: cur = sel ? l1 : l0 (rounds after the first)
+    uint32_t cur_slot;     // window slot expanded in the bucket's first round, NONE after
+    uint32_t bcur;         // current bucket
+    uint32_t win_base;     // bucket of window slot 0
+    uint32_t bid_base;     // tag of bucket b is bid_base + b + 1
+    uint32_t bid_top;      // one past the largest bucket tagged in this tree
+    int cnt;               // live vertices with keys beyond the current bucket
+    uint64_t t_lo, t_hi;   // current bucket [t_lo, t_hi)
+    uint64_t w_hi;         // end of the window
+    uint32_t min_b;
     uint32_t out_n;
-    int far_live;
-    int live;
-    int tmp_live;
-    uint32_t tmp_min;
     int abort;
     int ok;
+    int live_sum;
     unsigned long long base;
+    uint32_t sub_n[NWIN_MAX];
+    // high-degree rows queued for CTA-wide processing in the current round
+    uint32_t hub_n, hub_next;
+    uint32_t hub_dv[HUBQ], hub_av[HUBQ], hub_deg[HUBQ], hub_pre[HUBQ + 1];
+    uint64_t hub_rs[HUBQ];
 };
 
 struct Slot {
     uint64_t *key;
     uint32_t *rtag, *wtag, *ftag;
-    uint32_t *l0, *l1, *win, *far, *touch;
+    uint32_t *l0, *l1, *far, *touch, *sub;  // sub: nwin lists of n entries
 };
 
 __device__ __forceinline__ bool is_live(uint64_t k, uint32_t v, uint32_t h) {
@@ -84,14 +104,22 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t *l
     if (pred) list[base + __popc(m & ((1u << lane) - 1))] = val;
 }
 
+// list a pending vertex in bucket b of the window (the tag dedups per bucket)
+__device__ __forceinline__ void sub_append(Shared &S, const Slot &sl, uint32_t n, uint32_t u,
+                                           uint32_t b) {
+    const uint32_t s = b - S.win_base;
+    const uint32_t tag = S.bid_base + b + 1;
+    if (atomicExch(&sl.wtag[u], tag) != tag) sl.sub[size_t(s) * n + atomicAdd(&S.sub_n[s], 1u)] = u;
+}
+
 // Relaxation of one arc (v -> u, weight w) of a vertex expanded with distance
 // dv and inclusive ancestor av = min(anc(v), v), in two stages so that a lane
 // can have several key loads in flight:
 //   probe:  form the candidate key and load the target's key from L2 (keys
 //           only decrease, so a stale read never hides an improvement)
-//   commit: if the candidate is smaller, atomicMin; on improvement, record
-//           the vertex as touched and list it for the bucket it now falls in
-
+//   commit: if the candidate is smaller, atomicMin; on improvement, update
+//           the live-pending count, record the vertex as touched and list it
+//           for the bucket it now falls in
 struct Probe {
     uint64_t cand;
     uint64_t seen;
@@ -114,37 +142,71 @@ __device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot
     q.live = true;
 }
 
-__device__ __forceinline__ void commit(Shared &S, const Slot &sl, uint32_t h, uint32_t av,
+__device__ __forceinline__ void commit(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t h,
                                        const Probe &q) {
-    const uint32_t u = q.u;
     if (q.cand >= q.seen) return;
+    const uint32_t u = q.u;
     const uint64_t old = atomicMin((unsigned long long *)&sl.key[u], (unsigned long long)q.cand);
     if (q.cand >= old) return;
     if (old == KEY_INF) sl.touch[atomicAdd(&S.touch_n, 1u)] = u;
-    const uint64_t nd = key_dist(q.cand);
-    if (nd < S.t_hi) {
+    const uint32_t nb = key_dist(q.cand) / p.delta;
+    const bool f_new = nb > S.bcur && is_live(q.cand, u, h);
+    const bool f_old = old != KEY_INF && key_dist(old) / p.delta > S.bcur && is_live(old, u, h);
+    if (f_new != f_old) atomicAdd(&S.cnt, f_new ? 1 : -1);
+    if (nb == S.bcur) {
         if (atomicExch(&sl.rtag[u], S.rid) != S.rid) {
             uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
             nxt[atomicAdd(&S.nxt_n, 1u)] = u;
         }
-    } else if (nd < S.w_hi) {
-        if (atomicExch(&sl.wtag[u], S.wid) != S.wid) sl.win[atomicAdd(&S.win_n, 1u)] = u;
-    } else {
-        if (atomicExch(&sl.ftag[u], S.fid) != S.fid) sl.far[atomicAdd(&S.far_n, 1u)] = u;
-        if (av == h && u > h) S.far_live = 1;
+    } else if (key_dist(q.cand) < S.w_hi) {
+        sub_append(S, sl, p.n, u, nb);
+    } else if (atomicExch(&sl.ftag[u], S.fid) != S.fid) {
+        sl.far[atomicAdd(&S.far_n, 1u)] = u;
     }
 }
 
-constexpr int UNROLL = 4;
+// relax arcs [j0, min(j0 + CHUNK, deg)) of one row, UNROLL arcs per lane in flight
+__device__ __forceinline__ void relax_chunk(const TreeLaunch &p, Shared &S, const Slot &sl,
+                                            uint32_t h, uint32_t dv, uint32_t av, uint64_t rs,
+                                            uint32_t deg, uint32_t j0, unsigned long long &arcs) {
+    const int lane = threadIdx.x & 31;
+    Probe q[UNROLL];
+    uint2 a[UNROLL];
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        const uint32_t j = j0 + k * 32 + lane;
+        if (j < deg) a[k] = __ldg(&p.arc[rs + j]);
+    }
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        const uint32_t j = j0 + k * 32 + lane;
+        q[k].live = false;
+        if (j < deg) {
+            ++arcs;
+            probe(p, S, sl, dv, av, a[k], q[k]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k)
+        if (q[k].live) commit(p, S, sl, h, q[k]);
+}
 
-// expand every vertex of the current list once
+// Expand the current list once. In the first round of a bucket the list is
+// the bucket's window list, whose stale entries (keys since lowered into an
+// earlier bucket) are skipped. Rows shorter than 32 arcs are packed densely
+// over the lanes of a warp; rows of 32..HUB_DEG-1 arcs are walked by the warp
+// that met them; longer rows (hubs of scale-free graphs) are queued and split
+// into CHUNK-arc pieces that all warps claim, so one hub does not hold the
+// whole CTA at the round barrier.
 template <int TPB>
 __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t h,
                              unsigned long long &expanded, unsigned long long &arcs) {
     constexpr int NW = TPB / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t *cur = S.sel ? sl.l1 : sl.l0;
+    const uint32_t *cur = S.cur_slot != NONE ? sl.sub + size_t(S.cur_slot) * p.n
+                                             : (S.sel ? sl.l1 : sl.l0);
     const uint32_t n_cur = S.cur_n;
+    const uint64_t t_lo = S.t_lo;
     for (uint32_t base = warp * 32; base < n_cur; base += NW * 32) {
         const uint32_t i = base + lane;
         uint32_t dv = 0, av = 0, deg = 0;
@@ -152,14 +214,27 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
         if (i < n_cur) {
             const uint32_t v = cur[i];
             const uint64_t k = __ldcg(&sl.key[v]);
-            dv = key_dist(k);
-            av = min(key_anc(k), v);
-            rs = __ldg(&p.row[v]);
-            deg = uint32_t(__ldg(&p.row[v + 1]) - rs);
-            ++expanded;
+            if (key_dist(k) >= t_lo) {  // else stale: expanded in an earlier bucket
+                dv = key_dist(k);
+                av = min(key_anc(k), v);
+                rs = __ldg(&p.row[v]);
+                deg = uint32_t(__ldg(&p.row[v + 1]) - rs);
+                ++expanded;
+            }
         }
-        // high-degree vertices: the whole warp walks the row, 32 arcs per step
-        unsigned big = __ballot_sync(FULL, deg >= LARGE_DEG);
+        bool queued = false;
+        if (deg >= HUB_DEG) {
+            const uint32_t slot = atomicAdd(&S.hub_n, 1u);
+            if (slot < HUBQ) {
+                S.hub_dv[slot] = dv;
+                S.hub_av[slot] = av;
+                S.hub_deg[slot] = deg;
+                S.hub_rs[slot] = rs;
+                queued = true;
+            }
+        }
+        // rows of 32+ arcs not queued: the whole warp walks the row
+        unsigned big = __ballot_sync(FULL, deg >= LARGE_DEG && !queued);
         while (big) {
             const int src = __ffs(big) - 1;
             big &= big - 1;
@@ -167,27 +242,8 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
             const uint32_t ba = __shfl_sync(FULL, av, src);
             const uint64_t brs = __shfl_sync(FULL, rs, src);
             const uint32_t bdeg = __shfl_sync(FULL, deg, src);
-            for (uint32_t j0 = 0; j0 < bdeg; j0 += 32 * UNROLL) {
-                Probe q[UNROLL];
-                uint2 a[UNROLL];
-#pragma unroll
-                for (int k = 0; k < UNROLL; ++k) {
-                    const uint32_t j = j0 + k * 32 + lane;
-                    if (j < bdeg) a[k] = __ldg(&p.arc[brs + j]);
-                }
-#pragma unroll
-                for (int k = 0; k < UNROLL; ++k) {
-                    const uint32_t j = j0 + k * 32 + lane;
-                    q[k].live = false;
-                    if (j < bdeg) {
-                        ++arcs;
-                        probe(p, S, sl, bd, ba, a[k], q[k]);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < UNROLL; ++k)
-                    if (q[k].live) commit(S, sl, h, ba, q[k]);
-            }
+            for (uint32_t j0 = 0; j0 < bdeg; j0 += CHUNK)
+                relax_chunk(p, S, sl, h, bd, ba, brs, bdeg, j0, arcs);
         }
         // low-degree vertices: pack their arcs densely over the lanes
         const uint32_t ds = deg < LARGE_DEG ? deg : 0;
@@ -216,70 +272,131 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
                 Probe q;
                 ++arcs;
                 probe(p, S, sl, od, oa, __ldg(&p.arc[ors + (j - oex)]), q);
-                if (q.live) commit(S, sl, h, oa, q);
+                if (q.live) commit(p, S, sl, h, q);
             }
         }
     }
+    __syncthreads();
+    // queued hub rows: CHUNK-arc pieces claimed by any warp
+    const uint32_t nh = min(S.hub_n, HUBQ);
+    if (nh) {
+        if (warp == 0) {
+            uint32_t run = 0;
+            for (uint32_t b = 0; b < nh; b += 32) {
+                const uint32_t it = b + lane;
+                const uint32_t c = it < nh ? (S.hub_deg[it] + CHUNK - 1) / CHUNK : 0;
+                uint32_t inc = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(FULL, inc, o);
+                    if (lane >= o) inc += t;
+                }
+                if (it < nh) S.hub_pre[it] = run + inc - c;
+                run += __shfl_sync(FULL, inc, 31);
+            }
+            if (lane == 0) {
+                S.hub_pre[nh] = run;
+                S.hub_next = 0;
+            }
+        }
+        __syncthreads();
+        const uint32_t chunks = S.hub_pre[nh];
+        for (;;) {
+            uint32_t c = 0;
+            if (lane == 0) c = atomicAdd(&S.hub_next, 1u);
+            c = __shfl_sync(FULL, c, 0);
+            if (c >= chunks) break;
+            uint32_t lo = 0, hi = nh;  // largest item with hub_pre[item] <= c
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (S.hub_pre[mid] <= c) lo = mid; else hi = mid;
+            }
+            relax_chunk(p, S, sl, h, S.hub_dv[lo], S.hub_av[lo], S.hub_rs[lo], S.hub_deg[lo],
+                        (c - S.hub_pre[lo]) * CHUNK, arcs);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) S.hub_n = 0;
 }
 
-// block-wide min / or helpers (result valid in all threads after return)
 __device__ __forceinline__ uint32_t warp_min(uint32_t x) {
 #pragma unroll
     for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(FULL, x, o));
     return x;
 }
 
-// Pass over a pending list (win or far) with in-place compaction.
-//   mode 0: drop entries with dist < drop_below (stale); report live / min of the rest
-//   mode 1: entries with dist < take_below move to `dst` (dst tag set to dst_tag);
-//           the rest stay; report live / min of the rest
-// Tags of removed entries are cleared so the vertex can be listed again.
+// Far list pass with in-place compaction. Entries whose bucket is below
+// `drop_below` are stale (listed in the window or expanded) and are dropped;
+// with `move` set, entries whose bucket is below S.win_base + nwin move to
+// the window lists; the minimum bucket of the remaining entries goes to
+// S.min_b. Tags of removed entries are cleared so the vertex can be listed
+// again.
 template <int TPB>
-__device__ void list_pass(Shared &S, const Slot &sl, uint32_t h, uint32_t *list, uint32_t *count,
-                          uint32_t *tag, int mode, uint64_t bound, uint32_t *dst,
-                          uint32_t *dst_count, uint32_t *dst_tagarr, uint32_t dst_tag,
-                          int *live_out, uint32_t *min_out) {
-    const uint32_t n_in = *count;
-    if (threadIdx.x == 0) S.out_n = 0;
+__device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t drop_below,
+                         bool move) {
+    const uint32_t n_in = S.far_n;
     __syncthreads();
-    bool live = false;
-    uint32_t mn = 0xFFFFFFFFu;
+    if (threadIdx.x == 0) {
+        S.out_n = 0;
+        S.min_b = NONE;
+    }
+    __syncthreads();
+    const uint32_t win_end = S.win_base + p.nwin;
+    uint32_t mn = NONE;
     for (uint32_t base = 0; base < n_in; base += TPB) {
         const uint32_t i = base + threadIdx.x;
-        bool keep = false, move = false;
+        bool keep = false;
         uint32_t u = 0;
         if (i < n_in) {
-            u = list[i];
-            const uint64_t k = __ldcg(&sl.key[u]);
-            const uint32_t d = key_dist(k);
-            if (d < bound) {
-                tag[u] = 0;
-                move = (mode == 1);
-                if (move && dst_tagarr) dst_tagarr[u] = dst_tag;
+            u = sl.far[i];
+            const uint32_t b = key_dist(__ldcg(&sl.key[u])) / p.delta;
+            if (b < drop_below) {
+                sl.ftag[u] = 0;
+            } else if (move && b < win_end) {
+                sl.ftag[u] = 0;
+                sub_append(S, sl, p.n, u, b);
             } else {
                 keep = true;
-                live |= is_live(k, u, h);
-                mn = min(mn, d);
+                mn = min(mn, b);
             }
         }
         __syncthreads();  // every entry of this chunk is read before any is rewritten
-        warp_append(keep, u, list, &S.out_n);
-        if (mode == 1) warp_append(move, u, dst, dst_count);
+        warp_append(keep, u, sl.far, &S.out_n);
     }
-    // the tag resets above are plain stores, while tags are later updated by
+    // tag resets above are plain stores, while tags are later updated by
     // atomics performed in L2: publish them device-wide before the barrier
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) *count = S.out_n;
     mn = warp_min(mn);
-    if ((threadIdx.x & 31) == 0) atomicMin(min_out, mn);
-    live = __syncthreads_or(live);
-    if (threadIdx.x == 0 && live) *live_out = 1;
+    if ((threadIdx.x & 31) == 0) atomicMin(&S.min_b, mn);
+    __syncthreads();
+    if (threadIdx.x == 0) S.far_n = S.out_n;
+    __syncthreads();
+}
+
+// live vertices among the window list of bucket b (entries whose key is in b)
+template <int TPB>
+__device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t h,
+                                     uint32_t slot, uint32_t b) {
+    __syncthreads();
+    if (threadIdx.x == 0) S.live_sum = 0;
+    __syncthreads();
+    const uint32_t *lst = sl.sub + size_t(slot) * p.n;
+    const uint32_t cnt = S.sub_n[slot];
+    int c = 0;
+    for (uint32_t i = threadIdx.x; i < cnt; i += TPB) {
+        const uint32_t u = lst[i];
+        const uint64_t k = __ldcg(&sl.key[u]);
+        c += (key_dist(k) / p.delta == b && is_live(k, u, h));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&S.live_sum, c);
     __syncthreads();
 }
 
 template <int TPB>
-__global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
+__global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch p) {
     __shared__ Shared S;
     const uint32_t n = p.n;
     const size_t so = size_t(blockIdx.x) * n;
@@ -288,23 +405,24 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
     sl.rtag = p.rtag + so;
     sl.wtag = p.wtag + so;
     sl.ftag = p.ftag + so;
-    uint32_t *lb = p.lists + so * 5;
+    uint32_t *lb = p.lists + so * (4 + p.nwin);
     sl.l0 = lb;
     sl.l1 = lb + n;
-    sl.win = lb + 2 * size_t(n);
-    sl.far = lb + 3 * size_t(n);
-    sl.touch = lb + 4 * size_t(n);
+    sl.far = lb + 2 * size_t(n);
+    sl.touch = lb + 3 * size_t(n);
+    sl.sub = lb + 4 * size_t(n);
 
     unsigned long long expanded = 0, arcs = 0, trivial = 0, trees = 0;
     if (threadIdx.x == 0) {
+        S.hub_n = 0;
         S.rid = p.slot_ctr[blockIdx.x * 4 + 0];
-        S.wid = p.slot_ctr[blockIdx.x * 4 + 1];
+        S.bid_base = p.slot_ctr[blockIdx.x * 4 + 1];
         S.fid = p.slot_ctr[blockIdx.x * 4 + 2];
     }
 
     for (;;) {
         if (threadIdx.x == 0) {
-            uint32_t r = 0xFFFFFFFFu;
+            uint32_t r = NONE;
             if (!p.flags[1] && !p.flags[0]) {
                 const uint32_t i = atomicAdd(p.next_root, 1u);
                 if (i < p.root_count) r = p.root_list ? p.root_list[i] : p.root_begin + i;
@@ -313,7 +431,7 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
         }
         __syncthreads();
         const uint32_t h = S.root;
-        if (h == 0xFFFFFFFFu) break;
+        if (h == NONE) break;
         ++trees;
 
         // trivial tree: every neighbour outranks the root, so after the root is
@@ -337,19 +455,23 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
             nlab = 1;
         } else {
             // ---- tree search
+            for (uint32_t s = threadIdx.x; s < p.nwin; s += TPB) S.sub_n[s] = 0;
             if (threadIdx.x == 0) {
                 S.cur_n = 1;
                 S.nxt_n = 0;
-                S.win_n = 0;
                 S.far_n = 0;
                 S.touch_n = 1;
                 S.sel = 0;
+                S.cur_slot = NONE;
                 S.rid += 1;
-                S.wid += 1;
                 S.fid += 1;
+                S.bcur = 0;
+                S.win_base = 0;
+                S.bid_top = p.nwin;
+                S.cnt = 0;
+                S.t_lo = 0;
                 S.t_hi = p.delta;
                 S.w_hi = uint64_t(p.delta) * p.nwin;
-                S.far_live = 0;
                 S.abort = 0;
                 sl.l0[0] = h;
                 sl.touch[0] = h;
@@ -368,7 +490,8 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
                 if (S.nxt_n) {  // the current bucket is not settled yet
                     __syncthreads();
                     if (threadIdx.x == 0) {
-                        S.sel ^= 1u;
+                        S.sel ^= 1u;  // the next round reads the list this round appended to
+                        S.cur_slot = NONE;
                         S.cur_n = S.nxt_n;
                         S.nxt_n = 0;
                         S.rid += 1;
@@ -376,56 +499,50 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
                     __syncthreads();
                     continue;
                 }
-                // bucket settled: all keys below t_hi are final.
-                // 1) pending vertices of the window: drop stale ones, find live / min
-                if (threadIdx.x == 0) { S.live = 0; S.min_d = 0xFFFFFFFFu; }
+                // bucket settled: every key below t_hi is final
                 __syncthreads();
-                list_pass<TPB>(S, sl, h, sl.win, &S.win_n, sl.wtag, 0, S.t_hi, nullptr, nullptr,
-                               nullptr, 0, &S.live, &S.min_d);
-                // 2) beyond the window: scanned only if a live key was ever sent there
-                if (!S.live && S.far_live) {
-                    if (threadIdx.x == 0) { S.tmp_live = 0; S.tmp_min = 0xFFFFFFFFu; }
-                    __syncthreads();
-                    list_pass<TPB>(S, sl, h, sl.far, &S.far_n, sl.ftag, 0, S.w_hi, nullptr,
-                                   nullptr, nullptr, 0, &S.tmp_live, &S.tmp_min);
-                    if (threadIdx.x == 0) { S.far_live = S.tmp_live; S.live = S.tmp_live; }
-                    __syncthreads();
+                if (threadIdx.x == 0) {
+                    if (S.bcur >= S.win_base) S.sub_n[S.bcur - S.win_base] = 0;  // consumed
+                    S.cur_slot = NONE;
+                    S.min_b = NONE;
                 }
-                if (!S.live) break;  // no pending vertex can still receive the root as hub
-                // 3) the window is empty: open the next window at the nearest far entry
-                if (S.win_n == 0) {
-                    if (threadIdx.x == 0) { S.tmp_live = 0; S.tmp_min = 0xFFFFFFFFu; }
-                    __syncthreads();
-                    list_pass<TPB>(S, sl, h, sl.far, &S.far_n, sl.ftag, 0, S.w_hi, nullptr,
-                                   nullptr, nullptr, 0, &S.tmp_live, &S.tmp_min);
-                    if (S.far_n == 0) break;
+                __syncthreads();
+                if (S.cnt == 0) break;  // no pending vertex can still receive the root as hub
+                // next non-empty bucket of the window
+                if (threadIdx.x == 0) {
+                    const uint32_t s0 = S.bcur >= S.win_base ? S.bcur - S.win_base + 1 : 0;
+                    for (uint32_t s = s0; s < p.nwin; ++s)
+                        if (S.sub_n[s]) { S.min_b = S.win_base + s; break; }
+                }
+                __syncthreads();
+                if (S.min_b == NONE) {
+                    // window used up: restart it at the nearest far bucket
+                    far_pass<TPB>(p, S, sl, S.win_base + p.nwin, false);
+                    if (S.far_n == 0) break;  // nothing pending at all
                     if (threadIdx.x == 0) {
-                        S.min_d = S.tmp_min;
-                        const uint64_t wlo = (uint64_t(S.min_d) / p.delta) * p.delta;
-                        S.w_hi = wlo + uint64_t(p.delta) * p.nwin;
-                        S.wid += 1;
-                        S.tmp_live = 0;
-                        S.tmp_min = 0xFFFFFFFFu;
+                        S.win_base = S.min_b;
+                        S.w_hi = uint64_t(S.win_base + p.nwin) * p.delta;
+                        if (S.win_base + p.nwin > S.bid_top) S.bid_top = S.win_base + p.nwin;
+                        for (uint32_t s = 0; s < p.nwin; ++s) S.sub_n[s] = 0;
                     }
                     __syncthreads();
-                    list_pass<TPB>(S, sl, h, sl.far, &S.far_n, sl.ftag, 1, S.w_hi, sl.win,
-                                   &S.win_n, sl.wtag, S.wid, &S.tmp_live, &S.tmp_min);
-                    if (threadIdx.x == 0) S.far_live = S.tmp_live;  // live among what stays far
+                    far_pass<TPB>(p, S, sl, 0, true);
+                    if (threadIdx.x == 0) S.min_b = S.win_base;
                     __syncthreads();
                 }
-                // 4) the next non-empty bucket becomes current: move its entries to cur
+                // enter bucket min_b: its live vertices stop counting as pending
+                const uint32_t nb = S.min_b, slot = nb - S.win_base;
+                count_live_in_bucket<TPB>(p, S, sl, h, slot, nb);
                 if (threadIdx.x == 0) {
-                    const uint64_t tlo = (uint64_t(S.min_d) / p.delta) * p.delta;
-                    S.t_hi = tlo + p.delta;
+                    S.cnt -= S.live_sum;
+                    S.bcur = nb;
+                    S.t_lo = uint64_t(nb) * p.delta;
+                    S.t_hi = S.t_lo + p.delta;
+                    S.cur_slot = slot;
+                    S.cur_n = S.sub_n[slot];
                     S.rid += 1;
-                    S.cur_n = 0;
-                    S.tmp_live = 0;
-                    S.tmp_min = 0xFFFFFFFFu;
                 }
                 __syncthreads();
-                list_pass<TPB>(S, sl, h, sl.win, &S.win_n, sl.wtag, 1, S.t_hi,
-                               S.sel ? sl.l1 : sl.l0, &S.cur_n, nullptr, 0, &S.tmp_live,
-                               &S.tmp_min);
             }
             __syncthreads();
             if (S.abort) {
@@ -436,7 +553,10 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
                 break;
             }
             // ---- label emission: live touched vertices, staged in l0 (vertex) / l1 (dist)
-            if (threadIdx.x == 0) S.out_n = 0;
+            if (threadIdx.x == 0) {
+                S.out_n = 0;
+                S.bid_base += S.bid_top + 2;  // fresh window tags for the next tree
+            }
             __syncthreads();
             const uint32_t nt = S.touch_n;
             for (uint32_t base = 0; base < nt; base += TPB) {
@@ -514,7 +634,7 @@ __global__ void __launch_bounds__(TPB) plant_trees_kernel(TreeLaunch p) {
         atomicAdd(&p.stats[2], trivial);
         atomicAdd(&p.stats[3], trees);
         p.slot_ctr[blockIdx.x * 4 + 0] = S.rid;
-        p.slot_ctr[blockIdx.x * 4 + 1] = S.wid;
+        p.slot_ctr[blockIdx.x * 4 + 1] = S.bid_base;
         p.slot_ctr[blockIdx.x * 4 + 2] = S.fid;
     }
 }
@@ -535,6 +655,7 @@ int occ() {
 }  // namespace
 
 cudaError_t launch_plant_trees(const TreeLaunch &p, int tpt, int slots, cudaStream_t s) {
+    if (p.nwin < 2 || p.nwin > NWIN_MAX) return cudaErrorInvalidValue;
     switch (tpt) {
         case 32: return launch_t<32>(p, slots, s);
         case 64: return launch_t<64>(p, slots, s);
