@@ -205,6 +205,28 @@ chl_status chl_labels_copy(const chl_labels *L, uint64_t *offsets, uint32_t *hub
 chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t *out,
                      chl_mem mem, void *stream);
 
+/*
+ * chl_query_noalloc — the same queries as chl_query, without allocating any
+ * memory. The paper has no counterpart: this entry point exists for callers
+ * that must not allocate device memory on the query path, such as a serving
+ * thread running inside a memory budget owned by another runtime, or one that
+ * cannot take the allocator's synchronisation.
+ *   L, pairs, q, out, mem, stream   as for chl_query
+ * Scratch: one fixed device array inside the library (about 12 MiB, held on
+ * every GPU that loads the library until the process exits) stages the pairs
+ * and answers of host-memory calls and holds the bad-vertex flag.
+ * Limits and rules:
+ *   - q <= 1048576 (2^20) pairs per call; larger q returns CHL_EINVAL.
+ *   - The first call on a device resolves the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call uses the same array: calls whose work overlaps on the GPU
+ *     (other streams, other host threads) race and must be serialised by the
+ *     caller.
+ * Errors: as chl_query.
+ */
+chl_status chl_query_noalloc(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t *out,
+                             chl_mem mem, void *stream);
+
 /* Release the labels object (NULL is allowed). Synchronises its stream. */
 void chl_labels_free(chl_labels *L);
 

@@ -27,6 +27,7 @@ __all__ = [
     "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "ChlError", "chl_csr", "chl_build_opts",
     "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
     "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
+    "chl_query_noalloc",
     "Labels", "build_labels", "query",
 ]
 
@@ -127,6 +128,8 @@ def lib():
             L.chl_labels_copy.restype = i32
             L.chl_query.argtypes = [vp, vp, u64, vp, i32, vp]
             L.chl_query.restype = i32
+            L.chl_query_noalloc.argtypes = [vp, vp, u64, vp, i32, vp]
+            L.chl_query_noalloc.restype = i32
             L.chl_labels_free.argtypes = [vp]
             L.chl_labels_free.restype = None
             L.chl_last_error.argtypes = []
@@ -180,6 +183,12 @@ def chl_labels_copy(handle: int, offsets: int, hub: int, dist: int, mem: int, st
 
 def chl_query(handle: int, pairs: int, q: int, out: int, mem: int, stream: int):
     _check(lib().chl_query(handle, pairs, q, out, mem, stream))
+
+
+def chl_query_noalloc(handle: int, pairs: int, q: int, out: int, mem: int, stream: int):
+    """chl_query without any allocation: at most 2^20 pairs per call, staged
+    in one fixed device array that all calls share (see include/chl.h)."""
+    _check(lib().chl_query_noalloc(handle, pairs, q, out, mem, stream))
 
 
 def chl_labels_free(handle: int):

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -480,4 +481,79 @@ extern "C" void chl_labels_free(chl_labels *L) {
     cudaFree(L->hubpos);
     cudaFree(L->dist);
     delete L;
+}
+
+// ------------------------------------------------------------------ queries without allocation
+// chl_query_noalloc serves callers that must not allocate device memory at
+// query time: a request path running inside a memory budget that another
+// runtime owns, or a latency-critical thread that cannot afford the
+// allocator's synchronisation. It runs the same query kernel as chl_query
+// but stages pairs, answers and the bad-vertex flag in one fixed device
+// array of this file instead of memory allocated per call.
+namespace {
+
+constexpr uint64_t NOALLOC_MAX_PAIRS = uint64_t(1) << 20;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+struct NoAllocScratch {
+    uint32_t pairs[2 * NOALLOC_MAX_PAIRS];
+    uint32_t out[NOALLOC_MAX_PAIRS];
+    int bad;
+};
+
+// Host code must not use this name as a device address: it is a host-side
+// stand-in. Its device address is resolved per device with
+// cudaGetSymbolAddress below. Every GPU that loads the library holds it
+// (about 12 MiB) until the process exits.
+static __device__ __align__(256) NoAllocScratch g_noalloc_scratch;
+
+std::mutex g_noalloc_mu;
+NoAllocScratch *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+}  // namespace
+
+extern "C" chl_status chl_query_noalloc(const chl_labels *L, const uint32_t *pairs, uint64_t q,
+                                        uint32_t *out, chl_mem mem, void *stream) {
+    g_err[0] = 0;
+    if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    if (q == 0) return CHL_OK;
+    if (!pairs || !out) return set_error(CHL_EINVAL, "pairs or out is NULL");
+    if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
+    if (q > NOALLOC_MAX_PAIRS)
+        return set_error(CHL_EINVAL, "chl_query_noalloc takes at most %llu pairs per call, got %llu",
+                         (unsigned long long)NOALLOC_MAX_PAIRS, (unsigned long long)q);
+    cudaStream_t s = (cudaStream_t)stream;
+    chl_status st = CHL_OK;
+    int dev = 0, hbad = 0;
+    NoAllocScratch *sc = nullptr;
+    const uint32_t *dp = pairs;
+    uint32_t *dout = out;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        st = set_error(CHL_EINVAL, "device %d outside the %d devices supported", dev, NOALLOC_MAX_DEVICES);
+        goto done;
+    }
+    {
+        // first call on a device: resolve the scratch array's device address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *a = nullptr;
+            CUDA_TRY(cudaGetSymbolAddress(&a, g_noalloc_scratch));
+            g_noalloc_addr[dev] = (NoAllocScratch *)a;
+        }
+        sc = g_noalloc_addr[dev];
+    }
+    CUDA_TRY(cudaMemsetAsync(&sc->bad, 0, sizeof(int), s));
+    if (mem == CHL_MEM_HOST) {
+        CUDA_TRY(cudaMemcpyAsync(sc->pairs, pairs, q * 8, cudaMemcpyHostToDevice, s));
+        dp = sc->pairs;
+        dout = sc->out;
+    }
+    CUDA_TRY(launch_query(L->n, L->offsets, L->hubpos, L->dist, dp, q, dout, &sc->bad, s));
+    if (mem == CHL_MEM_HOST) CUDA_TRY(cudaMemcpyAsync(out, sc->out, q * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&hbad, &sc->bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) st = set_error(CHL_EINVAL, "a query vertex id is >= n");
+done:
+    return st;
 }
