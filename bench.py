@@ -181,6 +181,12 @@ def main():
     ap.add_argument("--queries", type=int, default=1_000_000)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/cpu/e2e legs")
+    ap.add_argument("--case", default=None,
+                    help="profiling case: one build of the roots at rank positions [b, b+count), "
+                         "given as b:count; prints its counters and exits")
+    ap.add_argument("--opts", default=None,
+                    help="build options k=v,... (e.g. threads_per_tree=256,bucket_delta=1); "
+                         "skips the tuner")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -224,8 +230,25 @@ def main():
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream(dev)
 
+    # search parameters measured once for this graph (chl_tune), outside the timed region
+    if args.opts:
+        opts = {k: int(v) for k, v in (kv.split("=") for kv in args.opts.split(","))}
+        tune_rep = {"trials": 0, "sample_roots": 0}
+    else:
+        opts, tune_rep = chl.tune(DG, R)
+    if args.case:
+        b, c = (int(x) for x in args.case.split(":"))
+        torch.cuda.synchronize(dev)
+        L = chl.build_labels(DG, R, root_begin=b, root_end=min(g.n, b + c), **opts)
+        st = L.stats()
+        L.free()
+        print(json.dumps({"case": name, "roots": [b, min(g.n, b + c)], "opts": opts,
+                          **{k: st[k] for k in ("tree_ms", "build_ms", "expanded", "arcs",
+                                                "labels", "trees")}}), flush=True)
+        return
+
     def step():
-        L = chl.build_labels(DG, R)
+        L = chl.build_labels(DG, R, **opts)
         L.query(P, out=out)
         return L
 
@@ -278,7 +301,8 @@ def main():
         "config": {"workload": name, "description": WORKLOAD_TEXT.get(name, name), "n": g.n,
                    "arcs": g.num_arcs, "queries_per_step": args.queries,
                    "l2": "256 MiB buffer written between timed steps; per-step state > L2",
-                   "replicas": world},
+                   "replicas": world, "tuned": opts,
+                   "tune": {"trials": tune_rep["trials"], "sample_roots": tune_rep["sample_roots"]}},
         "build_s": float(np.mean(build_ms)) / 1000.0,
         "tree_kernel_ms": float(np.mean(tree_ms)),
         "labels": int(T), "als": T / g.n,
@@ -290,7 +314,7 @@ def main():
     }
 
     # ---- queries: batch throughput and single-query launch latency
-    L = chl.build_labels(DG, R)
+    L = chl.build_labels(DG, R, **opts)
     qt = []
     for _ in range(5):
         ev0.record(stream)
@@ -359,7 +383,7 @@ def main():
         for i in range(args.steps):
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
-            Lh = chl.build_labels(HG, rank_h)
+            Lh = chl.build_labels(HG, rank_h, **opts)
             off, hub, dist_ = Lh.to_numpy()
             Lh.query(pairs_p, out=out_h)
             torch.cuda.synchronize(dev)

@@ -166,6 +166,32 @@ typedef struct {
 chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opts *opts,
                      void *stream, chl_labels **out);
 
+/*
+ * chl_tune — pick the search parameters of chl_build for a graph by
+ * measurement (the paper has no counterpart; its parameters α, β and Ψ_th
+ * belong to other algorithms). The tree kernel runs on a rank-strided sample
+ * of about four roots per tree slot (every (n/K)-th rank position, so the
+ * sample has the build's mix of large and small trees) for candidate bucket
+ * widths, then block sizes, then window sizes (coordinate search), and the
+ * fastest is kept.
+ *   g, rank, stream   as for chl_build
+ *   base              fields set (non-zero) are kept fixed; NULL = tune all
+ *   best              receives base with threads_per_tree, bucket_delta and
+ *                     window_buckets filled in; pass it to chl_build
+ *   report            optional: trials run, sample size, best trial time
+ * Errors: as chl_build.
+ */
+typedef struct {
+    int32_t trials;
+    uint32_t sample_roots;
+    double best_tree_ms;
+    uint64_t best_expanded;
+    uint64_t best_arcs;
+} chl_tune_report;
+
+chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl_build_opts *base,
+                    void *stream, chl_build_opts *best, chl_tune_report *report);
+
 /* n, total number of labels, and device bytes held by the object. */
 chl_status chl_labels_info(const chl_labels *L, uint32_t *n, uint64_t *total, uint64_t *bytes);
 

@@ -27,7 +27,7 @@ __all__ = [
     "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "ChlError", "chl_csr", "chl_build_opts",
     "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
     "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
-    "chl_query_noalloc",
+    "chl_query_noalloc", "chl_tune", "chl_tune_report", "tune",
     "Labels", "build_labels", "query",
 ]
 
@@ -93,6 +93,14 @@ class chl_build_opts(C.Structure):
                 ("flags", C.c_int32), ("label_capacity", C.c_uint64)]
 
 
+class chl_tune_report(C.Structure):
+    _fields_ = [("trials", C.c_int32), ("sample_roots", C.c_uint32), ("best_tree_ms", C.c_double),
+                ("best_expanded", C.c_uint64), ("best_arcs", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class chl_build_stats(C.Structure):
     _fields_ = [("trees", C.c_uint64), ("labels", C.c_uint64), ("expanded", C.c_uint64),
                 ("arcs", C.c_uint64), ("trivial", C.c_uint64), ("build_ms", C.c_double),
@@ -118,6 +126,9 @@ def lib():
             L.chl_build.argtypes = [C.POINTER(chl_csr), vp, C.POINTER(chl_build_opts), vp,
                                     C.POINTER(vp)]
             L.chl_build.restype = i32
+            L.chl_tune.argtypes = [C.POINTER(chl_csr), vp, C.POINTER(chl_build_opts), vp,
+                                   C.POINTER(chl_build_opts), C.POINTER(chl_tune_report)]
+            L.chl_tune.restype = i32
             L.chl_labels_info.argtypes = [vp, C.POINTER(u32), C.POINTER(u64), C.POINTER(u64)]
             L.chl_labels_info.restype = i32
             L.chl_labels_stats.argtypes = [vp, C.POINTER(chl_build_stats)]
@@ -157,6 +168,13 @@ def chl_build(g: chl_csr, rank_ptr: int, opts: chl_build_opts | None, stream: in
     _check(lib().chl_build(C.byref(g), rank_ptr, C.byref(opts) if opts is not None else None,
                            stream, C.byref(out)))
     return out.value
+
+
+def chl_tune(g: chl_csr, rank_ptr: int, base: chl_build_opts | None, stream: int):
+    best, rep = chl_build_opts(), chl_tune_report()
+    _check(lib().chl_tune(C.byref(g), rank_ptr, C.byref(base) if base is not None else None,
+                          stream, C.byref(best), C.byref(rep)))
+    return best, rep
 
 
 def chl_labels_info(handle: int):
@@ -289,11 +307,7 @@ class Labels:
         return out
 
 
-def build_labels(g, rank, stream: int | None = None, **opts) -> Labels:
-    """Canonical hub labels of graph g (object with n, row_ptr, col, w; numpy
-    arrays or CUDA tensors) under rank R (permutation, larger = more important).
-    opts: fields of chl_build_opts (root_begin, root_end, threads_per_tree,
-    bucket_delta, window_buckets, slots, mode)."""
+def _csr_args(g, rank):
     rp, mem, k1 = _ptr_mem(g.row_ptr, np.uint64)
     cp, mem2, k2 = _ptr_mem(g.col, np.uint32)
     wp, mem3, k3 = _ptr_mem(g.w, np.uint32)
@@ -302,6 +316,28 @@ def build_labels(g, rank, stream: int | None = None, **opts) -> Labels:
         raise ValueError("graph arrays and rank must all be host arrays or all CUDA tensors")
     narcs = (k2.numel() if _is_torch(k2) else k2.size)
     csr = chl_csr(int(g.n), int(narcs), rp, cp if narcs else None, wp if narcs else None, mem)
+    return csr, rkp, (k1, k2, k3, k4)
+
+
+def tune(g, rank, stream: int | None = None, **fixed):
+    """Measured choice of threads_per_tree, bucket_delta and window_buckets
+    for this graph (chl_tune). Returns (build options for build_labels,
+    tuning report)."""
+    csr, rkp, keep = _csr_args(g, rank)
+    base = chl_build_opts()
+    for k, v in fixed.items():
+        setattr(base, k, int(v))
+    best, rep = chl_tune(csr, rkp, base, _current_stream() if stream is None else stream)
+    out = {k: getattr(best, k) for k in ("threads_per_tree", "bucket_delta", "window_buckets")}
+    return out, rep.as_dict()
+
+
+def build_labels(g, rank, stream: int | None = None, **opts) -> Labels:
+    """Canonical hub labels of graph g (object with n, row_ptr, col, w; numpy
+    arrays or CUDA tensors) under rank R (permutation, larger = more important).
+    opts: fields of chl_build_opts (root_begin, root_end, threads_per_tree,
+    bucket_delta, window_buckets, slots, mode)."""
+    csr, rkp, keep = _csr_args(g, rank)
     o = chl_build_opts()
     for k, v in opts.items():
         setattr(o, k, int(v))

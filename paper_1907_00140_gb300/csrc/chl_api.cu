@@ -1,6 +1,7 @@
 // C ABI of libchl.so (declared in include/chl.h): argument checks, device
 // memory, the build driver (graph preparation, persistent tree launch with
 // retry on a full label buffer, label assembly) and the query entry point.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -56,16 +57,20 @@ struct Params {
     int slots;
 };
 
-// Defaults of the search parameters from graph statistics. Bucket width:
-// about a sixteenth of the mean weight keeps buckets narrow enough that early
-// termination overshoots little (the test runs at bucket granularity) while a
-// bucket still holds many vertices of a large tree.
+// Untuned defaults of the search parameters from graph statistics (chl_tune
+// measures instead). Bucket width: low-diameter graphs with many vertices per
+// unit of distance (mean degree >= 8, the scale-free families) need narrow
+// buckets, since early termination is decided at bucket granularity; sparse
+// high-diameter graphs (road-like) want wide buckets, so that a tree needs few
+// bucket rounds.
 Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_t free_bytes) {
     Params p;
-    p.tpt = o.threads_per_tree ? o.threads_per_tree : 128;
-    uint32_t d = o.bucket_delta > 0 ? uint32_t(o.bucket_delta) : uint32_t(g.w_mean / 16.0);
+    p.tpt = o.threads_per_tree ? o.threads_per_tree : 256;
+    const double mean_deg = g.n ? double(g.m2) / double(g.n) : 0.0;
+    const double dflt = mean_deg >= 8.0 ? g.w_mean / 128.0 : 2.0 * g.w_mean;
+    uint32_t d = o.bucket_delta > 0 ? uint32_t(o.bucket_delta) : uint32_t(dflt);
     p.delta = d < 1 ? 1 : d;
-    p.nwin = o.window_buckets > 0 ? uint32_t(o.window_buckets) : 16;
+    p.nwin = o.window_buckets > 0 ? uint32_t(o.window_buckets) : 32;
     int per_sm = plant_max_slots_per_sm(p.tpt);
     if (per_sm < 1) per_sm = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
@@ -555,5 +560,232 @@ extern "C" chl_status chl_query_noalloc(const chl_labels *L, const uint32_t *pai
     CUDA_TRY(cudaStreamSynchronize(s));
     if (hbad) st = set_error(CHL_EINVAL, "a query vertex id is >= n");
 done:
+    return st;
+}
+
+// ------------------------------------------------------------------ autotuner
+namespace {
+
+// One trial: the tree kernel alone on a root list, with fresh slot state;
+// returns its device time (ms) or a negative value when the labels did not
+// fit the trial buffer.
+chl_status tree_trial(const RankGraph &rg, const Params &P, const uint32_t *roots, uint32_t count,
+                      uint64_t cap, cudaStream_t s, float *ms, unsigned long long *stats4) {
+    chl_status st = CHL_OK;
+    const uint32_t n = rg.n;
+    DevBuf b_key, b_tags, b_lists, b_ctr, b_ctl, b_ov, b_oh, b_od, b_fail;
+    b_key.s = b_tags.s = b_lists.s = b_ctr.s = b_ctl.s = b_ov.s = b_oh.s = b_od.s = b_fail.s = s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    Control hc{};
+    Control *ctl = nullptr;
+    TreeLaunch tl{};
+    *ms = -1.0f;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    CUDA_TRY(cudaMallocAsync(&b_key.p, size_t(P.slots) * n * 8, s));
+    CUDA_TRY(cudaMemsetAsync(b_key.p, 0xFF, size_t(P.slots) * n * 8, s));
+    CUDA_TRY(cudaMallocAsync(&b_tags.p, size_t(P.slots) * n * 12, s));
+    CUDA_TRY(cudaMemsetAsync(b_tags.p, 0, size_t(P.slots) * n * 12, s));
+    CUDA_TRY(cudaMallocAsync(&b_lists.p, size_t(P.slots) * n * 4 * (4 + P.nwin), s));
+    CUDA_TRY(cudaMallocAsync(&b_ctr.p, size_t(P.slots) * 16, s));
+    CUDA_TRY(cudaMemsetAsync(b_ctr.p, 0, size_t(P.slots) * 16, s));
+    CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
+    CUDA_TRY(cudaMemsetAsync(b_ctl.p, 0, sizeof(Control), s));
+    CUDA_TRY(cudaMallocAsync(&b_fail.p, size_t(count + 1) * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_ov.p, cap * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_oh.p, cap * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
+    ctl = (Control *)b_ctl.p;
+    tl.n = n;
+    tl.row = rg.row;
+    tl.arc = rg.arc;
+    tl.vert_at = rg.vert_at;
+    tl.root_list = roots;
+    tl.root_begin = 0;
+    tl.root_count = count;
+    tl.delta = P.delta;
+    tl.nwin = P.nwin;
+    tl.key = (uint64_t *)b_key.p;
+    tl.rtag = (uint32_t *)b_tags.p;
+    tl.wtag = tl.rtag + size_t(P.slots) * n;
+    tl.ftag = tl.wtag + size_t(P.slots) * n;
+    tl.lists = (uint32_t *)b_lists.p;
+    tl.slot_ctr = (uint32_t *)b_ctr.p;
+    tl.out_v = (uint32_t *)b_ov.p;
+    tl.out_h = (uint32_t *)b_oh.p;
+    tl.out_d = (uint32_t *)b_od.p;
+    tl.out_cap = cap;
+    tl.out_count = &ctl->out_count;
+    tl.next_root = &ctl->next_root;
+    tl.failed = (uint32_t *)b_fail.p;
+    tl.failed_count = &ctl->failed_count;
+    tl.flags = ctl->flags;
+    tl.stats = ctl->stats;
+    CUDA_TRY(cudaEventRecord(e0, s));
+    CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
+    CUDA_TRY(cudaEventRecord(e1, s));
+    CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hc.flags[0]) {
+        st = set_error(hc.flags[0] == ERR_DIST_OVERFLOW ? CHL_EOVERFLOW : CHL_ETIMEOUT,
+                       "tuning trial failed (code %d)", hc.flags[0]);
+        goto done;
+    }
+    if (!hc.flags[1]) CUDA_TRY(cudaEventElapsedTime(ms, e0, e1));
+    for (int k = 0; k < 4; ++k) stats4[k] = hc.stats[k];
+done:
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace
+
+extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl_build_opts *base,
+                               void *stream, chl_build_opts *best, chl_tune_report *report) {
+    g_err[0] = 0;
+    if (!g || !rank || !best) return set_error(CHL_EINVAL, "graph, rank or best is NULL");
+    if (g->n == 0) return set_error(CHL_EINVAL, "graph has no vertices");
+    if (g->n >= 0x7FFFFFFFu) return set_error(CHL_EINVAL, "n must be < 2^31");
+    if (!g->row_ptr || (g->num_arcs && (!g->col || !g->w)))
+        return set_error(CHL_EINVAL, "graph arrays are NULL");
+    if (g->mem != CHL_MEM_DEVICE && g->mem != CHL_MEM_HOST)
+        return set_error(CHL_EINVAL, "unknown memory kind");
+    chl_build_opts o{};
+    if (base) o = *base;
+    if (o.mode != 0) return set_error(CHL_EINVAL, "chl_tune tunes the batched mode (mode 0)");
+    cudaStream_t s = (cudaStream_t)stream;
+    chl_status st = CHL_OK;
+    const uint32_t n = g->n;
+    const uint64_t m2 = g->num_arcs;
+    const uint64_t *d_row = g->row_ptr;
+    const uint32_t *d_col = g->col, *d_w = g->w, *d_rank = rank;
+    DevBuf b_row, b_col, b_w, b_rank, b_roots;
+    b_row.s = b_col.s = b_w.s = b_rank.s = b_roots.s = s;
+    RankGraph rg;
+    int launches = 0, dev = 0, sms = 0, trials = 0;
+    size_t free_b = 0, total_b = 0;
+    std::vector<uint32_t> roots;
+    uint32_t K = 0;
+    uint64_t cap = 0;
+    Params bestP{};
+    float best_ms = -1.0f;
+    unsigned long long best_stats[4] = {0, 0, 0, 0};
+    CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (g->mem == CHL_MEM_HOST) {
+        CUDA_TRY(cudaMallocAsync(&b_row.p, (size_t(n) + 1) * 8, s));
+        CUDA_TRY(cudaMallocAsync(&b_col.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(cudaMallocAsync(&b_w.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(cudaMallocAsync(&b_rank.p, size_t(n) * 4, s));
+        CUDA_TRY(cudaMemcpyAsync(b_row.p, g->row_ptr, (size_t(n) + 1) * 8, cudaMemcpyHostToDevice, s));
+        if (m2) {
+            CUDA_TRY(cudaMemcpyAsync(b_col.p, g->col, m2 * 4, cudaMemcpyHostToDevice, s));
+            CUDA_TRY(cudaMemcpyAsync(b_w.p, g->w, m2 * 4, cudaMemcpyHostToDevice, s));
+        }
+        CUDA_TRY(cudaMemcpyAsync(b_rank.p, rank, size_t(n) * 4, cudaMemcpyHostToDevice, s));
+        d_row = (const uint64_t *)b_row.p;
+        d_col = (const uint32_t *)b_col.p;
+        d_w = (const uint32_t *)b_w.p;
+        d_rank = (const uint32_t *)b_rank.p;
+    }
+    st = prepare_graph(n, m2, d_row, d_col, d_w, d_rank, rg, s, &launches);
+    if (st != CHL_OK) goto done;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    {
+        // rank-strided sample: every (n/K)-th rank position, about four trees per slot
+        const Params p0 = choose_params(rg, o, sms, free_b);
+        K = uint32_t(4 * (uint64_t)p0.slots);
+        if (K > n) K = n;
+        if (K < 1) K = 1;
+        roots.resize(K);
+        for (uint32_t i = 0; i < K; ++i) roots[i] = uint32_t((uint64_t(i) * n) / K);
+        CUDA_TRY(cudaMallocAsync(&b_roots.p, size_t(K) * 4, s));
+        CUDA_TRY(cudaMemcpyAsync(b_roots.p, roots.data(), size_t(K) * 4, cudaMemcpyHostToDevice, s));
+        cap = uint64_t(K) * 256 + 4 * uint64_t(n);
+        const uint64_t fit = uint64_t(0.15 * double(free_b)) / 12;
+        if (cap > fit) cap = fit;
+    }
+    {
+        // coordinate search: bucket width, then threads per tree, then window
+        const double wm = rg.w_mean > 1.0 ? rg.w_mean : 1.0;
+        std::vector<uint32_t> deltas;
+        if (o.bucket_delta > 0) {
+            deltas.push_back(uint32_t(o.bucket_delta));
+        } else {
+            const double f[] = {0.0, 1.0 / 64, 1.0 / 16, 1.0 / 4, 1.0, 2.0};
+            for (double x : f) {
+                uint32_t d = uint32_t(wm * x);
+                if (d < 1) d = 1;
+                bool seen = false;
+                for (uint32_t e : deltas) seen |= (e == d);
+                if (!seen) deltas.push_back(d);
+            }
+        }
+        std::vector<int> tpts;
+        if (o.threads_per_tree) tpts.push_back(o.threads_per_tree);
+        else tpts = {256, 128, 512};
+        std::vector<int> wins;
+        if (o.window_buckets) wins.push_back(o.window_buckets);
+        else wins = {32, 16, 64};
+        auto run = [&](uint32_t d, int t, int w, Params *outP, float *outms,
+                       unsigned long long *st4) -> chl_status {
+            chl_build_opts q = o;
+            q.bucket_delta = int32_t(d);
+            q.threads_per_tree = t;
+            q.window_buckets = w;
+            size_t fb = 0, tb = 0;
+            cudaMemGetInfo(&fb, &tb);
+            Params P = choose_params(rg, q, sms, fb);
+            float ms = -1.0f;
+            uint64_t c = cap;
+            chl_status r = CHL_OK;
+            for (int a = 0; a < 4; ++a) {
+                r = tree_trial(rg, P, (const uint32_t *)b_roots.p, K, c, s, &ms, st4);
+                if (r != CHL_OK || ms >= 0) break;
+                c *= 4;  // labels did not fit: a larger trial buffer
+            }
+            ++trials;
+            *outP = P;
+            *outms = ms;
+            return r;
+        };
+        Params P;
+        float ms;
+        unsigned long long st4[4];
+        for (uint32_t d : deltas) {
+            st = run(d, tpts[0], wins[0], &P, &ms, st4);
+            if (st != CHL_OK) goto done;
+            if (ms >= 0 && (best_ms < 0 || ms < best_ms)) { best_ms = ms; bestP = P; std::copy(st4, st4 + 4, best_stats); }
+        }
+        for (size_t i = 1; i < tpts.size(); ++i) {
+            st = run(bestP.delta, tpts[i], int(bestP.nwin), &P, &ms, st4);
+            if (st != CHL_OK) goto done;
+            if (ms >= 0 && ms < best_ms) { best_ms = ms; bestP = P; std::copy(st4, st4 + 4, best_stats); }
+        }
+        for (size_t i = 1; i < wins.size(); ++i) {
+            st = run(bestP.delta, bestP.tpt, wins[i], &P, &ms, st4);
+            if (st != CHL_OK) goto done;
+            if (ms >= 0 && ms < best_ms) { best_ms = ms; bestP = P; std::copy(st4, st4 + 4, best_stats); }
+        }
+    }
+    if (best_ms < 0) {
+        st = set_error(CHL_ENOMEM, "no tuning trial completed");
+        goto done;
+    }
+    *best = o;
+    best->threads_per_tree = bestP.tpt;
+    best->bucket_delta = int32_t(bestP.delta);
+    best->window_buckets = int32_t(bestP.nwin);
+    best->slots = o.slots;  // 0 keeps the memory-budgeted default at build time
+    if (report) {
+        report->trials = trials;
+        report->sample_roots = K;
+        report->best_tree_ms = best_ms;
+        report->best_expanded = best_stats[0];
+        report->best_arcs = best_stats[1];
+    }
+done:
+    free_graph(rg, s);
     return st;
 }

@@ -44,6 +44,7 @@ def test_null_arguments_are_einval(lib):
     assert out.value is None
     assert lib.chl_query(None, None, 0, None, 0, None) == chl.CHL_EINVAL
     assert lib.chl_labels_info(None, None, None, None) == chl.CHL_EINVAL
+    assert lib.chl_tune(None, None, None, None, None, None) == chl.CHL_EINVAL
     lib.chl_labels_free(None)
 
 

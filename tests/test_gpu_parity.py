@@ -137,6 +137,17 @@ def test_ba2k_launch_configurations(ba2k, opts):
     assert_same(ref, off, hub, dist)
 
 
+def test_tuned_parameters_are_exact(ba2k):
+    g, rank, ref = ba2k
+    opts, rep = chl.tune(DG(g), dev(rank))
+    assert rep["trials"] >= 3 and rep["sample_roots"] >= 1 and rep["best_tree_ms"] > 0
+    assert opts["threads_per_tree"] in (128, 256, 512) and opts["bucket_delta"] >= 1
+    _, off, hub, dist = gpu_labels(g, rank, **opts)
+    assert_same(ref, off, hub, dist)
+    fixed, _ = chl.tune(DG(g), dev(rank), bucket_delta=7)
+    assert fixed["bucket_delta"] == 7
+
+
 def test_root_ranges_partition_labels_by_hub(ba2k):
     g, rank, ref = ba2k
     n = g.n
