@@ -107,11 +107,16 @@ typedef struct chl_labels chl_labels;
  *                          dynamically in rank order by one launch);
  *                          1 = plain: one launch per root (one CTA of
  *                          threads_per_tree threads, default 512, builds it)
- *   flags                  reserved, must be 0
+ *   flags                  bit set of CHL_FLAG_*; other bits are rejected
  *   label_capacity         initial size of the label buffer in labels; when
  *                          a tree does not fit, the buffer doubles and the
  *                          roots that did not fit are built again
  */
+/* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
+   every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
+   labels are the same either way). */
+#define CHL_FLAG_WIDE_KEYS 1
+
 typedef struct {
     uint32_t root_begin;
     uint32_t root_end;

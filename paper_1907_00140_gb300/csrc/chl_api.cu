@@ -55,6 +55,7 @@ struct Params {
     uint32_t delta;
     uint32_t nwin;
     int slots;
+    int kb;  // bytes per tree key: 4 or 8
 };
 
 // Untuned defaults of the search parameters from graph statistics (chl_tune
@@ -71,11 +72,15 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     uint32_t d = o.bucket_delta > 0 ? uint32_t(o.bucket_delta) : uint32_t(dflt);
     p.delta = d < 1 ? 1 : d;
     p.nwin = o.window_buckets > 0 ? uint32_t(o.window_buckets) : 32;
+    // 4-byte keys hold distances up to 2^31 - 2; every tentative distance of a
+    // tree search is at most w_max * n (a simple path plus one arc)
+    const bool narrow_fits = double(g.w_max) * double(g.n) <= double(0x7FFFFFFE);
+    p.kb = (narrow_fits && !(o.flags & CHL_FLAG_WIDE_KEYS)) ? 4 : 8;
     int per_sm = plant_max_slots_per_sm(p.tpt);
     if (per_sm < 1) per_sm = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
-    // slot state per vertex: key 8 + three tags 12 + (4 + nwin) lists of 4 bytes
-    const double per_slot = (20.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
+    // slot state per vertex: key + three tags 12 + (4 + nwin) lists of 4 bytes
+    const double per_slot = (p.kb + 12.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
     const double budget = 0.35 * double(free_bytes);
     long long cap = (long long)(budget / per_slot);
     if (o.slots <= 0 && slots > cap) slots = cap;
@@ -89,6 +94,46 @@ struct DevBuf {
     cudaStream_t s = nullptr;
     ~DevBuf() {
         if (p) cudaFreeAsync(p, s);
+    }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+    }
+};
+
+// Per-slot search state of the tree kernel, in its idle form: keys all ones
+// (unreached), tags and instance counters 0.
+struct SlotState {
+    DevBuf key, tags, lists, ctr;
+    cudaError_t alloc(const Params &P, uint32_t n, cudaStream_t s) {
+        key.s = tags.s = lists.s = ctr.s = s;
+        const size_t sn = size_t(P.slots) * n;
+        cudaError_t e;
+        if ((e = cudaMallocAsync(&key.p, sn * P.kb, s))) return e;
+        if ((e = cudaMemsetAsync(key.p, 0xFF, sn * P.kb, s))) return e;
+        if ((e = cudaMallocAsync(&tags.p, sn * 12, s))) return e;
+        if ((e = cudaMemsetAsync(tags.p, 0, sn * 12, s))) return e;
+        if ((e = cudaMallocAsync(&lists.p, sn * 4 * (4 + P.nwin), s))) return e;
+        if ((e = cudaMallocAsync(&ctr.p, size_t(P.slots) * 16, s))) return e;
+        if ((e = cudaMemsetAsync(ctr.p, 0, size_t(P.slots) * 16, s))) return e;
+        return cudaSuccess;
+    }
+    void fill(const Params &P, uint32_t n, TreeLaunch &tl) const {
+        tl.delta = P.delta;
+        tl.nwin = P.nwin;
+        tl.key = key.p;
+        tl.key_bytes = P.kb;
+        tl.rtag = (uint32_t *)tags.p;
+        tl.wtag = tl.rtag + size_t(P.slots) * n;
+        tl.ftag = tl.wtag + size_t(P.slots) * n;
+        tl.lists = (uint32_t *)lists.p;
+        tl.slot_ctr = (uint32_t *)ctr.p;
+    }
+    void release() {
+        key.release();
+        tags.release();
+        lists.release();
+        ctr.release();
     }
 };
 
@@ -135,7 +180,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         return set_error(CHL_EINVAL, "window_buckets must be in [2,64]");
     if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
     if (o.bucket_delta < 0 || o.slots < 0) return set_error(CHL_EINVAL, "negative option");
-    if (o.flags != 0) return set_error(CHL_EINVAL, "flags is reserved and must be 0");
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS)) return set_error(CHL_EINVAL, "unknown bit in flags");
 
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;
@@ -145,8 +190,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const uint64_t m2 = g->num_arcs;
     const uint64_t *d_row = g->row_ptr;
     const uint32_t *d_col = g->col, *d_w = g->w, *d_rank = rank;
-    DevBuf b_row, b_col, b_w, b_rank, b_key, b_tags, b_lists, b_ctr, b_ctl, b_ov, b_oh, b_od,
-        b_fail, b_roots;
+    DevBuf b_row, b_col, b_w, b_rank, b_ctl, b_ov, b_oh, b_od, b_fail, b_roots;
+    SlotState slot;
     RankGraph rg;
     Params P{};
     Control hc{};
@@ -167,7 +212,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventRecord(ev[0], s));
-    b_row.s = b_col.s = b_w.s = b_rank.s = b_key.s = b_tags.s = b_lists.s = b_ctr.s = b_ctl.s = s;
+    b_row.s = b_col.s = b_w.s = b_rank.s = b_ctl.s = s;
     b_ov.s = b_oh.s = b_od.s = b_fail.s = b_roots.s = s;
 
     // inputs on the device
@@ -204,14 +249,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     P = choose_params(rg, o, sms, free_b);
     if (o.mode == 1) { P.slots = 1; P.tpt = o.threads_per_tree ? o.threads_per_tree : 512; }
 
-    // slot state
-    CUDA_TRY(cudaMallocAsync(&b_key.p, size_t(P.slots) * n * 8, s));
-    CUDA_TRY(cudaMemsetAsync(b_key.p, 0xFF, size_t(P.slots) * n * 8, s));
-    CUDA_TRY(cudaMallocAsync(&b_tags.p, size_t(P.slots) * n * 12, s));
-    CUDA_TRY(cudaMemsetAsync(b_tags.p, 0, size_t(P.slots) * n * 12, s));
-    CUDA_TRY(cudaMallocAsync(&b_lists.p, size_t(P.slots) * n * 4 * (4 + P.nwin), s));
-    CUDA_TRY(cudaMallocAsync(&b_ctr.p, size_t(P.slots) * 16, s));
-    CUDA_TRY(cudaMemsetAsync(b_ctr.p, 0, size_t(P.slots) * 16, s));
+    CUDA_TRY(slot.alloc(P, n, s));
     CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
     ctl = (Control *)b_ctl.p;
     CUDA_TRY(cudaMallocAsync(&b_fail.p, size_t(re - rb + 1) * 4, s));
@@ -240,14 +278,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         tl.row = rg.row;
         tl.arc = rg.arc;
         tl.vert_at = rg.vert_at;
-        tl.delta = P.delta;
-        tl.nwin = P.nwin;
-        tl.key = (uint64_t *)b_key.p;
-        tl.rtag = (uint32_t *)b_tags.p;
-        tl.wtag = tl.rtag + size_t(P.slots) * n;
-        tl.ftag = tl.wtag + size_t(P.slots) * n;
-        tl.lists = (uint32_t *)b_lists.p;
-        tl.slot_ctr = (uint32_t *)b_ctr.p;
+        slot.fill(P, n, tl);
         tl.out_v = (uint32_t *)b_ov.p;
         tl.out_h = (uint32_t *)b_oh.p;
         tl.out_d = (uint32_t *)b_od.p;
@@ -355,9 +386,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     }
     CUDA_TRY(cudaEventRecord(ev[2], s));
     // slot state is no longer needed: release it before assembly
-    cudaFreeAsync(b_key.p, s); b_key.p = nullptr;
-    cudaFreeAsync(b_tags.p, s); b_tags.p = nullptr;
-    cudaFreeAsync(b_lists.p, s); b_lists.p = nullptr;
+    slot.release();
 
     CUDA_TRY(assemble_labels(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
                              (const uint32_t *)b_od.p, rg.vert_at, csr, &too_long, s, &launches));
@@ -573,8 +602,9 @@ chl_status tree_trial(const RankGraph &rg, const Params &P, const uint32_t *root
                       uint64_t cap, cudaStream_t s, float *ms, unsigned long long *stats4) {
     chl_status st = CHL_OK;
     const uint32_t n = rg.n;
-    DevBuf b_key, b_tags, b_lists, b_ctr, b_ctl, b_ov, b_oh, b_od, b_fail;
-    b_key.s = b_tags.s = b_lists.s = b_ctr.s = b_ctl.s = b_ov.s = b_oh.s = b_od.s = b_fail.s = s;
+    DevBuf b_ctl, b_ov, b_oh, b_od, b_fail;
+    SlotState slot;
+    b_ctl.s = b_ov.s = b_oh.s = b_od.s = b_fail.s = s;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     Control hc{};
     Control *ctl = nullptr;
@@ -582,13 +612,7 @@ chl_status tree_trial(const RankGraph &rg, const Params &P, const uint32_t *root
     *ms = -1.0f;
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
-    CUDA_TRY(cudaMallocAsync(&b_key.p, size_t(P.slots) * n * 8, s));
-    CUDA_TRY(cudaMemsetAsync(b_key.p, 0xFF, size_t(P.slots) * n * 8, s));
-    CUDA_TRY(cudaMallocAsync(&b_tags.p, size_t(P.slots) * n * 12, s));
-    CUDA_TRY(cudaMemsetAsync(b_tags.p, 0, size_t(P.slots) * n * 12, s));
-    CUDA_TRY(cudaMallocAsync(&b_lists.p, size_t(P.slots) * n * 4 * (4 + P.nwin), s));
-    CUDA_TRY(cudaMallocAsync(&b_ctr.p, size_t(P.slots) * 16, s));
-    CUDA_TRY(cudaMemsetAsync(b_ctr.p, 0, size_t(P.slots) * 16, s));
+    CUDA_TRY(slot.alloc(P, n, s));
     CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
     CUDA_TRY(cudaMemsetAsync(b_ctl.p, 0, sizeof(Control), s));
     CUDA_TRY(cudaMallocAsync(&b_fail.p, size_t(count + 1) * 4, s));
@@ -603,14 +627,7 @@ chl_status tree_trial(const RankGraph &rg, const Params &P, const uint32_t *root
     tl.root_list = roots;
     tl.root_begin = 0;
     tl.root_count = count;
-    tl.delta = P.delta;
-    tl.nwin = P.nwin;
-    tl.key = (uint64_t *)b_key.p;
-    tl.rtag = (uint32_t *)b_tags.p;
-    tl.wtag = tl.rtag + size_t(P.slots) * n;
-    tl.ftag = tl.wtag + size_t(P.slots) * n;
-    tl.lists = (uint32_t *)b_lists.p;
-    tl.slot_ctr = (uint32_t *)b_ctr.p;
+    slot.fill(P, n, tl);
     tl.out_v = (uint32_t *)b_ov.p;
     tl.out_h = (uint32_t *)b_oh.p;
     tl.out_d = (uint32_t *)b_od.p;
@@ -654,6 +671,7 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     chl_build_opts o{};
     if (base) o = *base;
     if (o.mode != 0) return set_error(CHL_EINVAL, "chl_tune tunes the batched mode (mode 0)");
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS)) return set_error(CHL_EINVAL, "unknown bit in flags");
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;
     const uint32_t n = g->n;

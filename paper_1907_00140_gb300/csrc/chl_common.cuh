@@ -9,24 +9,6 @@
 
 namespace chl {
 
-// ------------------------------------------------------------------ keys
-// A tree search key packs (distance, ancestor) into 64 bits:
-//   key = dist << 32 | anc
-// where vertices are renumbered by rank position (pos 0 = most important),
-// so the ancestor with the highest rank R is the one with the smallest id.
-// Under unsigned min a shorter distance wins, and at equal distance the
-// higher-ranked ancestor wins: the tie rule of Algorithm 3 (equal-distance
-// branch) and of the worked example in Sec. 4.2 (a[v5] = v1).
-// `anc` is the smallest pos over the vertices of the best known paths from
-// the root, excluding the vertex itself; a vertex v is "live" (would receive
-// the root h as a hub) iff min(anc, v) == h, i.e. anc == h and v >= h.
-constexpr uint64_t KEY_INF = ~0ull;
-__host__ __device__ inline uint64_t make_key(uint32_t dist, uint32_t anc) {
-    return (uint64_t(dist) << 32) | anc;
-}
-__host__ __device__ inline uint32_t key_dist(uint64_t k) { return uint32_t(k >> 32); }
-__host__ __device__ inline uint32_t key_anc(uint64_t k) { return uint32_t(k); }
-
 // ------------------------------------------------------------------ graph in rank order
 // The input graph renumbered by rank position: vertex p of this graph is the
 // vertex of rank position p (R = n-1-p) of the caller's graph.
@@ -56,7 +38,8 @@ struct TreeLaunch {
     uint32_t delta;
     uint32_t nwin;
     // slot state: slot s owns [s*n, (s+1)*n) of each array
-    uint64_t *key;      // KEY_INF when idle
+    void *key;          // tree keys, all ones when idle (see chl_tree.cu)
+    int key_bytes;      // 4 (distances provably < 2^31 - 1) or 8
     uint32_t *rtag, *wtag, *ftag;
     uint32_t *lists;    // per slot: round lists l0, l1, far, touched, then nwin bucket lists
     uint32_t *slot_ctr; // [slot][4] persistent instance counters

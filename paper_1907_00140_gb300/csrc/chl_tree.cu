@@ -6,12 +6,12 @@
 // root claiming of Sec. 3.1 (threads pop the most important remaining root).
 //
 // Per tree the search is a bucketed label-correcting Dijkstra (delta-stepping,
-// bucket width delta) over packed keys dist<<32 | anc (see chl_common.cuh): a
-// 64-bit atomicMin keeps the shortest distance and, at equal distance, the
-// highest-ranked ancestor (Algorithm 3, equal-distance branch). Every vertex
-// that is expanded relaxes all its arcs, labelled or not: PLaNT does not
-// prune trees (Sec. 1, Sec. 4.2); a vertex outranked by its ancestor only gets
-// no label.
+// bucket width delta) over packed keys (see "Keys" below): an atomicMin keeps
+// the shortest distance and, at equal distance, prefers a path through a
+// vertex that outranks the root (Algorithm 3, equal-distance branch). Every
+// vertex that is expanded relaxes all its arcs, labelled or not: PLaNT does
+// not prune trees (Sec. 1, Sec. 4.2); a vertex outranked by its ancestor only
+// gets no label.
 //
 // Pending vertices (keys in later buckets) are held per bucket:
 //   sub[s]   one list per bucket of the current window of `nwin` buckets
@@ -55,6 +55,33 @@ constexpr uint32_t HUB_DEG = 4 * CHUNK;  // rows this long are shared by all war
 constexpr uint32_t HUBQ = 128;           // queued hub rows per round
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
+// ------------------------------------------------------------------ keys
+// Vertices are numbered by rank position (pos 0 = most important), so in the
+// tree of root h a vertex outranks h iff its pos is below h. Algorithm 3 keeps
+// per vertex its distance and the highest-ranked vertex a[v] on its shortest
+// paths; the label decision only asks whether a[v] is h itself, and a[v] can
+// never rank below h (every path starts at h). So one bit carries it:
+//   key = dist << 1 | clean
+// clean = 1 iff no vertex before v on the best known paths outranks h. Under
+// unsigned min a shorter distance wins and, at equal distance, clean = 0
+// wins: a vertex is outranked as soon as one of its shortest paths is (the
+// equal-distance branch of Algorithm 3; Sec. 4.2's example, a[v5] = v1).
+// v is live (would get the label (h, d)) iff clean and v >= h, and the bit
+// it passes on to its out-neighbours is exactly its own liveness.
+// K = uint32_t when every tentative distance is provably below 2^31 - 1 (the
+// host checks w_max * n), else uint64_t. All ones is "unreached".
+template <typename K>
+__device__ __forceinline__ K key_inf() { return ~K(0); }
+template <typename K>
+__device__ __forceinline__ K make_key(uint64_t dist, bool clean) { return (K(dist) << 1) | K(clean); }
+template <typename K>
+__device__ __forceinline__ uint32_t key_dist(K k) { return uint32_t(k >> 1); }
+// largest distance a key of type K holds below key_inf
+template <typename K>
+__device__ __forceinline__ uint64_t key_dist_limit() {
+    return sizeof(K) == 4 ? 0x7FFFFFFEull : 0xFFFFFFFEull;
+}
+
 struct Shared {
     uint32_t root;
     uint32_t cur_n, nxt_n, far_n, touch_n;
@@ -81,14 +108,16 @@ struct Shared {
     uint64_t hub_rs[HUBQ];
 };
 
+template <typename K>
 struct Slot {
-    uint64_t *key;
+    K *key;
     uint32_t *rtag, *wtag, *ftag;
     uint32_t *l0, *l1, *far, *touch, *sub;  // sub: nwin lists of n entries
 };
 
-__device__ __forceinline__ bool is_live(uint64_t k, uint32_t v, uint32_t h) {
-    return key_anc(k) == h && v >= h;
+template <typename K>
+__device__ __forceinline__ bool is_live(K k, uint32_t v, uint32_t h) {
+    return (k & 1) && v >= h;
 }
 
 // warp-aggregated append to a list counted by a shared-memory counter
@@ -105,7 +134,8 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t *l
 }
 
 // list a pending vertex in bucket b of the window (the tag dedups per bucket)
-__device__ __forceinline__ void sub_append(Shared &S, const Slot &sl, uint32_t n, uint32_t u,
+template <typename K>
+__device__ __forceinline__ void sub_append(Shared &S, const Slot<K> &sl, uint32_t n, uint32_t u,
                                            uint32_t b) {
     const uint32_t s = b - S.win_base;
     const uint32_t tag = S.bid_base + b + 1;
@@ -113,45 +143,57 @@ __device__ __forceinline__ void sub_append(Shared &S, const Slot &sl, uint32_t n
 }
 
 // Relaxation of one arc (v -> u, weight w) of a vertex expanded with distance
-// dv and inclusive ancestor av = min(anc(v), v), in two stages so that a lane
-// can have several key loads in flight:
+// dv and liveness lv (the clean bit it passes on), in two stages so that a
+// lane can have several key loads in flight:
 //   probe:  form the candidate key and load the target's key from L2 (keys
 //           only decrease, so a stale read never hides an improvement)
 //   commit: if the candidate is smaller, atomicMin; on improvement, update
 //           the live-pending count, record the vertex as touched and list it
 //           for the bucket it now falls in
+template <typename K>
 struct Probe {
-    uint64_t cand;
-    uint64_t seen;
+    K cand;
+    K seen;
     uint32_t u;
     bool live;  // still worth committing
 };
 
-__device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t dv,
-                                      uint32_t av, uint2 a, Probe &q) {
+__device__ __forceinline__ uint32_t atomic_min_key(uint32_t *a, uint32_t v) { return atomicMin(a, v); }
+__device__ __forceinline__ uint64_t atomic_min_key(uint64_t *a, uint64_t v) {
+    return atomicMin((unsigned long long *)a, (unsigned long long)v);
+}
+__device__ __forceinline__ void atomic_set_key(uint32_t *a, uint32_t v) { atomicExch(a, v); }
+__device__ __forceinline__ void atomic_set_key(uint64_t *a, uint64_t v) {
+    atomicExch((unsigned long long *)a, (unsigned long long)v);
+}
+
+template <typename K>
+__device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t dv,
+                                      bool lv, uint2 a, Probe<K> &q) {
     q.u = a.x;
     const uint64_t nd = uint64_t(dv) + a.y;
-    if (nd >= 0xFFFFFFFFull) {
+    if (nd > key_dist_limit<K>()) {
         atomicExch(&p.flags[0], ERR_DIST_OVERFLOW);
         S.abort = 1;
         q.live = false;
         return;
     }
-    q.cand = make_key(uint32_t(nd), av);
+    q.cand = make_key<K>(nd, lv);
     q.seen = __ldcg(&sl.key[q.u]);
     q.live = true;
 }
 
-__device__ __forceinline__ void commit(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t h,
-                                       const Probe &q) {
+template <typename K>
+__device__ __forceinline__ void commit(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t h,
+                                       const Probe<K> &q) {
     if (q.cand >= q.seen) return;
     const uint32_t u = q.u;
-    const uint64_t old = atomicMin((unsigned long long *)&sl.key[u], (unsigned long long)q.cand);
+    const K old = atomic_min_key(&sl.key[u], q.cand);
     if (q.cand >= old) return;
-    if (old == KEY_INF) sl.touch[atomicAdd(&S.touch_n, 1u)] = u;
+    if (old == key_inf<K>()) sl.touch[atomicAdd(&S.touch_n, 1u)] = u;
     const uint32_t nb = key_dist(q.cand) / p.delta;
     const bool f_new = nb > S.bcur && is_live(q.cand, u, h);
-    const bool f_old = old != KEY_INF && key_dist(old) / p.delta > S.bcur && is_live(old, u, h);
+    const bool f_old = old != key_inf<K>() && key_dist(old) / p.delta > S.bcur && is_live(old, u, h);
     if (f_new != f_old) atomicAdd(&S.cnt, f_new ? 1 : -1);
     if (nb == S.bcur) {
         if (atomicExch(&sl.rtag[u], S.rid) != S.rid) {
@@ -166,11 +208,12 @@ __device__ __forceinline__ void commit(const TreeLaunch &p, Shared &S, const Slo
 }
 
 // relax arcs [j0, min(j0 + CHUNK, deg)) of one row, UNROLL arcs per lane in flight
-__device__ __forceinline__ void relax_chunk(const TreeLaunch &p, Shared &S, const Slot &sl,
-                                            uint32_t h, uint32_t dv, uint32_t av, uint64_t rs,
+template <typename K>
+__device__ __forceinline__ void relax_chunk(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
+                                            uint32_t h, uint32_t dv, bool lv, uint64_t rs,
                                             uint32_t deg, uint32_t j0, unsigned long long &arcs) {
     const int lane = threadIdx.x & 31;
-    Probe q[UNROLL];
+    Probe<K> q[UNROLL];
     uint2 a[UNROLL];
 #pragma unroll
     for (int k = 0; k < UNROLL; ++k) {
@@ -183,7 +226,7 @@ __device__ __forceinline__ void relax_chunk(const TreeLaunch &p, Shared &S, cons
         q[k].live = false;
         if (j < deg) {
             ++arcs;
-            probe(p, S, sl, dv, av, a[k], q[k]);
+            probe(p, S, sl, dv, lv, a[k], q[k]);
         }
     }
 #pragma unroll
@@ -198,8 +241,8 @@ __device__ __forceinline__ void relax_chunk(const TreeLaunch &p, Shared &S, cons
 // that met them; longer rows (hubs of scale-free graphs) are queued and split
 // into CHUNK-arc pieces that all warps claim, so one hub does not hold the
 // whole CTA at the round barrier.
-template <int TPB>
-__device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t h,
+template <int TPB, typename K>
+__device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t h,
                              unsigned long long &expanded, unsigned long long &arcs) {
     constexpr int NW = TPB / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -209,14 +252,14 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
     const uint64_t t_lo = S.t_lo;
     for (uint32_t base = warp * 32; base < n_cur; base += NW * 32) {
         const uint32_t i = base + lane;
-        uint32_t dv = 0, av = 0, deg = 0;
+        uint32_t dv = 0, av = 0, deg = 0;  // av: liveness of v as 0/1
         uint64_t rs = 0;
         if (i < n_cur) {
             const uint32_t v = cur[i];
-            const uint64_t k = __ldcg(&sl.key[v]);
+            const K k = __ldcg(&sl.key[v]);
             if (key_dist(k) >= t_lo) {  // else stale: expanded in an earlier bucket
                 dv = key_dist(k);
-                av = min(key_anc(k), v);
+                av = is_live(k, v, h);
                 rs = __ldg(&p.row[v]);
                 deg = uint32_t(__ldg(&p.row[v + 1]) - rs);
                 ++expanded;
@@ -243,7 +286,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
             const uint64_t brs = __shfl_sync(FULL, rs, src);
             const uint32_t bdeg = __shfl_sync(FULL, deg, src);
             for (uint32_t j0 = 0; j0 < bdeg; j0 += CHUNK)
-                relax_chunk(p, S, sl, h, bd, ba, brs, bdeg, j0, arcs);
+                relax_chunk(p, S, sl, h, bd, ba != 0, brs, bdeg, j0, arcs);
         }
         // low-degree vertices: pack their arcs densely over the lanes
         const uint32_t ds = deg < LARGE_DEG ? deg : 0;
@@ -269,9 +312,9 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
             const uint32_t oex = __shfl_sync(FULL, excl, o);
             const uint64_t ors = __shfl_sync(FULL, rs, o);
             if (j < total) {
-                Probe q;
+                Probe<K> q;
                 ++arcs;
-                probe(p, S, sl, od, oa, __ldg(&p.arc[ors + (j - oex)]), q);
+                probe(p, S, sl, od, oa != 0, __ldg(&p.arc[ors + (j - oex)]), q);
                 if (q.live) commit(p, S, sl, h, q);
             }
         }
@@ -311,7 +354,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot &sl, uin
                 const uint32_t mid = (lo + hi) >> 1;
                 if (S.hub_pre[mid] <= c) lo = mid; else hi = mid;
             }
-            relax_chunk(p, S, sl, h, S.hub_dv[lo], S.hub_av[lo], S.hub_rs[lo], S.hub_deg[lo],
+            relax_chunk(p, S, sl, h, S.hub_dv[lo], S.hub_av[lo] != 0, S.hub_rs[lo], S.hub_deg[lo],
                         (c - S.hub_pre[lo]) * CHUNK, arcs);
         }
         __syncthreads();
@@ -331,8 +374,8 @@ __device__ __forceinline__ uint32_t warp_min(uint32_t x) {
 // the window lists; the minimum bucket of the remaining entries goes to
 // S.min_b. Tags of removed entries are cleared so the vertex can be listed
 // again.
-template <int TPB>
-__device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t drop_below,
+template <int TPB, typename K>
+__device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t drop_below,
                          bool move) {
     const uint32_t n_in = S.far_n;
     __syncthreads();
@@ -375,8 +418,8 @@ __device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_
 }
 
 // live vertices among the window list of bucket b (entries whose key is in b)
-template <int TPB>
-__device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot &sl, uint32_t h,
+template <int TPB, typename K>
+__device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t h,
                                      uint32_t slot, uint32_t b) {
     __syncthreads();
     if (threadIdx.x == 0) S.live_sum = 0;
@@ -386,7 +429,7 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot 
     int c = 0;
     for (uint32_t i = threadIdx.x; i < cnt; i += TPB) {
         const uint32_t u = lst[i];
-        const uint64_t k = __ldcg(&sl.key[u]);
+        const K k = __ldcg(&sl.key[u]);
         c += (key_dist(k) / p.delta == b && is_live(k, u, h));
     }
 #pragma unroll
@@ -395,13 +438,13 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot 
     __syncthreads();
 }
 
-template <int TPB>
+template <int TPB, typename K>
 __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch p) {
     __shared__ Shared S;
     const uint32_t n = p.n;
     const size_t so = size_t(blockIdx.x) * n;
-    Slot sl;
-    sl.key = p.key + so;
+    Slot<K> sl;
+    sl.key = (K *)p.key + so;
     sl.rtag = p.rtag + so;
     sl.wtag = p.wtag + so;
     sl.ftag = p.ftag + so;
@@ -475,12 +518,12 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 S.abort = 0;
                 sl.l0[0] = h;
                 sl.touch[0] = h;
-                atomicExch((unsigned long long *)&sl.key[h], (unsigned long long)make_key(0, h));
+                atomic_set_key(&sl.key[h], make_key<K>(0, true));
             }
             __syncthreads();
             uint32_t rounds = 0;
             for (;;) {
-                expand_round<TPB>(p, S, sl, h, expanded, arcs);
+                expand_round<TPB, K>(p, S, sl, h, expanded, arcs);
                 __syncthreads();
                 if (S.abort) break;
                 if (++rounds > MAX_ROUNDS_PER_TREE) {
@@ -517,7 +560,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 __syncthreads();
                 if (S.min_b == NONE) {
                     // window used up: restart it at the nearest far bucket
-                    far_pass<TPB>(p, S, sl, S.win_base + p.nwin, false);
+                    far_pass<TPB, K>(p, S, sl, S.win_base + p.nwin, false);
                     if (S.far_n == 0) break;  // nothing pending at all
                     if (threadIdx.x == 0) {
                         S.win_base = S.min_b;
@@ -526,13 +569,13 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                         for (uint32_t s = 0; s < p.nwin; ++s) S.sub_n[s] = 0;
                     }
                     __syncthreads();
-                    far_pass<TPB>(p, S, sl, 0, true);
+                    far_pass<TPB, K>(p, S, sl, 0, true);
                     if (threadIdx.x == 0) S.min_b = S.win_base;
                     __syncthreads();
                 }
                 // enter bucket min_b: its live vertices stop counting as pending
                 const uint32_t nb = S.min_b, slot = nb - S.win_base;
-                count_live_in_bucket<TPB>(p, S, sl, h, slot, nb);
+                count_live_in_bucket<TPB, K>(p, S, sl, h, slot, nb);
                 if (threadIdx.x == 0) {
                     S.cnt -= S.live_sum;
                     S.bcur = nb;
@@ -547,7 +590,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             __syncthreads();
             if (S.abort) {
                 // reset and give up on this tree; the host reports the error
-                for (uint32_t i = threadIdx.x; i < S.touch_n; i += TPB) sl.key[sl.touch[i]] = KEY_INF;
+                for (uint32_t i = threadIdx.x; i < S.touch_n; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
                 __threadfence();
                 __syncthreads();
                 break;
@@ -565,7 +608,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 uint32_t u = 0, d = 0;
                 if (i < nt) {
                     u = sl.touch[i];
-                    const uint64_t k = __ldcg(&sl.key[u]);
+                    const K k = __ldcg(&sl.key[u]);
                     lv = is_live(k, u, h);
                     d = key_dist(k);
                 }
@@ -585,7 +628,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             __syncthreads();
             nlab = S.out_n;
             // reset exactly what this tree modified
-            for (uint32_t i = threadIdx.x; i < nt; i += TPB) sl.key[sl.touch[i]] = KEY_INF;
+            for (uint32_t i = threadIdx.x; i < nt; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
             // the next tree reads keys with L2 loads and L2 atomics: the plain
             // reset stores must be visible there first, not only inside the CTA
             __threadfence();
@@ -641,15 +684,23 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
 
 template <int TPB>
 cudaError_t launch_t(const TreeLaunch &p, int slots, cudaStream_t s) {
-    plant_trees_kernel<TPB><<<slots, TPB, 0, s>>>(p);
+    if (p.key_bytes == 4)
+        plant_trees_kernel<TPB, uint32_t><<<slots, TPB, 0, s>>>(p);
+    else if (p.key_bytes == 8)
+        plant_trees_kernel<TPB, uint64_t><<<slots, TPB, 0, s>>>(p);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
+// both key widths are built under the same register cap, so they share the
+// occupancy of the wide form
 template <int TPB>
 int occ() {
-    int b = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB>, TPB, 0);
-    return b;
+    int b = 0, b4 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB, uint64_t>, TPB, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, plant_trees_kernel<TPB, uint32_t>, TPB, 0);
+    return b < b4 ? b : b4;
 }
 
 }  // namespace

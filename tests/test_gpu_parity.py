@@ -129,12 +129,29 @@ def test_ba2k_host_memory_path(ba2k):
     dict(threads_per_tree=512), dict(bucket_delta=1), dict(bucket_delta=1000),
     dict(window_buckets=2), dict(window_buckets=64, bucket_delta=1), dict(slots=1),
     dict(slots=7, threads_per_tree=32), dict(label_capacity=1), dict(mode=1),
-    dict(mode=1, threads_per_tree=64),
+    dict(mode=1, threads_per_tree=64), dict(flags=chl.CHL_FLAG_WIDE_KEYS),
+    dict(flags=chl.CHL_FLAG_WIDE_KEYS, threads_per_tree=64, bucket_delta=3),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_ba2k_launch_configurations(ba2k, opts):
     g, rank, ref = ba2k
     _, off, hub, dist = gpu_labels(g, rank, **opts)
     assert_same(ref, off, hub, dist)
+
+
+def test_heavy_weights_take_wide_keys():
+    """w_max * n above 2^31 - 1: the build must switch to 8-byte keys and stay
+    exact for distances above 2^31 (still below the 2^32 - 1 limit)."""
+    rng = np.random.default_rng(77)
+    g0 = W.barabasi_albert(300, 2, seed=77, wlo=1, whi=100)
+    eu, ev, _ = g0.edges()
+    edges = [(int(a), int(b), int(rng.integers(1 << 26, 1 << 27))) for a, b in zip(eu, ev)]
+    g = from_edges(g0.n, edges)
+    rank = W.degree_rank(g)
+    ref = O.build_labels(g, rank, "canonical")
+    assert not ref.overflow and int(ref.dist.max()) > (1 << 28)
+    for opts in (dict(), dict(bucket_delta=1 << 24)):
+        _, off, hub, dist = gpu_labels(g, rank, **opts)
+        assert_same(ref, off, hub, dist)
 
 
 def test_tuned_parameters_are_exact(ba2k):
