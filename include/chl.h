@@ -141,6 +141,8 @@ typedef struct {
  *   tree_ms        device time of the tree kernel alone
  *   sort_ms        device time of label assembly (count, scan, scatter, sort)
  *   launches       kernels launched by the build
+ *   rounds         expansion rounds of the tree searches (all trees)
+ *   buckets        distance buckets entered after the first (all trees)
  */
 typedef struct {
     uint64_t trees;
@@ -152,6 +154,8 @@ typedef struct {
     double tree_ms;
     double sort_ms;
     uint64_t launches;
+    uint64_t rounds;
+    uint64_t buckets;
 } chl_build_stats;
 
 /*

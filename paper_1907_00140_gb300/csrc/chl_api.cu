@@ -47,7 +47,7 @@ struct Control {
     unsigned int failed_count;
     int flags[2];
     unsigned long long out_count;
-    unsigned long long stats[4];
+    unsigned long long stats[6];
 };
 
 struct Params {
@@ -203,7 +203,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     float ms_total = 0, ms_tree = 0, ms_sort = 0;
     chl_labels *L = nullptr;
-    unsigned long long agg[4] = {0, 0, 0, 0};
+    unsigned long long agg[6] = {0, 0, 0, 0, 0, 0};
     std::vector<uint32_t> pending;  // roots still to build (after a full buffer)
     uint32_t claimed_upto = 0;
     bool first = true;
@@ -327,7 +327,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         }
         CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
-        for (int k = 0; k < 4; ++k) agg[k] += hc.stats[k];
+        for (int k = 0; k < 6; ++k) agg[k] += hc.stats[k];
         if (hc.flags[0] == ERR_DIST_OVERFLOW) {
             st = set_error(CHL_EOVERFLOW, "a shortest distance reaches UINT32_MAX");
             goto done;
@@ -418,6 +418,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     L->stats.expanded = agg[0];
     L->stats.arcs = agg[1];
     L->stats.trivial = agg[2];
+    L->stats.rounds = agg[4];
+    L->stats.buckets = agg[5];
     L->stats.build_ms = ms_total;
     L->stats.tree_ms = ms_tree;
     L->stats.sort_ms = ms_sort;

@@ -54,7 +54,7 @@ struct TreeLaunch {
     uint32_t *failed;          // roots whose labels did not fit
     unsigned int *failed_count;
     int *flags;                // [0] error code, [1] output full
-    unsigned long long *stats; // [0] expanded [1] arcs [2] trivial [3] trees
+    unsigned long long *stats; // [0] expanded [1] arcs [2] trivial [3] trees [4] rounds [5] buckets
 };
 
 enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2, ERR_RESERVE_LIMIT = 3 };

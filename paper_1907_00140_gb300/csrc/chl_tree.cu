@@ -47,12 +47,8 @@ namespace {
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t MAX_ROUNDS_PER_TREE = 1u << 26;
 constexpr uint32_t RESERVE_TRIES = 1u << 20;
-constexpr int LARGE_DEG = 32;
 constexpr uint32_t NWIN_MAX = 64;
 constexpr int UNROLL = 4;
-constexpr uint32_t CHUNK = 32 * UNROLL;  // arcs one warp relaxes per step
-constexpr uint32_t HUB_DEG = 4 * CHUNK;  // rows this long are shared by all warps
-constexpr uint32_t HUBQ = 128;           // queued hub rows per round
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 
 // ------------------------------------------------------------------ keys
@@ -100,12 +96,9 @@ struct Shared {
     int abort;
     int ok;
     int live_sum;
+    int fuse_live;         // the current list's first stage also counts its live entries
     unsigned long long base;
     uint32_t sub_n[NWIN_MAX];
-    // high-degree rows queued for CTA-wide processing in the current round
-    uint32_t hub_n, hub_next;
-    uint32_t hub_dv[HUBQ], hub_av[HUBQ], hub_deg[HUBQ], hub_pre[HUBQ + 1];
-    uint64_t hub_rs[HUBQ];
 };
 
 template <typename K>
@@ -207,159 +200,184 @@ __device__ __forceinline__ void commit(const TreeLaunch &p, Shared &S, const Slo
     }
 }
 
-// relax arcs [j0, min(j0 + CHUNK, deg)) of one row, UNROLL arcs per lane in flight
-template <typename K>
-__device__ __forceinline__ void relax_chunk(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
-                                            uint32_t h, uint32_t dv, bool lv, uint64_t rs,
-                                            uint32_t deg, uint32_t j0, unsigned long long &arcs) {
-    const int lane = threadIdx.x & 31;
-    Probe<K> q[UNROLL];
-    uint2 a[UNROLL];
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        const uint32_t j = j0 + k * 32 + lane;
-        if (j < deg) a[k] = __ldg(&p.arc[rs + j]);
+// Frontier staging of one chunk of up to TPB list entries, compacted to the
+// entries that are expanded (stale ones dropped): each row's start (with the
+// vertex's liveness in bit 63), its distance, and the exclusive prefix of the
+// degrees. The chunk's arcs then form one flat index range [0, total), cut
+// into one contiguous piece per warp, whatever the degree mix (a hub's row
+// and a thousand short rows alike). Every staged row has at least one arc
+// (a zero-degree vertex is never expanded: it is unreachable or a trivial
+// root), so row starts are distinct flat positions.
+template <int TPB>
+struct Frontier {
+    uint64_t rs[TPB];
+    uint64_t pre[TPB];
+    uint32_t dv[TPB];
+    uint32_t wrows[TPB / 32];
+    uint64_t wdeg[TPB / 32];
+};
+
+constexpr uint64_t LIVE_BIT = 1ull << 63;
+
+// largest o in [lo, hi) with pre[o] <= j, given pre[lo] <= j
+template <int TPB>
+__device__ __forceinline__ uint32_t owner(const Frontier<TPB> &F, uint64_t j, uint32_t lo,
+                                          uint32_t hi) {
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (F.pre[mid] <= j) lo = mid; else hi = mid;
     }
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        const uint32_t j = j0 + k * 32 + lane;
-        q[k].live = false;
-        if (j < deg) {
-            ++arcs;
-            probe(p, S, sl, dv, lv, a[k], q[k]);
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k)
-        if (q[k].live) commit(p, S, sl, h, q[k]);
+    return lo;
 }
 
-// Expand the current list once. In the first round of a bucket the list is
-// the bucket's window list, whose stale entries (keys since lowered into an
-// earlier bucket) are skipped. Rows shorter than 32 arcs are packed densely
-// over the lanes of a warp; rows of 32..HUB_DEG-1 arcs are walked by the warp
-// that met them; longer rows (hubs of scale-free graphs) are queued and split
-// into CHUNK-arc pieces that all warps claim, so one hub does not hold the
-// whole CTA at the round barrier.
+// Expand the current list once, in chunks of TPB entries. In the first round
+// of a bucket the list is the bucket's window list, whose stale entries (keys
+// since lowered into an earlier bucket) are skipped.
+//
+// Arc pass: a warp walks its piece in steps of STEP = 32 * UNROLL consecutive
+// arcs [i0, i0 + STEP). The rows starting inside a step are found with one
+// ballot per 32 rows and recorded as a STEP-bit mask of start positions; the
+// row of position q is then oa + (set bits at positions <= q), oa being the
+// row that covers i0 (the last row of the previous step). Lanes first load
+// UNROLL arcs, then UNROLL keys, then commit, so each lane has UNROLL
+// independent loads in flight at each stage.
 template <int TPB, typename K>
-__device__ void expand_round(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t h,
-                             unsigned long long &expanded, unsigned long long &arcs) {
+__device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, const Slot<K> &sl,
+                             uint32_t h, unsigned long long &expanded, unsigned long long &arcs) {
     constexpr int NW = TPB / 32;
+    constexpr uint32_t STEP = 32 * UNROLL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t *cur = S.cur_slot != NONE ? sl.sub + size_t(S.cur_slot) * p.n
                                              : (S.sel ? sl.l1 : sl.l0);
     const uint32_t n_cur = S.cur_n;
     const uint64_t t_lo = S.t_lo;
-    for (uint32_t base = warp * 32; base < n_cur; base += NW * 32) {
-        const uint32_t i = base + lane;
-        uint32_t dv = 0, av = 0, deg = 0;  // av: liveness of v as 0/1
-        uint64_t rs = 0;
+    // the bucket's live entries stop counting as pending when it is entered;
+    // for a list of one chunk this stage counts them (no commit has run yet)
+    const bool fuse = S.fuse_live != 0;
+    for (uint32_t cb = 0; cb < n_cur; cb += TPB) {
+        // ---- stage the chunk: rows, distances, liveness, degree prefix
+        const uint32_t i = cb + threadIdx.x;
+        uint64_t deg = 0, rs = 0;
+        uint32_t dv = 0;
+        bool lv = false, ok = false;
         if (i < n_cur) {
             const uint32_t v = cur[i];
             const K k = __ldcg(&sl.key[v]);
             if (key_dist(k) >= t_lo) {  // else stale: expanded in an earlier bucket
                 dv = key_dist(k);
-                av = is_live(k, v, h);
                 rs = __ldg(&p.row[v]);
-                deg = uint32_t(__ldg(&p.row[v + 1]) - rs);
+                deg = __ldg(&p.row[v + 1]) - rs;
+                lv = is_live(k, v, h);
+                if (lv) rs |= LIVE_BIT;
+                ok = deg != 0;
                 ++expanded;
             }
         }
-        bool queued = false;
-        if (deg >= HUB_DEG) {
-            const uint32_t slot = atomicAdd(&S.hub_n, 1u);
-            if (slot < HUBQ) {
-                S.hub_dv[slot] = dv;
-                S.hub_av[slot] = av;
-                S.hub_deg[slot] = deg;
-                S.hub_rs[slot] = rs;
-                queued = true;
-            }
+        const unsigned okm = __ballot_sync(FULL, ok);
+        if (fuse) {
+            const int c = __popc(__ballot_sync(FULL, lv));
+            if (lane == 0 && c) atomicSub(&S.cnt, c);
         }
-        // rows of 32+ arcs not queued: the whole warp walks the row
-        unsigned big = __ballot_sync(FULL, deg >= LARGE_DEG && !queued);
-        while (big) {
-            const int src = __ffs(big) - 1;
-            big &= big - 1;
-            const uint32_t bd = __shfl_sync(FULL, dv, src);
-            const uint32_t ba = __shfl_sync(FULL, av, src);
-            const uint64_t brs = __shfl_sync(FULL, rs, src);
-            const uint32_t bdeg = __shfl_sync(FULL, deg, src);
-            for (uint32_t j0 = 0; j0 < bdeg; j0 += CHUNK)
-                relax_chunk(p, S, sl, h, bd, ba != 0, brs, bdeg, j0, arcs);
-        }
-        // low-degree vertices: pack their arcs densely over the lanes
-        const uint32_t ds = deg < LARGE_DEG ? deg : 0;
-        uint32_t incl = ds;
+        uint64_t inc = deg;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += t;
+            const uint64_t t = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += t;
         }
-        const uint32_t total = __shfl_sync(FULL, incl, 31);
-        const uint32_t excl = incl - ds;
-        for (uint32_t jb = 0; jb < total; jb += 32) {
-            const uint32_t j = jb + lane;
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int c = o + step;
-                const uint32_t ex = __shfl_sync(FULL, excl, c);
-                if (ex <= j) o = c;
-            }
-            const uint32_t od = __shfl_sync(FULL, dv, o);
-            const uint32_t oa = __shfl_sync(FULL, av, o);
-            const uint32_t oex = __shfl_sync(FULL, excl, o);
-            const uint64_t ors = __shfl_sync(FULL, rs, o);
-            if (j < total) {
-                Probe<K> q;
-                ++arcs;
-                probe(p, S, sl, od, oa != 0, __ldg(&p.arc[ors + (j - oex)]), q);
-                if (q.live) commit(p, S, sl, h, q);
-            }
+        if (lane == 31) {
+            F.wdeg[warp] = inc;
+            F.wrows[warp] = __popc(okm);
         }
-    }
-    __syncthreads();
-    // queued hub rows: CHUNK-arc pieces claimed by any warp
-    const uint32_t nh = min(S.hub_n, HUBQ);
-    if (nh) {
-        if (warp == 0) {
-            uint32_t run = 0;
-            for (uint32_t b = 0; b < nh; b += 32) {
-                const uint32_t it = b + lane;
-                const uint32_t c = it < nh ? (S.hub_deg[it] + CHUNK - 1) / CHUNK : 0;
-                uint32_t inc = c;
+        __syncthreads();
+        // every warp sums the warp totals itself: its offsets and the chunk totals
+        uint64_t dl = 0, da = 0;
+        uint32_t rl = 0, ra = 0;
+        if (lane < NW) {
+            const uint64_t x = F.wdeg[lane];
+            const uint32_t r = F.wrows[lane];
+            da = x;
+            ra = r;
+            if (lane < warp) { dl = x; rl = r; }
+        }
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(FULL, inc, o);
-                    if (lane >= o) inc += t;
+        for (int o = 16; o; o >>= 1) {
+            dl += __shfl_xor_sync(FULL, dl, o);
+            da += __shfl_xor_sync(FULL, da, o);
+            rl += __shfl_xor_sync(FULL, rl, o);
+            ra += __shfl_xor_sync(FULL, ra, o);
+        }
+        if (ok) {
+            const uint32_t c = rl + __popc(okm & ((1u << lane) - 1));
+            F.rs[c] = rs;
+            F.dv[c] = dv;
+            F.pre[c] = dl + inc - deg;
+        }
+        const uint64_t total = da;
+        const uint32_t nrows = ra;
+        __syncthreads();
+
+        // ---- relax the chunk's arcs: warp w takes [lo, hi) of [0, total)
+        const uint64_t per = (total + NW - 1) / NW;
+        const uint64_t lo = per * warp;
+        const uint64_t hi = lo + per < total ? lo + per : total;
+        if (lo < hi) {
+            uint32_t oa = owner(F, lo, 0, nrows);
+            for (uint64_t i0 = lo; i0 < hi; i0 += STEP) {
+                const uint32_t span = hi - i0 < STEP ? uint32_t(hi - i0) : STEP;  // positions in this step
+                // start positions (1..span-1) of rows oa+1, oa+2, ... inside the step
+                uint32_t wm[UNROLL];
+#pragma unroll
+                for (int k = 0; k < UNROLL; ++k) wm[k] = 0;
+                uint32_t ob = oa;
+                for (;;) {
+                    const uint32_t o = ob + 1 + lane;
+                    uint32_t q = STEP;
+                    if (o < nrows) {
+                        const uint64_t st = F.pre[o];
+                        if (st < i0 + span) q = uint32_t(st - i0);
+                    }
+                    const unsigned m = __ballot_sync(FULL, q < STEP);
+#pragma unroll
+                    for (int k = 0; k < UNROLL; ++k)
+                        wm[k] |= __reduce_or_sync(FULL, (q >> 5) == uint32_t(k) ? 1u << (q & 31) : 0u);
+                    ob += __popc(m);
+                    if (m != FULL) break;
                 }
-                if (it < nh) S.hub_pre[it] = run + inc - c;
-                run += __shfl_sync(FULL, inc, 31);
-            }
-            if (lane == 0) {
-                S.hub_pre[nh] = run;
-                S.hub_next = 0;
+                uint32_t cum[UNROLL];
+                cum[0] = 0;
+#pragma unroll
+                for (int k = 1; k < UNROLL; ++k) cum[k] = cum[k - 1] + __popc(wm[k - 1]);
+                uint2 a[UNROLL];
+                uint32_t d[UNROLL];
+                bool lvk[UNROLL];
+#pragma unroll
+                for (int k = 0; k < UNROLL; ++k) {
+                    const uint32_t q = k * 32 + lane;
+                    if (q < span) {
+                        const uint32_t o = oa + cum[k] + __popc(wm[k] & ((2u << lane) - 1u));
+                        const uint64_t r = F.rs[o];
+                        d[k] = F.dv[o];
+                        lvk[k] = (r & LIVE_BIT) != 0;
+                        a[k] = __ldg(&p.arc[(r & ~LIVE_BIT) + (i0 + q - F.pre[o])]);
+                    }
+                }
+                Probe<K> pr[UNROLL];
+#pragma unroll
+                for (int k = 0; k < UNROLL; ++k) {
+                    pr[k].live = false;
+                    if (uint32_t(k * 32 + lane) < span) {
+                        ++arcs;
+                        probe(p, S, sl, d[k], lvk[k], a[k], pr[k]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < UNROLL; ++k)
+                    if (pr[k].live) commit(p, S, sl, h, pr[k]);
+                oa = ob;
             }
         }
-        __syncthreads();
-        const uint32_t chunks = S.hub_pre[nh];
-        for (;;) {
-            uint32_t c = 0;
-            if (lane == 0) c = atomicAdd(&S.hub_next, 1u);
-            c = __shfl_sync(FULL, c, 0);
-            if (c >= chunks) break;
-            uint32_t lo = 0, hi = nh;  // largest item with hub_pre[item] <= c
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (S.hub_pre[mid] <= c) lo = mid; else hi = mid;
-            }
-            relax_chunk(p, S, sl, h, S.hub_dv[lo], S.hub_av[lo] != 0, S.hub_rs[lo], S.hub_deg[lo],
-                        (c - S.hub_pre[lo]) * CHUNK, arcs);
-        }
-        __syncthreads();
+        __syncthreads();  // the next chunk rewrites the staging arrays
     }
-    if (threadIdx.x == 0) S.hub_n = 0;
 }
 
 __device__ __forceinline__ uint32_t warp_min(uint32_t x) {
@@ -441,6 +459,7 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot<
 template <int TPB, typename K>
 __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch p) {
     __shared__ Shared S;
+    __shared__ Frontier<TPB> F;
     const uint32_t n = p.n;
     const size_t so = size_t(blockIdx.x) * n;
     Slot<K> sl;
@@ -455,9 +474,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     sl.touch = lb + 3 * size_t(n);
     sl.sub = lb + 4 * size_t(n);
 
-    unsigned long long expanded = 0, arcs = 0, trivial = 0, trees = 0;
+    unsigned long long expanded = 0, arcs = 0, trivial = 0, trees = 0, rounds_all = 0, buckets = 0;
     if (threadIdx.x == 0) {
-        S.hub_n = 0;
         S.rid = p.slot_ctr[blockIdx.x * 4 + 0];
         S.bid_base = p.slot_ctr[blockIdx.x * 4 + 1];
         S.fid = p.slot_ctr[blockIdx.x * 4 + 2];
@@ -516,6 +534,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 S.t_hi = p.delta;
                 S.w_hi = uint64_t(p.delta) * p.nwin;
                 S.abort = 0;
+                S.fuse_live = 0;
                 sl.l0[0] = h;
                 sl.touch[0] = h;
                 atomic_set_key(&sl.key[h], make_key<K>(0, true));
@@ -523,9 +542,9 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             __syncthreads();
             uint32_t rounds = 0;
             for (;;) {
-                expand_round<TPB, K>(p, S, sl, h, expanded, arcs);
-                __syncthreads();
+                expand_round<TPB, K>(p, S, F, sl, h, expanded, arcs);  // ends with a barrier
                 if (S.abort) break;
+                ++rounds_all;
                 if (++rounds > MAX_ROUNDS_PER_TREE) {
                     if (threadIdx.x == 0) atomicExch(&p.flags[0], ERR_ROUND_LIMIT);
                     break;
@@ -535,6 +554,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                     if (threadIdx.x == 0) {
                         S.sel ^= 1u;  // the next round reads the list this round appended to
                         S.cur_slot = NONE;
+                        S.fuse_live = 0;
                         S.cur_n = S.nxt_n;
                         S.nxt_n = 0;
                         S.rid += 1;
@@ -542,22 +562,25 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                     __syncthreads();
                     continue;
                 }
-                // bucket settled: every key below t_hi is final
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    if (S.bcur >= S.win_base) S.sub_n[S.bcur - S.win_base] = 0;  // consumed
-                    S.cur_slot = NONE;
-                    S.min_b = NONE;
+                // bucket settled: every key below t_hi is final. Warp 0 marks
+                // its list consumed and finds the next non-empty window bucket.
+                if (threadIdx.x < 32) {
+                    const uint32_t s0 = S.bcur >= S.win_base ? S.bcur - S.win_base + 1 : 0;
+                    uint32_t found = NONE;
+                    for (uint32_t b0 = 0; b0 < p.nwin; b0 += 32) {
+                        const uint32_t sx = b0 + threadIdx.x;
+                        const unsigned m = __ballot_sync(FULL, sx >= s0 && sx < p.nwin && S.sub_n[sx] != 0);
+                        if (m) { found = S.win_base + b0 + __ffs(m) - 1; break; }
+                    }
+                    __syncwarp();
+                    if (threadIdx.x == 0) {
+                        if (S.bcur >= S.win_base) S.sub_n[S.bcur - S.win_base] = 0;  // consumed
+                        S.cur_slot = NONE;
+                        S.min_b = found;
+                    }
                 }
                 __syncthreads();
                 if (S.cnt == 0) break;  // no pending vertex can still receive the root as hub
-                // next non-empty bucket of the window
-                if (threadIdx.x == 0) {
-                    const uint32_t s0 = S.bcur >= S.win_base ? S.bcur - S.win_base + 1 : 0;
-                    for (uint32_t s = s0; s < p.nwin; ++s)
-                        if (S.sub_n[s]) { S.min_b = S.win_base + s; break; }
-                }
-                __syncthreads();
                 if (S.min_b == NONE) {
                     // window used up: restart it at the nearest far bucket
                     far_pass<TPB, K>(p, S, sl, S.win_base + p.nwin, false);
@@ -575,9 +598,12 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 }
                 // enter bucket min_b: its live vertices stop counting as pending
                 const uint32_t nb = S.min_b, slot = nb - S.win_base;
-                count_live_in_bucket<TPB, K>(p, S, sl, h, slot, nb);
+                ++buckets;
+                const bool fuse = S.sub_n[slot] <= TPB;
+                if (!fuse) count_live_in_bucket<TPB, K>(p, S, sl, h, slot, nb);
                 if (threadIdx.x == 0) {
-                    S.cnt -= S.live_sum;
+                    if (!fuse) S.cnt -= S.live_sum;
+                    S.fuse_live = fuse;
                     S.bcur = nb;
                     S.t_lo = uint64_t(nb) * p.delta;
                     S.t_hi = S.t_lo + p.delta;
@@ -676,6 +702,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     if (threadIdx.x == 0) {
         atomicAdd(&p.stats[2], trivial);
         atomicAdd(&p.stats[3], trees);
+        atomicAdd(&p.stats[4], rounds_all);
+        atomicAdd(&p.stats[5], buckets);
         p.slot_ctr[blockIdx.x * 4 + 0] = S.rid;
         p.slot_ctr[blockIdx.x * 4 + 1] = S.bid_base;
         p.slot_ctr[blockIdx.x * 4 + 2] = S.fid;
