@@ -97,8 +97,8 @@ typedef struct chl_labels chl_labels;
  *                          the most important vertex). root_end = 0 means n.
  *                          Trees are independent (Sec. 4.2), so disjoint
  *                          ranges partition the labels by hub.
- *   threads_per_tree       CUDA threads cooperating on one tree (32..512,
- *                          multiple of 32)
+ *   threads_per_tree       CUDA threads cooperating on one tree (a power of
+ *                          two in [32, 1024])
  *   bucket_delta           distance width of one bucket of the tree search
  *                          (>= 1)
  *   window_buckets         buckets held in the near window (2..64)

@@ -56,6 +56,9 @@ struct Params {
     uint32_t nwin;
     int slots;
     int kb;  // bytes per tree key: 4 or 8
+    uint32_t fin_words;  // settled-filter bitmap words per CTA
+    uint32_t w_min;
+    uint32_t n;
 };
 
 // Untuned defaults of the search parameters from graph statistics (chl_tune
@@ -76,11 +79,14 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     // tree search is at most w_max * n (a simple path plus one arc)
     const bool narrow_fits = double(g.w_max) * double(g.n) <= double(0x7FFFFFFE);
     p.kb = (narrow_fits && !(o.flags & CHL_FLAG_WIDE_KEYS)) ? 4 : 8;
-    int per_sm = plant_max_slots_per_sm(p.tpt);
+    p.fin_words = plant_fin_words(p.tpt, g.n);
+    p.w_min = g.w_min ? g.w_min : 1;
+    p.n = g.n;
+    int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words);
     if (per_sm < 1) per_sm = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
-    // slot state per vertex: key + three tags 12 + (4 + nwin) lists of 4 bytes
-    const double per_slot = (p.kb + 12.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
+    // slot state per vertex: key + round tag 4 + (4 + nwin) lists of 4 bytes
+    const double per_slot = (p.kb + 4.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
     const double budget = 0.35 * double(free_bytes);
     long long cap = (long long)(budget / per_slot);
     if (o.slots <= 0 && slots > cap) slots = cap;
@@ -111,8 +117,8 @@ struct SlotState {
         cudaError_t e;
         if ((e = cudaMallocAsync(&key.p, sn * P.kb, s))) return e;
         if ((e = cudaMemsetAsync(key.p, 0xFF, sn * P.kb, s))) return e;
-        if ((e = cudaMallocAsync(&tags.p, sn * 12, s))) return e;
-        if ((e = cudaMemsetAsync(tags.p, 0, sn * 12, s))) return e;
+        if ((e = cudaMallocAsync(&tags.p, sn * 4, s))) return e;
+        if ((e = cudaMemsetAsync(tags.p, 0, sn * 4, s))) return e;
         if ((e = cudaMallocAsync(&lists.p, sn * 4 * (4 + P.nwin), s))) return e;
         if ((e = cudaMallocAsync(&ctr.p, size_t(P.slots) * 16, s))) return e;
         if ((e = cudaMemsetAsync(ctr.p, 0, size_t(P.slots) * 16, s))) return e;
@@ -123,9 +129,10 @@ struct SlotState {
         tl.nwin = P.nwin;
         tl.key = key.p;
         tl.key_bytes = P.kb;
+        tl.w_min = P.w_min;
+        tl.fin_words = P.fin_words;
+        tl.fin_bits = P.fin_words * 32 < n ? P.fin_words * 32 : n;
         tl.rtag = (uint32_t *)tags.p;
-        tl.wtag = tl.rtag + size_t(P.slots) * n;
-        tl.ftag = tl.wtag + size_t(P.slots) * n;
         tl.lists = (uint32_t *)lists.p;
         tl.slot_ctr = (uint32_t *)ctr.p;
     }
@@ -174,8 +181,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const uint32_t n = g->n;
     const uint32_t rb = o.root_begin, re = o.root_end ? o.root_end : n;
     if (rb > re || re > n) return set_error(CHL_EINVAL, "root range [%u,%u) outside [0,%u)", rb, re, n);
-    if (o.threads_per_tree && (o.threads_per_tree % 32 || o.threads_per_tree < 32 || o.threads_per_tree > 512))
-        return set_error(CHL_EINVAL, "threads_per_tree must be 32..512 and a multiple of 32");
+    if (o.threads_per_tree && (o.threads_per_tree < 32 || o.threads_per_tree > 1024 ||
+                               (o.threads_per_tree & (o.threads_per_tree - 1))))
+        return set_error(CHL_EINVAL, "threads_per_tree must be a power of two in [32, 1024]");
     if (o.window_buckets && (o.window_buckets < 2 || o.window_buckets > 64))
         return set_error(CHL_EINVAL, "window_buckets must be in [2,64]");
     if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
@@ -246,8 +254,12 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (st != CHL_OK) goto done;
 
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    P = choose_params(rg, o, sms, free_b);
-    if (o.mode == 1) { P.slots = 1; P.tpt = o.threads_per_tree ? o.threads_per_tree : 512; }
+    {
+        chl_build_opts oq = o;
+        if (o.mode == 1 && !oq.threads_per_tree) oq.threads_per_tree = 512;  // plain form: one CTA
+        P = choose_params(rg, oq, sms, free_b);
+        if (o.mode == 1) P.slots = 1;
+    }
 
     CUDA_TRY(slot.alloc(P, n, s));
     CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
@@ -744,7 +756,7 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
         }
         std::vector<int> tpts;
         if (o.threads_per_tree) tpts.push_back(o.threads_per_tree);
-        else tpts = {256, 128, 512};
+        else tpts = {256, 128, 512, 1024};
         std::vector<int> wins;
         if (o.window_buckets) wins.push_back(o.window_buckets);
         else wins = {32, 16, 64};

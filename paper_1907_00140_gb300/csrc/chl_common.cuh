@@ -37,10 +37,13 @@ struct TreeLaunch {
     // search parameters
     uint32_t delta;
     uint32_t nwin;
+    uint32_t w_min;     // lightest arc weight
+    uint32_t fin_words; // settled-filter bitmap words in dynamic shared memory
+    uint32_t fin_bits;  // vertices (pos) the bitmap covers: min(n, 32 * fin_words)
     // slot state: slot s owns [s*n, (s+1)*n) of each array
     void *key;          // tree keys, all ones when idle (see chl_tree.cu)
     int key_bytes;      // 4 (distances provably < 2^31 - 1) or 8
-    uint32_t *rtag, *wtag, *ftag;
+    uint32_t *rtag;     // per slot: round id that last listed the vertex in nxt
     uint32_t *lists;    // per slot: round lists l0, l1, far, touched, then nwin bucket lists
     uint32_t *slot_ctr; // [slot][4] persistent instance counters
     // label output (structure of arrays)
@@ -62,7 +65,9 @@ enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2, ERR_RESER
 // launches (defined in chl_tree.cu)
 cudaError_t launch_plant_trees(const TreeLaunch &p, int threads_per_tree, int slots,
                                cudaStream_t s);
-int plant_max_slots_per_sm(int threads_per_tree);
+int plant_max_slots_per_sm(int threads_per_tree, uint32_t fin_words);
+// settled-filter words for n vertices that keep the CTAs per SM of fin_words = 0
+uint32_t plant_fin_words(int threads_per_tree, uint32_t n);
 
 // label assembly (chl_labels.cu)
 struct LabelCSR {

@@ -22,6 +22,11 @@
 //   nxt      vertices improved inside the current bucket during a round
 // plus `touched`, every vertex that got a finite key (for emission and for
 // resetting only what the tree modified, footnote of Sec. 3.1).
+// The value an atomicMin replaces says which lists already hold the vertex,
+// since buckets only move down: a window bucket is joined iff the old key was
+// in another bucket, far iff the old key was unreached (a key beyond the
+// window was far-listed when it was set, and keys never rise back past the
+// window). Only the per-round nxt list needs a tag (rtag, the round id).
 //
 // Early termination (Sec. 4.2). The paper stops when every vertex in
 // Dijkstra's queue is outranked; Algorithm 3 keeps the count `cnt` of queued
@@ -81,13 +86,11 @@ __device__ __forceinline__ uint64_t key_dist_limit() {
 struct Shared {
     uint32_t root;
     uint32_t cur_n, nxt_n, far_n, touch_n;
-    uint32_t rid, fid;
+    uint32_t rid;
     uint32_t sel;          // round lists: cur = sel ? l1 : l0 (rounds after the first)
     uint32_t cur_slot;     // window slot expanded in the bucket's first round, NONE after
     uint32_t bcur;         // current bucket
     uint32_t win_base;     // bucket of window slot 0
-    uint32_t bid_base;     // tag of bucket b is bid_base + b + 1
-    uint32_t bid_top;      // one past the largest bucket tagged in this tree
     int cnt;               // live vertices with keys beyond the current bucket
     uint64_t t_lo, t_hi;   // current bucket [t_lo, t_hi)
     uint64_t w_hi;         // end of the window
@@ -104,7 +107,7 @@ struct Shared {
 template <typename K>
 struct Slot {
     K *key;
-    uint32_t *rtag, *wtag, *ftag;
+    uint32_t *rtag;
     uint32_t *l0, *l1, *far, *touch, *sub;  // sub: nwin lists of n entries
 };
 
@@ -126,13 +129,12 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t val, uint32_t *l
     if (pred) list[base + __popc(m & ((1u << lane) - 1))] = val;
 }
 
-// list a pending vertex in bucket b of the window (the tag dedups per bucket)
+// list a pending vertex in bucket b of the window
 template <typename K>
 __device__ __forceinline__ void sub_append(Shared &S, const Slot<K> &sl, uint32_t n, uint32_t u,
                                            uint32_t b) {
     const uint32_t s = b - S.win_base;
-    const uint32_t tag = S.bid_base + b + 1;
-    if (atomicExch(&sl.wtag[u], tag) != tag) sl.sub[size_t(s) * n + atomicAdd(&S.sub_n[s], 1u)] = u;
+    sl.sub[size_t(s) * n + atomicAdd(&S.sub_n[s], 1u)] = u;
 }
 
 // Relaxation of one arc (v -> u, weight w) of a vertex expanded with distance
@@ -160,43 +162,104 @@ __device__ __forceinline__ void atomic_set_key(uint64_t *a, uint64_t v) {
     atomicExch((unsigned long long *)a, (unsigned long long)v);
 }
 
+// Settled filter (dynamic shared memory, one bit per vertex pos below
+// p.fin_bits): a vertex expanded with distance below t_lo + w_min, t_lo the
+// start of the current bucket, holds its final key. Buckets below t_lo are
+// settled, so any later relaxation starts from a distance >= t_lo and offers
+// at least t_lo + w_min; hence no later candidate can lower (or tie) that
+// key, and a probe of a marked target skips its key load. Bits are set when a
+// vertex is expanded and cleared per tree; a probe that misses a fresh bit
+// only does a load it could have saved.
+extern __shared__ uint32_t fin_bitmap[];
+
 template <typename K>
 __device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t dv,
                                       bool lv, uint2 a, Probe<K> &q) {
     q.u = a.x;
+    q.live = false;
     const uint64_t nd = uint64_t(dv) + a.y;
     if (nd > key_dist_limit<K>()) {
         atomicExch(&p.flags[0], ERR_DIST_OVERFLOW);
         S.abort = 1;
-        q.live = false;
         return;
     }
+    if (q.u < p.fin_bits && ((fin_bitmap[q.u >> 5] >> (q.u & 31)) & 1u)) return;
     q.cand = make_key<K>(nd, lv);
     q.seen = __ldcg(&sl.key[q.u]);
     q.live = true;
 }
 
+// Commit, called by all 32 lanes of a warp (lanes without a live probe take
+// part with nothing to do): the atomicMin, then warp-aggregated appends to the
+// touched list, the bucket lists and far, and one update of cnt per warp.
 template <typename K>
 __device__ __forceinline__ void commit(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t h,
                                        const Probe<K> &q) {
-    if (q.cand >= q.seen) return;
+    const int lane = threadIdx.x & 31;
     const uint32_t u = q.u;
-    const K old = atomic_min_key(&sl.key[u], q.cand);
-    if (q.cand >= old) return;
-    if (old == key_inf<K>()) sl.touch[atomicAdd(&S.touch_n, 1u)] = u;
-    const uint32_t nb = key_dist(q.cand) / p.delta;
-    const bool f_new = nb > S.bcur && is_live(q.cand, u, h);
-    const bool f_old = old != key_inf<K>() && key_dist(old) / p.delta > S.bcur && is_live(old, u, h);
-    if (f_new != f_old) atomicAdd(&S.cnt, f_new ? 1 : -1);
-    if (nb == S.bcur) {
-        if (atomicExch(&sl.rtag[u], S.rid) != S.rid) {
-            uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
-            nxt[atomicAdd(&S.nxt_n, 1u)] = u;
+    bool imp = false;
+    K old = 0;
+    if (q.live && q.cand < q.seen) {
+        old = atomic_min_key(&sl.key[u], q.cand);
+        imp = q.cand < old;
+    }
+    if (!__any_sync(FULL, imp)) return;
+    const bool unreached = imp && old == key_inf<K>();
+    int dcnt = 0;
+    uint32_t cls = 0;  // 0 none, 1 nxt (current bucket), 2 window bucket, 3 far
+    uint32_t sx = NONE;
+    if (imp) {
+        const uint32_t nb = key_dist(q.cand) / p.delta;
+        const bool f_new = nb > S.bcur && is_live(q.cand, u, h);
+        const bool f_old = !unreached && key_dist(old) / p.delta > S.bcur && is_live(old, u, h);
+        dcnt = int(f_new) - int(f_old);
+        if (nb == S.bcur) {
+            if (atomicExch(&sl.rtag[u], S.rid) != S.rid) cls = 1;
+        } else if (key_dist(q.cand) < S.w_hi) {
+            if (unreached || key_dist(old) / p.delta != nb) {
+                cls = 2;
+                sx = nb - S.win_base;
+            }
+        } else if (unreached) {
+            cls = 3;
         }
-    } else if (key_dist(q.cand) < S.w_hi) {
-        sub_append(S, sl, p.n, u, nb);
-    } else if (atomicExch(&sl.ftag[u], S.fid) != S.fid) {
-        sl.far[atomicAdd(&S.far_n, 1u)] = u;
+    }
+    // touched: first finite key
+    unsigned m = __ballot_sync(FULL, unreached);
+    if (m) {
+        const int ld = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == ld) base = atomicAdd(&S.touch_n, (uint32_t)__popc(m));
+        base = __shfl_sync(FULL, base, ld);
+        if (unreached) sl.touch[base + __popc(m & ((1u << lane) - 1))] = u;
+    }
+    const int dsum = __reduce_add_sync(FULL, dcnt);
+    if (lane == 0 && dsum) atomicAdd(&S.cnt, dsum);
+    m = __ballot_sync(FULL, cls == 1);
+    if (m) {
+        const int ld = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == ld) base = atomicAdd(&S.nxt_n, (uint32_t)__popc(m));
+        base = __shfl_sync(FULL, base, ld);
+        uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
+        if (cls == 1) nxt[base + __popc(m & ((1u << lane) - 1))] = u;
+    }
+    m = __ballot_sync(FULL, cls == 3);
+    if (m) {
+        const int ld = __ffs(m) - 1;
+        uint32_t base = 0;
+        if (lane == ld) base = atomicAdd(&S.far_n, (uint32_t)__popc(m));
+        base = __shfl_sync(FULL, base, ld);
+        if (cls == 3) sl.far[base + __popc(m & ((1u << lane) - 1))] = u;
+    }
+    if (__any_sync(FULL, cls == 2)) {
+        // lanes joining the same window bucket share one counter update
+        const unsigned g = __match_any_sync(FULL, sx);
+        const int ld = __ffs(g) - 1;
+        uint32_t base = 0;
+        if (cls == 2 && lane == ld) base = atomicAdd(&S.sub_n[sx], (uint32_t)__popc(g));
+        base = __shfl_sync(FULL, base, ld);
+        if (cls == 2) sl.sub[size_t(sx) * p.n + base + __popc(g & ((1u << lane) - 1))] = u;
     }
 }
 
@@ -269,6 +332,8 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, c
                 deg = __ldg(&p.row[v + 1]) - rs;
                 lv = is_live(k, v, h);
                 if (lv) rs |= LIVE_BIT;
+                if (v < p.fin_bits && uint64_t(dv) < t_lo + p.w_min)
+                    atomicOr(&fin_bitmap[v >> 5], 1u << (v & 31));
                 ok = deg != 0;
                 ++expanded;
             }
@@ -371,8 +436,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, c
                     }
                 }
 #pragma unroll
-                for (int k = 0; k < UNROLL; ++k)
-                    if (pr[k].live) commit(p, S, sl, h, pr[k]);
+                for (int k = 0; k < UNROLL; ++k) commit(p, S, sl, h, pr[k]);
                 oa = ob;
             }
         }
@@ -412,9 +476,8 @@ __device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint
             u = sl.far[i];
             const uint32_t b = key_dist(__ldcg(&sl.key[u])) / p.delta;
             if (b < drop_below) {
-                sl.ftag[u] = 0;
+                // stale: lowered into the window (and listed there) or expanded
             } else if (move && b < win_end) {
-                sl.ftag[u] = 0;
                 sub_append(S, sl, p.n, u, b);
             } else {
                 keep = true;
@@ -424,9 +487,6 @@ __device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint
         __syncthreads();  // every entry of this chunk is read before any is rewritten
         warp_append(keep, u, sl.far, &S.out_n);
     }
-    // tag resets above are plain stores, while tags are later updated by
-    // atomics performed in L2: publish them device-wide before the barrier
-    __threadfence();
     __syncthreads();
     mn = warp_min(mn);
     if ((threadIdx.x & 31) == 0) atomicMin(&S.min_b, mn);
@@ -465,8 +525,6 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     Slot<K> sl;
     sl.key = (K *)p.key + so;
     sl.rtag = p.rtag + so;
-    sl.wtag = p.wtag + so;
-    sl.ftag = p.ftag + so;
     uint32_t *lb = p.lists + so * (4 + p.nwin);
     sl.l0 = lb;
     sl.l1 = lb + n;
@@ -477,8 +535,6 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     unsigned long long expanded = 0, arcs = 0, trivial = 0, trees = 0, rounds_all = 0, buckets = 0;
     if (threadIdx.x == 0) {
         S.rid = p.slot_ctr[blockIdx.x * 4 + 0];
-        S.bid_base = p.slot_ctr[blockIdx.x * 4 + 1];
-        S.fid = p.slot_ctr[blockIdx.x * 4 + 2];
     }
 
     for (;;) {
@@ -517,6 +573,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
         } else {
             // ---- tree search
             for (uint32_t s = threadIdx.x; s < p.nwin; s += TPB) S.sub_n[s] = 0;
+            for (uint32_t i = threadIdx.x; i < p.fin_words; i += TPB) fin_bitmap[i] = 0;
             if (threadIdx.x == 0) {
                 S.cur_n = 1;
                 S.nxt_n = 0;
@@ -525,10 +582,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 S.sel = 0;
                 S.cur_slot = NONE;
                 S.rid += 1;
-                S.fid += 1;
                 S.bcur = 0;
                 S.win_base = 0;
-                S.bid_top = p.nwin;
                 S.cnt = 0;
                 S.t_lo = 0;
                 S.t_hi = p.delta;
@@ -588,7 +643,6 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                     if (threadIdx.x == 0) {
                         S.win_base = S.min_b;
                         S.w_hi = uint64_t(S.win_base + p.nwin) * p.delta;
-                        if (S.win_base + p.nwin > S.bid_top) S.bid_top = S.win_base + p.nwin;
                         for (uint32_t s = 0; s < p.nwin; ++s) S.sub_n[s] = 0;
                     }
                     __syncthreads();
@@ -624,7 +678,6 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             // ---- label emission: live touched vertices, staged in l0 (vertex) / l1 (dist)
             if (threadIdx.x == 0) {
                 S.out_n = 0;
-                S.bid_base += S.bid_top + 2;  // fresh window tags for the next tree
             }
             __syncthreads();
             const uint32_t nt = S.touch_n;
@@ -705,30 +758,67 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
         atomicAdd(&p.stats[4], rounds_all);
         atomicAdd(&p.stats[5], buckets);
         p.slot_ctr[blockIdx.x * 4 + 0] = S.rid;
-        p.slot_ctr[blockIdx.x * 4 + 1] = S.bid_base;
-        p.slot_ctr[blockIdx.x * 4 + 2] = S.fid;
     }
+}
+
+// both key widths may take up to the opt-in maximum of dynamic shared memory
+template <typename F>
+cudaError_t allow_smem_of(F kernel, int optin) {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+    if (!e) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     optin - int(fa.sharedSizeBytes));
+    return e;
+}
+
+template <int TPB>
+cudaError_t allow_smem() {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (!e) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!e) e = allow_smem_of(plant_trees_kernel<TPB, uint32_t>, optin);
+    if (!e) e = allow_smem_of(plant_trees_kernel<TPB, uint64_t>, optin);
+    return e;
 }
 
 template <int TPB>
 cudaError_t launch_t(const TreeLaunch &p, int slots, cudaStream_t s) {
+    cudaError_t e = allow_smem<TPB>();
+    if (e) return e;
+    const size_t smem = size_t(p.fin_words) * 4;
     if (p.key_bytes == 4)
-        plant_trees_kernel<TPB, uint32_t><<<slots, TPB, 0, s>>>(p);
+        plant_trees_kernel<TPB, uint32_t><<<slots, TPB, smem, s>>>(p);
     else if (p.key_bytes == 8)
-        plant_trees_kernel<TPB, uint64_t><<<slots, TPB, 0, s>>>(p);
+        plant_trees_kernel<TPB, uint64_t><<<slots, TPB, smem, s>>>(p);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-// both key widths are built under the same register cap, so they share the
-// occupancy of the wide form
+// CTAs per SM with `words` bitmap words; both key widths are built under the
+// same register cap, the smaller of the two is returned
 template <int TPB>
-int occ() {
+int occ(uint32_t words) {
+    if (allow_smem<TPB>()) return 0;
     int b = 0, b4 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB, uint64_t>, TPB, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, plant_trees_kernel<TPB, uint32_t>, TPB, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB, uint64_t>, TPB, size_t(words) * 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, plant_trees_kernel<TPB, uint32_t>, TPB, size_t(words) * 4);
     return b < b4 ? b : b4;
+}
+
+// the largest bitmap (<= want words) that keeps the register-limited number
+// of CTAs per SM
+template <int TPB>
+uint32_t fin_words_t(uint32_t want) {
+    const int full = occ<TPB>(0);
+    if (full <= 0) return 0;
+    uint32_t lo = 0, hi = want;  // occ(lo) == full holds for lo = 0
+    if (occ<TPB>(hi) >= full) return hi;
+    while (hi - lo > 32) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (occ<TPB>(mid) >= full) lo = mid; else hi = mid;
+    }
+    return lo & ~31u;
 }
 
 }  // namespace
@@ -741,17 +831,32 @@ cudaError_t launch_plant_trees(const TreeLaunch &p, int tpt, int slots, cudaStre
         case 128: return launch_t<128>(p, slots, s);
         case 256: return launch_t<256>(p, slots, s);
         case 512: return launch_t<512>(p, slots, s);
+        case 1024: return launch_t<1024>(p, slots, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-int plant_max_slots_per_sm(int tpt) {
+int plant_max_slots_per_sm(int tpt, uint32_t fin_words) {
     switch (tpt) {
-        case 32: return occ<32>();
-        case 64: return occ<64>();
-        case 128: return occ<128>();
-        case 256: return occ<256>();
-        case 512: return occ<512>();
+        case 32: return occ<32>(fin_words);
+        case 64: return occ<64>(fin_words);
+        case 128: return occ<128>(fin_words);
+        case 256: return occ<256>(fin_words);
+        case 512: return occ<512>(fin_words);
+        case 1024: return occ<1024>(fin_words);
+        default: return 0;
+    }
+}
+
+uint32_t plant_fin_words(int tpt, uint32_t n) {
+    const uint32_t want = (n + 31) / 32;
+    switch (tpt) {
+        case 32: return fin_words_t<32>(want);
+        case 64: return fin_words_t<64>(want);
+        case 128: return fin_words_t<128>(want);
+        case 256: return fin_words_t<256>(want);
+        case 512: return fin_words_t<512>(want);
+        case 1024: return fin_words_t<1024>(want);
         default: return 0;
     }
 }

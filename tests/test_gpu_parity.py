@@ -126,7 +126,8 @@ def test_ba2k_host_memory_path(ba2k):
 
 @pytest.mark.parametrize("opts", [
     dict(threads_per_tree=32), dict(threads_per_tree=64), dict(threads_per_tree=256),
-    dict(threads_per_tree=512), dict(bucket_delta=1), dict(bucket_delta=1000),
+    dict(threads_per_tree=512), dict(threads_per_tree=1024), dict(bucket_delta=1),
+    dict(bucket_delta=1000),
     dict(window_buckets=2), dict(window_buckets=64, bucket_delta=1), dict(slots=1),
     dict(slots=7, threads_per_tree=32), dict(label_capacity=1), dict(mode=1),
     dict(mode=1, threads_per_tree=64), dict(flags=chl.CHL_FLAG_WIDE_KEYS),
@@ -158,7 +159,7 @@ def test_tuned_parameters_are_exact(ba2k):
     g, rank, ref = ba2k
     opts, rep = chl.tune(DG(g), dev(rank))
     assert rep["trials"] >= 3 and rep["sample_roots"] >= 1 and rep["best_tree_ms"] > 0
-    assert opts["threads_per_tree"] in (128, 256, 512) and opts["bucket_delta"] >= 1
+    assert opts["threads_per_tree"] in (128, 256, 512, 1024) and opts["bucket_delta"] >= 1
     _, off, hub, dist = gpu_labels(g, rank, **opts)
     assert_same(ref, off, hub, dist)
     fixed, _ = chl.tune(DG(g), dev(rank), bucket_delta=7)
