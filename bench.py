@@ -121,7 +121,7 @@ def cpu_oracle_estimate(g, rank, T, budget_s=20.0, threads=None):
     order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
     rng = np.random.default_rng(7)
     est, timed, spent = 0.0, 0, 0.0
-    per = max(threads, 16)
+    per = max(8 * threads, 64)
     for lo, hi in strata(n):
         k = min(per, hi - lo)
         pos = np.sort(rng.choice(np.arange(lo, hi), k, replace=False))
