@@ -189,77 +189,100 @@ __device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot
     q.live = true;
 }
 
-// Commit, called by all 32 lanes of a warp (lanes without a live probe take
-// part with nothing to do): the atomicMin, then warp-aggregated appends to the
-// touched list, the bucket lists and far, and one update of cnt per warp.
+// Commit of one warp step, called by all 32 lanes: the atomicMins of all
+// UNROLL probes are issued together (independent, so their round trips
+// overlap), then each lane classifies its improvements, and the appends to
+// the touched list, nxt and far take one shared atomic per warp and list, the
+// window buckets one per bucket, the live-pending count one per warp.
 template <typename K>
-__device__ __forceinline__ void commit(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t h,
-                                       const Probe<K> &q) {
+__device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
+                                            uint32_t h, const Probe<K> (&q)[UNROLL]) {
     const int lane = threadIdx.x & 31;
-    const uint32_t u = q.u;
-    bool imp = false;
-    K old = 0;
-    if (q.live && q.cand < q.seen) {
-        old = atomic_min_key(&sl.key[u], q.cand);
-        imp = q.cand < old;
+    const unsigned lt = (1u << lane) - 1;
+    K old[UNROLL];
+    bool imp[UNROLL];
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        imp[k] = false;
+        old[k] = 0;
+        if (q[k].live && q[k].cand < q[k].seen) old[k] = atomic_min_key(&sl.key[q[k].u], q[k].cand);
     }
-    if (!__any_sync(FULL, imp)) return;
-    const bool unreached = imp && old == key_inf<K>();
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        imp[k] = q[k].live && q[k].cand < q[k].seen && q[k].cand < old[k];
+        any |= imp[k];
+    }
+    if (!__any_sync(FULL, any)) return;
     int dcnt = 0;
-    uint32_t cls = 0;  // 0 none, 1 nxt (current bucket), 2 window bucket, 3 far
-    uint32_t sx = NONE;
-    if (imp) {
-        const uint32_t nb = key_dist(q.cand) / p.delta;
-        const bool f_new = nb > S.bcur && is_live(q.cand, u, h);
-        const bool f_old = !unreached && key_dist(old) / p.delta > S.bcur && is_live(old, u, h);
-        dcnt = int(f_new) - int(f_old);
-        if (nb == S.bcur) {
-            if (atomicExch(&sl.rtag[u], S.rid) != S.rid) cls = 1;
-        } else if (key_dist(q.cand) < S.w_hi) {
-            if (unreached || key_dist(old) / p.delta != nb) {
-                cls = 2;
-                sx = nb - S.win_base;
+    uint32_t cls[UNROLL];  // 0 none, 1 nxt (current bucket), 2 window bucket, 3 far, | 4 unreached
+    uint32_t sx[UNROLL];
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        cls[k] = 0;
+        sx[k] = NONE;
+        if (imp[k]) {
+            const uint32_t u = q[k].u;
+            const bool unreached = old[k] == key_inf<K>();
+            const uint32_t nb = key_dist(q[k].cand) / p.delta;
+            const bool f_new = nb > S.bcur && is_live(q[k].cand, u, h);
+            const bool f_old = !unreached && key_dist(old[k]) / p.delta > S.bcur && is_live(old[k], u, h);
+            dcnt += int(f_new) - int(f_old);
+            if (nb == S.bcur) {
+                if (atomicExch(&sl.rtag[u], S.rid) != S.rid) cls[k] = 1;
+            } else if (key_dist(q[k].cand) < S.w_hi) {
+                if (unreached || key_dist(old[k]) / p.delta != nb) {
+                    cls[k] = 2;
+                    sx[k] = nb - S.win_base;
+                }
+            } else if (unreached) {
+                cls[k] = 3;
             }
-        } else if (unreached) {
-            cls = 3;
+            if (unreached) cls[k] |= 4;
         }
-    }
-    // touched: first finite key
-    unsigned m = __ballot_sync(FULL, unreached);
-    if (m) {
-        const int ld = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == ld) base = atomicAdd(&S.touch_n, (uint32_t)__popc(m));
-        base = __shfl_sync(FULL, base, ld);
-        if (unreached) sl.touch[base + __popc(m & ((1u << lane) - 1))] = u;
     }
     const int dsum = __reduce_add_sync(FULL, dcnt);
     if (lane == 0 && dsum) atomicAdd(&S.cnt, dsum);
-    m = __ballot_sync(FULL, cls == 1);
-    if (m) {
-        const int ld = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == ld) base = atomicAdd(&S.nxt_n, (uint32_t)__popc(m));
-        base = __shfl_sync(FULL, base, ld);
-        uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
-        if (cls == 1) nxt[base + __popc(m & ((1u << lane) - 1))] = u;
+    // touched (first finite key), nxt and far: one reservation per list
+    unsigned mt[UNROLL], mn[UNROLL], mf[UNROLL];
+    uint32_t ct = 0, cn = 0, cf = 0;
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        mt[k] = __ballot_sync(FULL, (cls[k] & 4) != 0);
+        mn[k] = __ballot_sync(FULL, (cls[k] & 3) == 1);
+        mf[k] = __ballot_sync(FULL, (cls[k] & 3) == 3);
+        ct += __popc(mt[k]);
+        cn += __popc(mn[k]);
+        cf += __popc(mf[k]);
     }
-    m = __ballot_sync(FULL, cls == 3);
-    if (m) {
-        const int ld = __ffs(m) - 1;
-        uint32_t base = 0;
-        if (lane == ld) base = atomicAdd(&S.far_n, (uint32_t)__popc(m));
-        base = __shfl_sync(FULL, base, ld);
-        if (cls == 3) sl.far[base + __popc(m & ((1u << lane) - 1))] = u;
+    uint32_t bt = 0, bn = 0, bf = 0;
+    if (lane == 0) {
+        if (ct) bt = atomicAdd(&S.touch_n, ct);
+        if (cn) bn = atomicAdd(&S.nxt_n, cn);
+        if (cf) bf = atomicAdd(&S.far_n, cf);
     }
-    if (__any_sync(FULL, cls == 2)) {
-        // lanes joining the same window bucket share one counter update
-        const unsigned g = __match_any_sync(FULL, sx);
-        const int ld = __ffs(g) - 1;
-        uint32_t base = 0;
-        if (cls == 2 && lane == ld) base = atomicAdd(&S.sub_n[sx], (uint32_t)__popc(g));
-        base = __shfl_sync(FULL, base, ld);
-        if (cls == 2) sl.sub[size_t(sx) * p.n + base + __popc(g & ((1u << lane) - 1))] = u;
+    bt = __shfl_sync(FULL, bt, 0);
+    bn = __shfl_sync(FULL, bn, 0);
+    bf = __shfl_sync(FULL, bf, 0);
+    uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        const uint32_t u = q[k].u;
+        if (cls[k] & 4) sl.touch[bt + __popc(mt[k] & lt)] = u;
+        if ((cls[k] & 3) == 1) nxt[bn + __popc(mn[k] & lt)] = u;
+        if ((cls[k] & 3) == 3) sl.far[bf + __popc(mf[k] & lt)] = u;
+        bt += __popc(mt[k]);
+        bn += __popc(mn[k]);
+        bf += __popc(mf[k]);
+        if (__any_sync(FULL, (cls[k] & 3) == 2)) {
+            // lanes joining the same window bucket share one counter update
+            const unsigned g = __match_any_sync(FULL, sx[k]);
+            const int ld = __ffs(g) - 1;
+            uint32_t base = 0;
+            if ((cls[k] & 3) == 2 && lane == ld) base = atomicAdd(&S.sub_n[sx[k]], (uint32_t)__popc(g));
+            base = __shfl_sync(FULL, base, ld);
+            if ((cls[k] & 3) == 2) sl.sub[size_t(sx[k]) * p.n + base + __popc(g & lt)] = u;
+        }
     }
 }
 
@@ -435,8 +458,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, c
                         probe(p, S, sl, d[k], lvk[k], a[k], pr[k]);
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < UNROLL; ++k) commit(p, S, sl, h, pr[k]);
+                commit_step(p, S, sl, h, pr);
                 oa = ob;
             }
         }
