@@ -30,7 +30,7 @@ _LIB = os.path.join(_HERE, "libchloracle.so")
 _lock = threading.Lock()
 _lib = None
 
-METHODS = {"canonical": 0, "plant": 1, "pll": 2}
+METHODS = {"canonical": 0, "plant": 1, "pll": 2, "plant_clt": 3}
 
 
 def build(force: bool = False) -> str:
@@ -54,7 +54,7 @@ def _load():
         if _lib is None:
             lib = C.CDLL(build())
             vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
-            lib.orc_build.argtypes = [u32, vp, vp, vp, vp, i32, vp, u64, i32, u64,
+            lib.orc_build.argtypes = [u32, vp, vp, vp, vp, i32, vp, u64, i32, u64, u32,
                                       C.POINTER(_Labels), vp]
             lib.orc_labels_free.argtypes = [C.POINTER(_Labels)]
             lib.orc_query.argtypes = [u32, vp, vp, vp, vp, vp, u64, vp, i32]
@@ -91,9 +91,13 @@ def _u(a, dt):
 
 
 def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
-                 tie_seed: int = 0, with_stats: bool = False):
+                 tie_seed: int = 0, with_stats: bool = False, eta: int = 16):
     """Canonical labels of graph `g` (workloads.Graph or any object with n,
     row_ptr, col, w) under ranking `rank`.
+
+    method: "canonical" (the definition), "plant" (Algorithm 3), "pll"
+    (sequential Algorithm 1) or "plant_clt" (Algorithm 3 pruned by the Common
+    Label Table of the `eta` most important hubs, Sec. 4.3; eta is capped at n).
 
     roots: None = every vertex in descending rank; else only labels with hub
     in `roots` are produced (each tree is independent, Sec. 4.2).
@@ -114,7 +118,7 @@ def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
     out = _Labels()
     rc = lib.orc_build(n, row.ctypes.data, col.ctypes.data, w.ctypes.data, rank.ctypes.data,
                        METHODS[method], rptr, nroots if rarr is not None else 0,
-                       int(threads), int(tie_seed), C.byref(out),
+                       int(threads), int(tie_seed), min(int(eta), n), C.byref(out),
                        stats.ctypes.data if stats is not None else None)
     if rc != 0:
         raise RuntimeError(f"orc_build failed: {rc}")

@@ -29,6 +29,15 @@
  *   ORC_PLL        Algorithm 1 (pruned Dijkstra with rank queries) run
  *                  sequentially over roots in descending rank; sequential
  *                  PLL outputs the CHL (Sec. 3, proof of Claim 1).
+ *   ORC_PLANT_CLT  PLaNT with the Common Label Table of Sec. 4.3: first the
+ *                  trees of the eta most important roots (Algorithm 3, no
+ *                  pruning); their labels, for every vertex, form the table
+ *                  HC. Every other tree is Algorithm 3 in which a popped v is
+ *                  pruned (no label, no relaxation) when a distance query on
+ *                  HC, min over the table's hubs c of d(h,c) + d(c,v), is at
+ *                  most delta_v. Sec. 4.3 states the resulting labels are not
+ *                  redundant because HC holds all labels of every hub ranked
+ *                  above any hub it prunes with.
  *
  * After construction every L_v is sorted by hub rank (Algorithm 2, line
  * "sort labels in L_v using hub rank"), most important hub first.
@@ -46,6 +55,7 @@
 #define ORC_CANONICAL 0
 #define ORC_PLANT 1
 #define ORC_PLL 2
+#define ORC_PLANT_CLT 3
 
 #define INF64 UINT64_MAX
 
@@ -217,6 +227,11 @@ typedef struct {
     const uint32_t *col;
     const uint32_t *w;
     const uint32_t *rank;
+    /* Common Label Table (Sec. 4.3), or NULL: hc[v * eta + i] = d(v, c_i) when
+       (c_i, d) is a label of v, UINT32_MAX otherwise, c_i the vertex of rank
+       n-1-i (i = 0 most important) */
+    const uint32_t *hc;
+    uint32_t eta;
 } graph;
 
 typedef struct { uint64_t settled, arcs, labels; } root_stats;
@@ -281,11 +296,23 @@ static inline uint32_t argmax_rank(const graph *g, uint32_t x, uint32_t y) {
     return g->rank[x] >= g->rank[y] ? x : y;
 }
 
+/* distance query on the Common Label Table between h and v (Sec. 4.3) */
+static uint64_t hc_query(const graph *g, uint32_t h, uint32_t v) {
+    uint64_t best = INF64;
+    const uint32_t *a = g->hc + (uint64_t)h * g->eta, *b = g->hc + (uint64_t)v * g->eta;
+    for (uint32_t i = 0; i < g->eta; ++i)
+        if (a[i] != UINT32_MAX && b[i] != UINT32_MAX && (uint64_t)a[i] + b[i] < best)
+            best = (uint64_t)a[i] + b[i];
+    return best;
+}
+
 static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st) {
     uint64_t *delta = ws->dist;
     uint32_t *a = ws->anc;          /* a[v] = v for untouched v (ws_reset invariant) */
     const uint32_t Rh = g->rank[h];
     uint64_t settled = 0, arcs = 0, nl = 0;
+    /* pruning by the Common Label Table applies to trees of roots outside it */
+    const int prune = g->hc && g->n - 1 - Rh >= g->eta;
     /* line 1-2: delta_h = 0, a[h] = h; add h to Q; cnt = 1 */
     ws_touch(ws, h);
     delta[h] = 0;
@@ -299,6 +326,7 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
         settled++;
         uint32_t nA = argmax_rank(g, v, a[v]);                 /* nA = argmax_{x in {v,a[v]}} R(x) */
         if (a[v] == h) cnt--;
+        if (prune && hc_query(g, h, v) <= delta[v]) continue;  /* Sec. 4.3: pruned */
         if (g->rank[nA] <= Rh) {                               /* R[nA] > R[h]: no label */
             if (emit(ws, v, h, delta[v])) return;              /* L_v = L_v U {(h, delta_v)} */
             nl++;
@@ -482,18 +510,52 @@ static int assemble(const graph *g, tbuf *parts, int nparts, orc_labels *out) {
     return 0;
 }
 
+/* Trees of roots[0..nroots) on `threads` threads with dynamic root claiming;
+   each thread's (v, h, d) triples are returned in parts[threads]. */
+static int run_trees(const graph *g, int method, const uint32_t *roots, uint64_t nroots, int threads,
+                     uint64_t tie_seed, root_stats *stats, tbuf *parts, int *ovf) {
+    int rc = 0;
+    job j;
+    j.g = g; j.method = method; j.roots = roots; j.nroots = nroots;
+    atomic_init(&j.next, 0);
+    j.stats = stats; j.tie_seed = tie_seed;
+    worker *wk = (worker *)calloc((size_t)threads, sizeof(worker));
+    pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    if (!wk || !tid) { free(wk); free(tid); return -1; }
+    for (int t = 0; t < threads; ++t) {
+        wk[t].j = &j;
+        if (ws_init(&wk[t].ws, g->n, tie_seed)) rc = -1;
+    }
+    if (!rc) {
+        for (int t = 1; t < threads; ++t) pthread_create(&tid[t], NULL, run_worker, &wk[t]);
+        run_worker(&wk[0]);
+        for (int t = 1; t < threads; ++t) pthread_join(tid[t], NULL);
+    }
+    for (int t = 0; t < threads; ++t) {
+        if (wk[t].rc) rc = -1;
+        *ovf |= wk[t].ws.overflow;
+        parts[t] = wk[t].ws.out;
+        wk[t].ws.out.buf = NULL;
+        ws_free(&wk[t].ws);
+    }
+    free(wk); free(tid);
+    return rc;
+}
+
 /*
  * Build labels with hubs in roots[0..nroots) (all vertices for a full build).
  * threads >= 1 (PLL always runs on one thread, in the given root order, which
  * must be descending rank for Algorithm 1). stats (optional) is indexed like
- * roots. Returns 0, -1 on allocation failure, -3 on bad arguments.
+ * roots. eta: size of the Common Label Table for ORC_PLANT_CLT (1..n), else
+ * ignored. Returns 0, -1 on allocation failure, -3 on bad arguments.
  */
 int orc_build(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const uint32_t *w,
               const uint32_t *rank, int method, const uint32_t *roots, uint64_t nroots,
-              int threads, uint64_t tie_seed, orc_labels *out, root_stats *stats) {
+              int threads, uint64_t tie_seed, uint32_t eta, orc_labels *out, root_stats *stats) {
     memset(out, 0, sizeof(*out));
-    if (n == 0 || method < 0 || method > 2) return -3;
-    graph g = { n, row_ptr, col, w, rank };
+    if (n == 0 || method < 0 || method > 3) return -3;
+    if (method == ORC_PLANT_CLT && (eta < 1 || eta > n)) return -3;
+    graph g = { n, row_ptr, col, w, rank, NULL, 0 };
     uint32_t *own_roots = NULL;
     if (!roots) {
         /* all vertices in descending rank (the paper's task queue order) */
@@ -503,45 +565,75 @@ int orc_build(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const ui
         roots = own_roots;
         nroots = n;
     }
-    int rc = 0;
+    if (threads < 1) threads = 1;
+    int rc = 0, ovf = 0;
     if (method == ORC_PLL) {
         tbuf part = { 0 };
-        int ovf = 0;
         rc = build_pll(&g, roots, nroots, tie_seed, &part, stats, &ovf);
         if (!rc) rc = assemble(&g, &part, 1, out);
-        out->overflow = ovf;
         free(part.buf);
-    } else {
-        if (threads < 1) threads = 1;
-        job j;
-        j.g = &g; j.method = method; j.roots = roots; j.nroots = nroots;
-        atomic_init(&j.next, 0);
-        j.stats = stats; j.tie_seed = tie_seed;
-        worker *wk = (worker *)calloc((size_t)threads, sizeof(worker));
-        pthread_t *tid = (pthread_t *)calloc((size_t)threads, sizeof(pthread_t));
+    } else if (method != ORC_PLANT_CLT) {
         tbuf *parts = (tbuf *)calloc((size_t)threads, sizeof(tbuf));
-        if (!wk || !tid || !parts) { free(wk); free(tid); free(parts); free(own_roots); return -1; }
-        for (int t = 0; t < threads; ++t) {
-            wk[t].j = &j;
-            if (ws_init(&wk[t].ws, n, tie_seed)) rc = -1;
+        if (!parts) { free(own_roots); return -1; }
+        rc = run_trees(&g, method, roots, nroots, threads, tie_seed, stats, parts, &ovf);
+        if (!rc) rc = assemble(&g, parts, threads, out);
+        for (int t = 0; t < threads; ++t) free(parts[t].buf);
+        free(parts);
+    } else {
+        /* 1. trees of the eta most important vertices, unpruned (Algorithm 3) */
+        uint32_t *top = (uint32_t *)malloc((size_t)eta * sizeof(uint32_t));
+        root_stats *tst = (root_stats *)calloc((size_t)eta, sizeof(root_stats));
+        uint32_t *hc = (uint32_t *)malloc((size_t)n * eta * sizeof(uint32_t));
+        tbuf *p1 = (tbuf *)calloc((size_t)threads, sizeof(tbuf));
+        tbuf *p2 = (tbuf *)calloc((size_t)threads + 1, sizeof(tbuf));
+        uint32_t *rest = (uint32_t *)malloc((size_t)nroots * sizeof(uint32_t) + 4);
+        uint64_t *rest_at = (uint64_t *)malloc((size_t)nroots * sizeof(uint64_t) + 8);
+        root_stats *rst = stats ? (root_stats *)calloc((size_t)nroots + 1, sizeof(root_stats)) : NULL;
+        if (!top || !tst || !hc || !p1 || !p2 || !rest || !rest_at || (stats && !rst)) rc = -1;
+        if (!rc) {
+            for (uint32_t v = 0; v < n; ++v)
+                if (n - 1 - rank[v] < eta) top[n - 1 - rank[v]] = v;
+            rc = run_trees(&g, ORC_PLANT, top, eta, threads, tie_seed, tst, p1, &ovf);
         }
         if (!rc) {
-            for (int t = 1; t < threads; ++t) pthread_create(&tid[t], NULL, run_worker, &wk[t]);
-            run_worker(&wk[0]);
-            for (int t = 1; t < threads; ++t) pthread_join(tid[t], NULL);
+            /* 2. the Common Label Table: every label of those eta hubs */
+            for (size_t i = 0; i < (size_t)n * eta; ++i) hc[i] = UINT32_MAX;
+            for (int t = 0; t < threads; ++t)
+                for (size_t i = 0; i < p1[t].len; ++i) {
+                    const triple *x = &p1[t].buf[i];
+                    hc[(uint64_t)x->v * eta + (n - 1 - rank[x->hub])] = x->dist;
+                }
+            /* 3. every other requested tree, pruned by distance queries on HC */
+            uint64_t nrest = 0;
+            for (uint64_t i = 0; i < nroots; ++i)
+                if (n - 1 - rank[roots[i]] >= eta) { rest_at[nrest] = i; rest[nrest++] = roots[i]; }
+            g.hc = hc; g.eta = eta;
+            rc = run_trees(&g, ORC_PLANT, rest, nrest, threads, tie_seed, rst, p2, &ovf);
+            if (!rc && stats) {
+                for (uint64_t k = 0; k < nrest; ++k) stats[rest_at[k]] = rst[k];
+                for (uint64_t i = 0; i < nroots; ++i)
+                    if (n - 1 - rank[roots[i]] < eta) stats[i] = tst[n - 1 - rank[roots[i]]];
+            }
         }
-        int ovf = 0;
-        for (int t = 0; t < threads; ++t) {
-            if (wk[t].rc) rc = -1;
-            ovf |= wk[t].ws.overflow;
-            parts[t] = wk[t].ws.out;
-            wk[t].ws.out.buf = NULL;
+        if (!rc) {
+            /* requested labels: phase-3 trees plus the requested trees of phase 1 */
+            uint8_t *want = (uint8_t *)calloc(eta, 1);
+            if (!want) rc = -1;
+            for (uint64_t i = 0; !rc && i < nroots; ++i)
+                if (n - 1 - rank[roots[i]] < eta) want[n - 1 - rank[roots[i]]] = 1;
+            for (int t = 0; !rc && t < threads; ++t)
+                for (size_t i = 0; i < p1[t].len; ++i) {
+                    const triple *x = &p1[t].buf[i];
+                    if (want[n - 1 - rank[x->hub]] && tpush(&p2[threads], x->v, x->hub, x->dist)) rc = -1;
+                }
+            free(want);
+            if (!rc) rc = assemble(&g, p2, threads + 1, out);
         }
-        if (!rc) rc = assemble(&g, parts, threads, out);
-        out->overflow = ovf;
-        for (int t = 0; t < threads; ++t) { ws_free(&wk[t].ws); free(parts[t].buf); }
-        free(wk); free(tid); free(parts);
+        if (p1) for (int t = 0; t < threads; ++t) free(p1[t].buf);
+        if (p2) for (int t = 0; t <= threads; ++t) free(p2[t].buf);
+        free(top); free(tst); free(hc); free(p1); free(p2); free(rest); free(rest_at); free(rst);
     }
+    out->overflow = ovf;
     free(own_roots);
     if (rc) orc_labels_free(out);
     return rc;

@@ -79,3 +79,32 @@ def test_rmat18_sampled_parity():
 
 def test_grid512_sampled_parity():
     check_workload("grid512", 512)
+
+
+@pytest.mark.slow
+def test_rmat21_sampled_root_ranges():
+    """R-MAT scale 21 (1.24M vertices, 63.5M arcs): trees of sampled rank-position
+    ranges built by the GPU (root_begin/root_end, the sharded form) equal the
+    oracle's trees of the same roots, bit for bit; the distances they carry equal
+    Dijkstra's from those roots."""
+    g, rank = W.load("rmat21")
+    n = g.n
+    order = np.empty(n, np.uint32)
+    order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
+    G, R = DG(g), dev(rank)
+    A = csr_matrix((g.w.astype(np.float64), g.col.astype(np.int64), g.row_ptr.astype(np.int64)),
+                   shape=(n, n))
+    for rb, re in [(0, 48), (1000, 1032), (400_000, 400_256), (n - 256, n)]:
+        L = chl.build_labels(G, R, root_begin=rb, root_end=re)
+        off, hub, dist = L.to_numpy()
+        L.free()
+        ref = O.build_labels(g, rank, "plant", roots=order[rb:re], threads=16)
+        assert np.array_equal(off, ref.offsets)
+        assert np.array_equal(hub, ref.hub)
+        assert np.array_equal(dist, ref.dist)
+        # the label distances of the first root of the range are its Dijkstra distances
+        h = int(order[rb])
+        D = dijkstra(A, indices=[h])[0]
+        sel = hub == h
+        vert = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))[sel]
+        assert np.array_equal(dist[sel], D[vert].astype(np.uint32))

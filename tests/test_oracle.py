@@ -360,3 +360,59 @@ def test_overflow_flag():
     rank = np.array([3, 2, 1, 0], np.uint32)
     assert O.build_labels(g, rank, "plant").overflow
     assert not O.build_labels(from_edges(3, [(0, 1, 5), (1, 2, 5)]), rank[:3] - 1, "plant").overflow
+
+
+# ------------------------------------------------------------------ Common Label Table (Sec. 4.3)
+@pytest.mark.parametrize("name,g,rank", tiny_cases(), ids=[c[0] for c in tiny_cases()])
+@pytest.mark.parametrize("eta", [1, 2, 5])
+def test_common_label_table_brute_force(name, g, rank, eta):
+    """Pruning the trees with distance queries on the labels of the eta most
+    important hubs leaves the labeling equal to the definition."""
+    got = as_dict(O.build_labels(g, rank, "plant_clt", eta=eta))
+    assert got == brute_chl(g, rank)
+
+
+@pytest.mark.parametrize("eta", [1, 3])
+def test_common_label_table_fixtures(eta):
+    for fx in ("a1_counterexample.txt", "fig1_tie_fragment.txt"):
+        g, rank, _, _ = read_fixture(fx)
+        assert as_dict(O.build_labels(g, rank, "plant_clt", eta=eta)) == brute_chl(g, rank)
+
+
+@pytest.mark.parametrize("which", ["ba2k", "grid24", "rmat10"])
+@pytest.mark.parametrize("eta", [3, 16])
+def test_common_label_table_agrees_and_prunes(which, eta):
+    if which == "ba2k":
+        g, rank = W.load("ba2k")
+    elif which == "grid24":
+        g = W.grid(24, 55, seed=9)
+        rank = W.spt_count_rank(g, 16, seed=9)
+    else:
+        g = W.rmat(10, 8, seed=10, wlo=1, whi=20)
+        rank = W.degree_rank(g)
+    a, sa = O.build_labels(g, rank, "plant", threads=4, with_stats=True)
+    b, sb = O.build_labels(g, rank, "plant_clt", threads=4, eta=eta, with_stats=True)
+    assert np.array_equal(a.offsets, b.offsets)
+    assert np.array_equal(a.hub, b.hub)
+    assert np.array_equal(a.dist, b.dist)
+    assert (sb[:, 2] == sa[:, 2]).all()                  # labels per tree unchanged
+    n = g.n
+    pos = n - 1 - rank.astype(np.int64)
+    order = np.argsort(pos)
+    top = pos[order] < eta
+    assert (sb[top] == sa[top]).all()                    # top trees are not pruned
+    assert sb[:, 1].sum() < sa[:, 1].sum()               # the others scan fewer arcs
+
+
+def test_common_label_table_root_subset():
+    """Trees of roots outside the table still see the whole table."""
+    g, rank = W.load("ba2k")
+    full = O.build_labels(g, rank, "plant")
+    n = g.n
+    order = np.empty(n, np.uint32)
+    order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
+    for roots in (order[100:400], order[10:30], order[::9]):
+        part = O.build_labels(g, rank, "plant_clt", roots=roots, eta=16, threads=2)
+        keep = np.isin(full.hub, roots)
+        assert np.array_equal(part.hub, full.hub[keep])
+        assert np.array_equal(part.dist, full.dist[keep])
