@@ -111,6 +111,15 @@ typedef struct chl_labels chl_labels;
  *   label_capacity         initial size of the label buffer in labels; when
  *                          a tree does not fit, the buffer doubles and the
  *                          roots that did not fit are built again
+ *   common_hubs            eta of the Common Label Table (Sec. 4.3): the trees
+ *                          of the eta most important roots are built first and
+ *                          all their labels kept in a table; every other tree
+ *                          skips (no label, no relaxation) a vertex whose
+ *                          distance query on that table is at most its tree
+ *                          distance. The labels are unchanged. 0 = the paper's
+ *                          eta = 16; negative = no table; at most
+ *                          CHL_MAX_COMMON_HUBS. Requested trees of the eta
+ *                          most important roots are built unpruned.
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
@@ -127,7 +136,10 @@ typedef struct {
     int32_t mode;
     int32_t flags;
     uint64_t label_capacity;
+    int32_t common_hubs;
 } chl_build_opts;
+
+#define CHL_MAX_COMMON_HUBS 64
 
 
 /*
@@ -143,6 +155,7 @@ typedef struct {
  *   launches       kernels launched by the build
  *   rounds         expansion rounds of the tree searches (all trees)
  *   buckets        distance buckets entered after the first (all trees)
+ *   pruned         expansions cut by the Common Label Table (all trees)
  */
 typedef struct {
     uint64_t trees;
@@ -156,6 +169,7 @@ typedef struct {
     uint64_t launches;
     uint64_t rounds;
     uint64_t buckets;
+    uint64_t pruned;
 } chl_build_stats;
 
 /*

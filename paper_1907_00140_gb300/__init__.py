@@ -91,7 +91,7 @@ class chl_build_opts(C.Structure):
     _fields_ = [("root_begin", C.c_uint32), ("root_end", C.c_uint32),
                 ("threads_per_tree", C.c_int32), ("bucket_delta", C.c_int32),
                 ("window_buckets", C.c_int32), ("slots", C.c_int32), ("mode", C.c_int32),
-                ("flags", C.c_int32), ("label_capacity", C.c_uint64)]
+                ("flags", C.c_int32), ("label_capacity", C.c_uint64), ("common_hubs", C.c_int32)]
 
 
 class chl_tune_report(C.Structure):
@@ -106,7 +106,7 @@ class chl_build_stats(C.Structure):
     _fields_ = [("trees", C.c_uint64), ("labels", C.c_uint64), ("expanded", C.c_uint64),
                 ("arcs", C.c_uint64), ("trivial", C.c_uint64), ("build_ms", C.c_double),
                 ("tree_ms", C.c_double), ("sort_ms", C.c_double), ("launches", C.c_uint64),
-                ("rounds", C.c_uint64), ("buckets", C.c_uint64)]
+                ("rounds", C.c_uint64), ("buckets", C.c_uint64), ("pruned", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -47,7 +47,7 @@ struct Control {
     unsigned int failed_count;
     int flags[2];
     unsigned long long out_count;
-    unsigned long long stats[6];
+    unsigned long long stats[7];
 };
 
 struct Params {
@@ -56,6 +56,7 @@ struct Params {
     uint32_t nwin;
     int slots;
     int kb;  // bytes per tree key: 4 or 8
+    uint32_t eta;  // Common Label Table hubs (0 = no table)
     uint32_t fin_words;  // settled-filter bitmap words per CTA
     uint32_t w_min;
     uint32_t n;
@@ -80,6 +81,10 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     const bool narrow_fits = double(g.w_max) * double(g.n) <= double(0x7FFFFFFE);
     p.kb = (narrow_fits && !(o.flags & CHL_FLAG_WIDE_KEYS)) ? 4 : 8;
     p.fin_words = plant_fin_words(p.tpt, g.n);
+    {
+        const int want = o.common_hubs == 0 ? 16 : o.common_hubs;  // the paper's eta = 16
+        p.eta = want < 0 ? 0u : (uint32_t(want) < g.n ? uint32_t(want) : g.n);
+    }
     p.w_min = g.w_min ? g.w_min : 1;
     p.n = g.n;
     int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words);
@@ -144,6 +149,18 @@ struct SlotState {
     }
 };
 
+// Common Label Table (Sec. 4.3): all labels of the `hubs` most important
+// vertices, as a dense [n][stride] table of distances (all ones = no label).
+struct CommonTable {
+    DevBuf buf;
+    uint32_t hubs = 0, stride = 0;
+    void fill(TreeLaunch &tl) const {
+        tl.hc = (const uint32_t *)buf.p;
+        tl.hc_hubs = buf.p ? hubs : 0;
+        tl.hc_stride = stride;
+    }
+};
+
 }  // namespace
 }  // namespace chl
 
@@ -160,9 +177,78 @@ using namespace chl;
         }                                                                        \
     } while (0)
 
+namespace {
+
+// Build the Common Label Table: the trees of roots [0, P.eta), unpruned, into
+// a scratch label buffer (at most n labels per tree, so it always fits), then
+// one scatter of their records into the table.
+chl_status build_common_table(const RankGraph &rg, const Params &P, const SlotState &slot,
+                              cudaStream_t s, CommonTable &t, int *launches,
+                              unsigned long long *agg) {
+    chl_status st = CHL_OK;
+    const uint32_t n = rg.n;
+    DevBuf b_ov, b_oh, b_od, b_ctl, b_fail;
+    b_ov.s = b_oh.s = b_od.s = b_ctl.s = b_fail.s = t.buf.s = s;
+    const uint64_t cap = uint64_t(P.eta) * n + 1;
+    Control hc{};
+    Control *ctl = nullptr;
+    TreeLaunch tl{};
+    t.hubs = P.eta;
+    t.stride = (P.eta + 3) & ~3u;
+    CUDA_TRY(cudaMallocAsync(&t.buf.p, size_t(n) * t.stride * 4, s));
+    CUDA_TRY(cudaMemsetAsync(t.buf.p, 0xFF, size_t(n) * t.stride * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_ov.p, cap * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_oh.p, cap * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_fail.p, (size_t(P.eta) + 1) * 4, s));
+    CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
+    CUDA_TRY(cudaMemsetAsync(b_ctl.p, 0, sizeof(Control), s));
+    ctl = (Control *)b_ctl.p;
+    tl.n = n;
+    tl.row = rg.row;
+    tl.arc = rg.arc;
+    tl.vert_at = rg.vert_at;
+    tl.root_list = nullptr;
+    tl.root_begin = 0;
+    tl.root_count = P.eta;
+    slot.fill(P, n, tl);  // no table: these trees are not pruned
+    tl.out_v = (uint32_t *)b_ov.p;
+    tl.out_h = (uint32_t *)b_oh.p;
+    tl.out_d = (uint32_t *)b_od.p;
+    tl.out_cap = cap;
+    tl.out_count = &ctl->out_count;
+    tl.next_root = &ctl->next_root;
+    tl.failed = (uint32_t *)b_fail.p;
+    tl.failed_count = &ctl->failed_count;
+    tl.flags = ctl->flags;
+    tl.stats = ctl->stats;
+    CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
+    ++*launches;
+    CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hc.flags[0] == ERR_DIST_OVERFLOW) {
+        st = set_error(CHL_EOVERFLOW, "a shortest distance reaches UINT32_MAX");
+        goto done;
+    }
+    if (hc.flags[0] || hc.flags[1]) {
+        st = set_error(CHL_ETIMEOUT, "common label table trees failed (code %d)", hc.flags[0]);
+        goto done;
+    }
+    if (agg)
+        for (int k = 0; k < 7; ++k) agg[k] += hc.stats[k];
+    CUDA_TRY(launch_clt_fill((const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
+                             (const uint32_t *)b_od.p, hc.out_count, rg.pos_of, (uint32_t *)t.buf.p,
+                             t.stride, s));
+    ++*launches;
+done:
+    return st;
+}
+
+}  // namespace
+
 extern "C" const char *chl_last_error(void) { return g_err; }
 
-extern "C" const char *chl_version(void) { return "chl-gb300 0.1 (sm_103a)"; }
+extern "C" const char *chl_version(void) { return "chl-gb300 0.2 (sm_103a)"; }
 
 extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opts *opts,
                                 void *stream, chl_labels **out) {
@@ -187,6 +273,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (o.window_buckets && (o.window_buckets < 2 || o.window_buckets > 64))
         return set_error(CHL_EINVAL, "window_buckets must be in [2,64]");
     if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
+    if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
+        return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
     if (o.bucket_delta < 0 || o.slots < 0) return set_error(CHL_EINVAL, "negative option");
     if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS)) return set_error(CHL_EINVAL, "unknown bit in flags");
 
@@ -200,6 +288,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const uint32_t *d_col = g->col, *d_w = g->w, *d_rank = rank;
     DevBuf b_row, b_col, b_w, b_rank, b_ctl, b_ov, b_oh, b_od, b_fail, b_roots;
     SlotState slot;
+    CommonTable table;
     RankGraph rg;
     Params P{};
     Control hc{};
@@ -211,7 +300,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
     float ms_total = 0, ms_tree = 0, ms_sort = 0;
     chl_labels *L = nullptr;
-    unsigned long long agg[6] = {0, 0, 0, 0, 0, 0};
+    unsigned long long agg[7] = {0, 0, 0, 0, 0, 0, 0};
     std::vector<uint32_t> pending;  // roots still to build (after a full buffer)
     uint32_t claimed_upto = 0;
     bool first = true;
@@ -284,6 +373,11 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
 
     CUDA_TRY(cudaEventRecord(ev[1], s));
+    // the table is needed when some requested tree lies outside it
+    if (P.eta && re > P.eta) {
+        st = build_common_table(rg, P, slot, s, table, &launches, nullptr);
+        if (st != CHL_OK) goto done;
+    }
     for (int attempt = 0;; ++attempt) {
         TreeLaunch tl{};
         tl.n = n;
@@ -291,6 +385,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         tl.arc = rg.arc;
         tl.vert_at = rg.vert_at;
         slot.fill(P, n, tl);
+        table.fill(tl);
         tl.out_v = (uint32_t *)b_ov.p;
         tl.out_h = (uint32_t *)b_oh.p;
         tl.out_d = (uint32_t *)b_od.p;
@@ -339,7 +434,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         }
         CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaStreamSynchronize(s));
-        for (int k = 0; k < 6; ++k) agg[k] += hc.stats[k];
+        for (int k = 0; k < 7; ++k) agg[k] += hc.stats[k];
         if (hc.flags[0] == ERR_DIST_OVERFLOW) {
             st = set_error(CHL_EOVERFLOW, "a shortest distance reaches UINT32_MAX");
             goto done;
@@ -397,8 +492,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         }
     }
     CUDA_TRY(cudaEventRecord(ev[2], s));
-    // slot state is no longer needed: release it before assembly
+    // slot state and table are no longer needed: release them before assembly
     slot.release();
+    table.buf.release();
 
     CUDA_TRY(assemble_labels(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
                              (const uint32_t *)b_od.p, rg.vert_at, csr, &too_long, s, &launches));
@@ -432,6 +528,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     L->stats.trivial = agg[2];
     L->stats.rounds = agg[4];
     L->stats.buckets = agg[5];
+    L->stats.pruned = agg[6];
     L->stats.build_ms = ms_total;
     L->stats.tree_ms = ms_tree;
     L->stats.sort_ms = ms_sort;
@@ -612,8 +709,9 @@ namespace {
 // One trial: the tree kernel alone on a root list, with fresh slot state;
 // returns its device time (ms) or a negative value when the labels did not
 // fit the trial buffer.
-chl_status tree_trial(const RankGraph &rg, const Params &P, const uint32_t *roots, uint32_t count,
-                      uint64_t cap, cudaStream_t s, float *ms, unsigned long long *stats4) {
+chl_status tree_trial(const RankGraph &rg, const Params &P, const CommonTable &table,
+                      const uint32_t *roots, uint32_t count, uint64_t cap, cudaStream_t s, float *ms,
+                      unsigned long long *stats4) {
     chl_status st = CHL_OK;
     const uint32_t n = rg.n;
     DevBuf b_ctl, b_ov, b_oh, b_od, b_fail;
@@ -642,6 +740,7 @@ chl_status tree_trial(const RankGraph &rg, const Params &P, const uint32_t *root
     tl.root_begin = 0;
     tl.root_count = count;
     slot.fill(P, n, tl);
+    table.fill(tl);
     tl.out_v = (uint32_t *)b_ov.p;
     tl.out_h = (uint32_t *)b_oh.p;
     tl.out_d = (uint32_t *)b_od.p;
@@ -685,6 +784,8 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     chl_build_opts o{};
     if (base) o = *base;
     if (o.mode != 0) return set_error(CHL_EINVAL, "chl_tune tunes the batched mode (mode 0)");
+    if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
+        return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
     if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS)) return set_error(CHL_EINVAL, "unknown bit in flags");
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;
@@ -693,6 +794,7 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     const uint64_t *d_row = g->row_ptr;
     const uint32_t *d_col = g->col, *d_w = g->w, *d_rank = rank;
     DevBuf b_row, b_col, b_w, b_rank, b_roots;
+    CommonTable table;
     b_row.s = b_col.s = b_w.s = b_rank.s = b_roots.s = s;
     RankGraph rg;
     int launches = 0, dev = 0, sms = 0, trials = 0;
@@ -737,6 +839,13 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
         cap = uint64_t(K) * 256 + 4 * uint64_t(n);
         const uint64_t fit = uint64_t(0.15 * double(free_b)) / 12;
         if (cap > fit) cap = fit;
+        // the trials prune with the Common Label Table as the build will
+        if (p0.eta && n > p0.eta) {
+            SlotState ts;
+            CUDA_TRY(ts.alloc(p0, n, s));
+            st = build_common_table(rg, p0, ts, s, table, &launches, nullptr);
+            if (st != CHL_OK) goto done;
+        }
     }
     {
         // coordinate search: bucket width, then threads per tree, then window
@@ -773,7 +882,7 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
             uint64_t c = cap;
             chl_status r = CHL_OK;
             for (int a = 0; a < 4; ++a) {
-                r = tree_trial(rg, P, (const uint32_t *)b_roots.p, K, c, s, &ms, st4);
+                r = tree_trial(rg, P, table, (const uint32_t *)b_roots.p, K, c, s, &ms, st4);
                 if (r != CHL_OK || ms >= 0) break;
                 c *= 4;  // labels did not fit: a larger trial buffer
             }

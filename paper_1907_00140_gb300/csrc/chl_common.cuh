@@ -40,6 +40,12 @@ struct TreeLaunch {
     uint32_t w_min;     // lightest arc weight
     uint32_t fin_words; // settled-filter bitmap words in dynamic shared memory
     uint32_t fin_bits;  // vertices (pos) the bitmap covers: min(n, 32 * fin_words)
+    // Common Label Table (Sec. 4.3), or hc = null: hc[v * hc_stride + c] =
+    // d(v, c) for table hub c (pos c < hc_hubs) when (c, d) is a label of v,
+    // else all ones; hc_stride = hc_hubs rounded up to a multiple of 4
+    const uint32_t *hc;
+    uint32_t hc_hubs;
+    uint32_t hc_stride;
     // slot state: slot s owns [s*n, (s+1)*n) of each array
     void *key;          // tree keys, all ones when idle (see chl_tree.cu)
     int key_bytes;      // 4 (distances provably < 2^31 - 1) or 8
@@ -57,7 +63,7 @@ struct TreeLaunch {
     uint32_t *failed;          // roots whose labels did not fit
     unsigned int *failed_count;
     int *flags;                // [0] error code, [1] output full
-    unsigned long long *stats; // [0] expanded [1] arcs [2] trivial [3] trees [4] rounds [5] buckets
+    unsigned long long *stats; // [0] expanded [1] arcs [2] trivial [3] trees [4] rounds [5] buckets [6] pruned
 };
 
 enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2, ERR_RESERVE_LIMIT = 3 };
@@ -68,6 +74,10 @@ cudaError_t launch_plant_trees(const TreeLaunch &p, int threads_per_tree, int sl
 int plant_max_slots_per_sm(int threads_per_tree, uint32_t fin_words);
 // settled-filter words for n vertices that keep the CTAs per SM of fin_words = 0
 uint32_t plant_fin_words(int threads_per_tree, uint32_t n);
+// Common Label Table entries from label records of the table's trees
+cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
+                            unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
+                            uint32_t stride, cudaStream_t s);
 
 // label assembly (chl_labels.cu)
 struct LabelCSR {

@@ -55,6 +55,7 @@ constexpr uint32_t RESERVE_TRIES = 1u << 20;
 constexpr uint32_t NWIN_MAX = 64;
 constexpr int UNROLL = 4;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
+constexpr uint32_t CLT_MAX = 64;  // largest Common Label Table (hubs)
 
 // ------------------------------------------------------------------ keys
 // Vertices are numbered by rank position (pos 0 = most important), so in the
@@ -100,6 +101,8 @@ struct Shared {
     int ok;
     int live_sum;
     int fuse_live;         // the current list's first stage also counts its live entries
+    int prune;             // this tree prunes by the Common Label Table
+    uint32_t hch[CLT_MAX]; // table row of the root: d(h, c) per table hub c
     unsigned long long base;
     uint32_t sub_n[NWIN_MAX];
 };
@@ -327,9 +330,28 @@ __device__ __forceinline__ uint32_t owner(const Frontier<TPB> &F, uint64_t j, ui
 // row that covers i0 (the last row of the previous step). Lanes first load
 // UNROLL arcs, then UNROLL keys, then commit, so each lane has UNROLL
 // independent loads in flight at each stage.
+// Common Label Table pruning (Sec. 4.3): the distance query between the root
+// and v over the table hubs, min_c d(h, c) + d(c, v); the table row of v is
+// read as 16-byte vectors (rows are padded to a multiple of 4 hubs)
+__device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared &S, uint32_t v) {
+    const uint4 *row = reinterpret_cast<const uint4 *>(p.hc + size_t(v) * p.hc_stride);
+    uint64_t best = ~0ull;
+    for (uint32_t c4 = 0; c4 < p.hc_stride / 4; ++c4) {
+        const uint4 x = __ldg(&row[c4]);
+        const uint32_t b[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const uint32_t a = S.hch[c4 * 4 + j];
+            if (a != 0xFFFFFFFFu && b[j] != 0xFFFFFFFFu && uint64_t(a) + b[j] < best) best = uint64_t(a) + b[j];
+        }
+    }
+    return best;
+}
+
 template <int TPB, typename K>
 __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, const Slot<K> &sl,
-                             uint32_t h, unsigned long long &expanded, unsigned long long &arcs) {
+                             uint32_t h, unsigned long long &expanded, unsigned long long &arcs,
+                             unsigned long long &pruned) {
     constexpr int NW = TPB / 32;
     constexpr uint32_t STEP = 32 * UNROLL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -357,8 +379,15 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, c
                 if (lv) rs |= LIVE_BIT;
                 if (v < p.fin_bits && uint64_t(dv) < t_lo + p.w_min)
                     atomicOr(&fin_bitmap[v >> 5], 1u << (v & 31));
-                ok = deg != 0;
                 ++expanded;
+                if (S.prune && clt_query(p, S, v) <= dv) {
+                    // a table hub, which outranks h, lies on a shortest h-v path:
+                    // v gets no label and is not expanded (Sec. 4.3)
+                    ++pruned;
+                    deg = 0;
+                    if (k & 1) atomic_min_key(&sl.key[v], make_key<K>(dv, false));
+                }
+                ok = deg != 0;
             }
         }
         const unsigned okm = __ballot_sync(FULL, ok);
@@ -555,6 +584,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     sl.sub = lb + 4 * size_t(n);
 
     unsigned long long expanded = 0, arcs = 0, trivial = 0, trees = 0, rounds_all = 0, buckets = 0;
+    unsigned long long pruned = 0;
     if (threadIdx.x == 0) {
         S.rid = p.slot_ctr[blockIdx.x * 4 + 0];
     }
@@ -596,6 +626,13 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             // ---- tree search
             for (uint32_t s = threadIdx.x; s < p.nwin; s += TPB) S.sub_n[s] = 0;
             for (uint32_t i = threadIdx.x; i < p.fin_words; i += TPB) fin_bitmap[i] = 0;
+            // trees of roots outside the table prune with it; the table's own
+            // trees (which built it) do not
+            const bool prune = p.hc && h >= p.hc_hubs;
+            if (prune)
+                for (uint32_t c = threadIdx.x; c < p.hc_stride; c += TPB)
+                    S.hch[c] = __ldg(&p.hc[size_t(h) * p.hc_stride + c]);
+            if (threadIdx.x == 0) S.prune = prune;
             if (threadIdx.x == 0) {
                 S.cur_n = 1;
                 S.nxt_n = 0;
@@ -619,7 +656,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             __syncthreads();
             uint32_t rounds = 0;
             for (;;) {
-                expand_round<TPB, K>(p, S, F, sl, h, expanded, arcs);  // ends with a barrier
+                expand_round<TPB, K>(p, S, F, sl, h, expanded, arcs, pruned);  // ends with a barrier
                 if (S.abort) break;
                 ++rounds_all;
                 if (++rounds > MAX_ROUNDS_PER_TREE) {
@@ -769,10 +806,12 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     for (int o = 16; o; o >>= 1) {
         expanded += __shfl_xor_sync(FULL, expanded, o);
         arcs += __shfl_xor_sync(FULL, arcs, o);
+        pruned += __shfl_xor_sync(FULL, pruned, o);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&p.stats[0], expanded);
         atomicAdd(&p.stats[1], arcs);
+        if (pruned) atomicAdd(&p.stats[6], pruned);
     }
     if (threadIdx.x == 0) {
         atomicAdd(&p.stats[2], trivial);
@@ -881,6 +920,33 @@ uint32_t plant_fin_words(int tpt, uint32_t n) {
         case 1024: return fin_words_t<1024>(want);
         default: return 0;
     }
+}
+
+}  // namespace chl
+
+namespace chl {
+namespace {
+
+// Common Label Table from the labels of the table's own trees: record i is
+// (caller vertex out_v[i], hub pos out_h[i] < hubs, distance out_d[i])
+__global__ void clt_fill_kernel(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
+                                unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
+                                uint32_t stride) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
+         i += (unsigned long long)gridDim.x * blockDim.x)
+        hc[size_t(pos_of[out_v[i]]) * stride + out_h[i]] = out_d[i];
+}
+
+}  // namespace
+
+cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
+                            unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
+                            uint32_t stride, cudaStream_t s) {
+    if (!count) return cudaSuccess;
+    unsigned long long blocks = (count + 255) / 256;
+    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    clt_fill_kernel<<<unsigned(blocks), 256, 0, s>>>(out_v, out_h, out_d, count, pos_of, hc, stride);
+    return cudaGetLastError();
 }
 
 }  // namespace chl

@@ -131,6 +131,9 @@ def test_ba2k_host_memory_path(ba2k):
     dict(window_buckets=2), dict(window_buckets=64, bucket_delta=1), dict(slots=1),
     dict(slots=7, threads_per_tree=32), dict(label_capacity=1), dict(mode=1),
     dict(mode=1, threads_per_tree=64), dict(flags=chl.CHL_FLAG_WIDE_KEYS),
+    dict(common_hubs=-1), dict(common_hubs=1), dict(common_hubs=4), dict(common_hubs=64),
+    dict(common_hubs=64, bucket_delta=5, threads_per_tree=128),
+    dict(mode=1, common_hubs=8), dict(common_hubs=3, flags=chl.CHL_FLAG_WIDE_KEYS),
     dict(flags=chl.CHL_FLAG_WIDE_KEYS, threads_per_tree=64, bucket_delta=3),
 ], ids=lambda o: ",".join(f"{k}={v}" for k, v in o.items()))
 def test_ba2k_launch_configurations(ba2k, opts):
@@ -166,12 +169,24 @@ def test_tuned_parameters_are_exact(ba2k):
     assert fixed["bucket_delta"] == 7
 
 
+def test_common_label_table_prunes(ba2k):
+    """The table (Sec. 4.3) cuts expansions and arcs but not one label."""
+    g, rank, ref = ba2k
+    G, R = DG(g), dev(rank)
+    off_ = chl.build_labels(G, R, common_hubs=-1)
+    on_ = chl.build_labels(G, R, common_hubs=16)
+    a, b = off_.stats(), on_.stats()
+    assert a["pruned"] == 0 and b["pruned"] > 0
+    assert b["arcs"] < a["arcs"] and b["labels"] == a["labels"] == ref.total
+    assert_same(ref, *on_.to_numpy())
+
+
 def test_root_ranges_partition_labels_by_hub(ba2k):
     g, rank, ref = ba2k
     n = g.n
     order = np.empty(n, np.uint32)
     order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
-    for rb, re in [(0, 1), (0, 64), (64, 700), (700, n), (n - 1, n), (5, 5)]:
+    for rb, re in [(0, 1), (0, 64), (64, 700), (700, n), (n - 1, n), (5, 5), (10, 20), (16, 17)]:
         want = O.build_labels(g, rank, "plant", roots=order[rb:re])
         _, off, hub, dist = gpu_labels(g, rank, root_begin=rb, root_end=re)
         assert_same(want, off, hub, dist)
