@@ -156,6 +156,8 @@ typedef struct {
  *   rounds         expansion rounds of the tree searches (all trees)
  *   buckets        distance buckets entered after the first (all trees)
  *   pruned         expansions cut by the Common Label Table (all trees)
+ *   table_ms       device time of building the Common Label Table (its trees
+ *                  and the table fill; part of tree_ms), 0 without a table
  */
 typedef struct {
     uint64_t trees;
@@ -170,6 +172,7 @@ typedef struct {
     uint64_t rounds;
     uint64_t buckets;
     uint64_t pruned;
+    double table_ms;
 } chl_build_stats;
 
 /*

@@ -14,7 +14,11 @@ otherwise a stratified estimate: every one of the 64 most important roots,
 then rank-position strata of doubling width with `per_stratum` seeded roots
 each (mean x stratum size), with a standard error.
 
-Usage:  python oracle/work_units.py [workload ...]   (writes oracle/work_units.json)
+With the Common Label Table (Sec. 4.3) the trees explore less; the entry
+"<workload>/clt<eta>" holds S and A of Algorithm 3 pruned by the table of the
+eta most important hubs (the table's own trees included), same sampling.
+
+Usage:  python oracle/work_units.py [workload[/clt<eta>] ...]   (writes oracle/work_units.json)
 """
 import json
 import os
@@ -40,14 +44,16 @@ def strata(n):
     return list(zip(edges[:-1], edges[1:]))
 
 
-def units(name, per_stratum=96, threads=None, exact_below=5000, seed=1, pll_below=1_000_000):
+def units(name, per_stratum=96, threads=None, exact_below=5000, seed=1, pll_below=1_000_000,
+          eta=0):
     threads = threads or os.cpu_count()
     g, rank = W.load(name)
+    method = "plant_clt" if eta else "plant"
     n = g.n
     order = np.empty(n, np.uint32)
     order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
     t0 = time.time()
-    T_exact = n < pll_below
+    T_exact = n < pll_below and not eta
     T = O.build_labels(g, rank, "pll").total if T_exact else None
     t_pll = time.time() - t0
     rng = np.random.default_rng(seed)
@@ -60,7 +66,8 @@ def units(name, per_stratum=96, threads=None, exact_below=5000, seed=1, pll_belo
             pos = np.arange(lo, hi)
         else:
             pos = np.sort(rng.choice(np.arange(lo, hi), per_stratum, replace=False))
-        _, st = O.build_labels(g, rank, "plant", roots=order[pos], threads=threads, with_stats=True)
+        _, st = O.build_labels(g, rank, method, roots=order[pos], threads=threads, with_stats=True,
+                               eta=eta or 16)
         s, a = st[:, 0].astype(np.float64), st[:, 1].astype(np.float64)
         t = st[:, 2].astype(np.float64)
         k = len(pos)
@@ -79,8 +86,9 @@ def units(name, per_stratum=96, threads=None, exact_below=5000, seed=1, pll_belo
         "S": float(S), "A": float(A), "S_stderr": float(varS ** 0.5), "A_stderr": float(varA ** 0.5),
         "roots_sampled": int(sampled), "exact": bool(sampled == n),
         "method": ("T: sequential Algorithm 1; " if T_exact else "T, ") +
-                  "S, A: Algorithm 3 with early termination, "
-                  "stratified by rank position (all of the top 64, then doubling strata)",
+                  "S, A: Algorithm 3 with early termination" +
+                  (f", pruned by the Common Label Table of the {eta} most important hubs" if eta else "") +
+                  ", stratified by rank position (all of the top 64, then doubling strata)",
         "pll_seconds": round(t_pll, 1),
     }
     if not T_exact:
@@ -94,7 +102,8 @@ def main(names):
         data = json.load(open(OUT))
     for name in names:
         t = time.time()
-        data[name] = units(name)
+        base, _, clt = name.partition("/clt")
+        data[name] = units(base, eta=int(clt) if clt else 0)
         data[name]["seconds"] = round(time.time() - t, 1)
         print(name, json.dumps(data[name]), flush=True)
         with open(OUT, "w") as f:

@@ -297,8 +297,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     uint64_t cap = 0;
     uint64_t T = 0;
     int too_long = 0;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    float ms_total = 0, ms_tree = 0, ms_sort = 0;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    float ms_total = 0, ms_tree = 0, ms_sort = 0, ms_table = 0;
+    bool with_table = false;
     chl_labels *L = nullptr;
     unsigned long long agg[7] = {0, 0, 0, 0, 0, 0, 0};
     std::vector<uint32_t> pending;  // roots still to build (after a full buffer)
@@ -377,7 +378,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (P.eta && re > P.eta) {
         st = build_common_table(rg, P, slot, s, table, &launches, nullptr);
         if (st != CHL_OK) goto done;
+        with_table = true;
     }
+    CUDA_TRY(cudaEventRecord(ev[4], s));
     for (int attempt = 0;; ++attempt) {
         TreeLaunch tl{};
         tl.n = n;
@@ -507,6 +510,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     cudaEventElapsedTime(&ms_total, ev[0], ev[3]);
     cudaEventElapsedTime(&ms_tree, ev[1], ev[2]);
     cudaEventElapsedTime(&ms_sort, ev[2], ev[3]);
+    if (with_table) cudaEventElapsedTime(&ms_table, ev[1], ev[4]);
 
     L = new (std::nothrow) chl_labels;
     if (!L) {
@@ -532,6 +536,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     L->stats.build_ms = ms_total;
     L->stats.tree_ms = ms_tree;
     L->stats.sort_ms = ms_sort;
+    L->stats.table_ms = ms_table;
     L->stats.launches = uint64_t(launches);
     csr = LabelCSR{};
     *out = L;
