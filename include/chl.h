@@ -288,6 +288,102 @@ const char *chl_last_error(void);
 /* Library version string. */
 const char *chl_version(void);
 
+/* ====================================================================== serving
+ * A request loop on one GPU (the paper has no counterpart: it answers queries
+ * one at a time from resident labels, Sec. 5 QLSN). Label sets stay resident in
+ * device memory; PPSD queries that arrive while others are on the GPU are
+ * gathered into the next batch (continuous batching) of one launch that may mix
+ * label sets, with up to `query_slots` batches in flight on their own streams;
+ * build requests run on worker threads and streams beside the queries and are
+ * admitted in arrival order once their estimated device memory fits.
+ */
+typedef struct chl_server chl_server;
+
+/*
+ * Server options. Zero-initialise; 0 selects the default.
+ *   query_slots        batches in flight at once (default 3; each has its own
+ *                      stream and pinned staging)
+ *   max_batch          pairs per batch (default 1048576); a request larger than
+ *                      this is rejected
+ *   batching           0 = continuous batching (default); 1 = plain: one launch
+ *                      per request, each waited for before the next (the
+ *                      baseline the batching is measured against)
+ *   build_workers      builds that may run at once (default 2)
+ *   build_slots        tree slots of a build run by the server when the request
+ *                      does not set opts.slots (default: SMs - 16, so that
+ *                      query batches keep SMs while trees run)
+ *   build_budget       bytes that running builds may hold by their estimate
+ *                      (default: free device memory at creation minus 4 GiB)
+ */
+typedef struct {
+    int32_t query_slots;
+    uint64_t max_batch;
+    int32_t batching;
+    int32_t build_workers;
+    int32_t build_slots;
+    uint64_t build_budget;
+} chl_server_opts;
+
+/* Counters since creation: batches launched, pairs answered, largest batch,
+   builds admitted and finished, and the peak sum of admitted build estimates. */
+typedef struct {
+    uint64_t batches;
+    uint64_t pairs;
+    uint64_t max_batch_seen;
+    uint64_t builds_done;
+    uint64_t builds_failed;
+    uint64_t build_bytes_peak;
+} chl_server_stats;
+
+/* Start a server on the current device (threads and streams are created).
+   Errors: CHL_EINVAL, CHL_ENOMEM, CHL_ECUDA. */
+chl_status chl_server_create(const chl_server_opts *opts, chl_server **out);
+
+/* Make a label set resident for queries; *set_id receives its id (0, 1, ...,
+   at most 4096 sets). L stays owned by the caller and must outlive every query
+   on it. Call before submitting queries on it. */
+chl_status chl_server_add_set(chl_server *S, const chl_labels *L, uint32_t *set_id);
+
+/* Queue `count` pairs (host uint32 [count][2], caller vertex ids of the set)
+   for answers into host `out[count]`; both arrays must stay valid until the
+   ticket completes. Ids are checked here: CHL_EINVAL for an id >= n, an unknown
+   set, or count > max_batch. */
+chl_status chl_server_submit_query(chl_server *S, uint32_t set_id, const uint32_t *pairs,
+                                   uint64_t count, uint32_t *out, uint64_t *ticket);
+
+/* Queue a build (as chl_build; g, rank and their arrays must stay valid until
+   the ticket completes). Admitted in arrival order when its estimate (graph,
+   slot state, labels at 256 per vertex) fits the budget and free memory. */
+chl_status chl_server_submit_build(chl_server *S, const chl_csr *g, const uint32_t *rank,
+                                   const chl_build_opts *opts, uint64_t *ticket);
+
+/* Wait for a ticket (timeout_s < 0: no limit; CHL_ETIMEOUT when it runs out,
+   the ticket stays valid). On completion returns the request's status, its
+   latency from submission in *latency_s (optional) and, for a build, the new
+   labels in *built (optional; owned by the caller, else freed). A ticket can be
+   waited for once. */
+chl_status chl_server_wait(chl_server *S, uint64_t ticket, double timeout_s, chl_labels **built,
+                           double *latency_s);
+
+/*
+ * Open-loop replay: request i (pairs[pair_off[i] .. pair_off[i+1]) of set
+ * set_of[i]) arrives arrival_s[i] seconds after the call starts (non-decreasing
+ * times). The batcher takes every request that has arrived when a batch slot
+ * frees, exactly as for submitted requests; latency_s[i] = completion -
+ * arrival, answers into out[pair_off[i] ..]. *wall_s receives the time from the
+ * start to the last completion. Submitted requests and builds keep being served
+ * during the replay. Host arrays.
+ */
+chl_status chl_server_replay(chl_server *S, uint64_t nreq, const double *arrival_s,
+                             const uint32_t *set_of, const uint64_t *pair_off,
+                             const uint32_t *pairs, uint32_t *out, double *latency_s, double *wall_s);
+
+chl_status chl_server_stats_get(const chl_server *S, chl_server_stats *stats);
+
+/* Finish every queued request, stop the threads and free the server (NULL is
+   allowed). Label sets added stay owned by the caller. */
+void chl_server_destroy(chl_server *S);
+
 #ifdef __cplusplus
 }
 #endif

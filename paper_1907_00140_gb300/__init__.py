@@ -23,7 +23,7 @@ import threading
 import numpy as np
 
 __all__ = [
-    "build", "lib", "CHL_OK", "CHL_EINVAL", "CHL_ENOMEM", "CHL_ECUDA", "CHL_ETIMEOUT",
+    "build", "lib", "Server", "CHL_OK", "CHL_EINVAL", "CHL_ENOMEM", "CHL_ECUDA", "CHL_ETIMEOUT",
     "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "ChlError", "chl_csr", "chl_build_opts",
     "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
     "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
@@ -34,7 +34,8 @@ __all__ = [
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
-_SOURCES = ["chl_api.cu", "chl_graph.cu", "chl_tree.cu", "chl_labels.cu", "chl_query.cu"]
+_SOURCES = ["chl_api.cu", "chl_graph.cu", "chl_tree.cu", "chl_labels.cu", "chl_query.cu",
+            "chl_serve.cu"]
 LIB_PATH = os.path.join(_HERE, "libchl.so")
 ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -102,6 +103,21 @@ class chl_tune_report(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class chl_server_opts(C.Structure):
+    _fields_ = [("query_slots", C.c_int32), ("max_batch", C.c_uint64), ("batching", C.c_int32),
+                ("build_workers", C.c_int32), ("build_slots", C.c_int32),
+                ("build_budget", C.c_uint64)]
+
+
+class chl_server_stats(C.Structure):
+    _fields_ = [("batches", C.c_uint64), ("pairs", C.c_uint64), ("max_batch_seen", C.c_uint64),
+                ("builds_done", C.c_uint64), ("builds_failed", C.c_uint64),
+                ("build_bytes_peak", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class chl_build_stats(C.Structure):
     _fields_ = [("trees", C.c_uint64), ("labels", C.c_uint64), ("expanded", C.c_uint64),
                 ("arcs", C.c_uint64), ("trivial", C.c_uint64), ("build_ms", C.c_double),
@@ -150,6 +166,22 @@ def lib():
             L.chl_last_error.restype = C.c_char_p
             L.chl_version.argtypes = []
             L.chl_version.restype = C.c_char_p
+            L.chl_server_create.argtypes = [C.POINTER(chl_server_opts), C.POINTER(vp)]
+            L.chl_server_add_set.argtypes = [vp, vp, C.POINTER(u32)]
+            L.chl_server_submit_query.argtypes = [vp, u32, vp, u64, vp, C.POINTER(u64)]
+            L.chl_server_submit_build.argtypes = [vp, C.POINTER(chl_csr), vp,
+                                                  C.POINTER(chl_build_opts), C.POINTER(u64)]
+            L.chl_server_wait.argtypes = [vp, u64, C.c_double, C.POINTER(vp),
+                                          C.POINTER(C.c_double)]
+            L.chl_server_replay.argtypes = [vp, u64, vp, vp, vp, vp, vp, vp,
+                                            C.POINTER(C.c_double)]
+            L.chl_server_stats_get.argtypes = [vp, C.POINTER(chl_server_stats)]
+            L.chl_server_destroy.argtypes = [vp]
+            L.chl_server_destroy.restype = None
+            for f in ("chl_server_create", "chl_server_add_set", "chl_server_submit_query",
+                      "chl_server_submit_build", "chl_server_wait", "chl_server_replay",
+                      "chl_server_stats_get"):
+                getattr(L, f).restype = i32
             _lib = L
     return _lib
 
@@ -350,3 +382,84 @@ def build_labels(g, rank, stream: int | None = None, **opts) -> Labels:
 
 def query(labels: Labels, pairs, **kw):
     return labels.query(pairs, **kw)
+
+
+# ------------------------------------------------------------------ serving loop
+class Server:
+    """Owner of a chl_server: resident label sets, continuous batching of
+    queries, builds admitted by device memory (see include/chl.h)."""
+
+    def __init__(self, **opts):
+        o = chl_server_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        h = C.c_void_p()
+        _check(lib().chl_server_create(C.byref(o), C.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().chl_server_destroy(self.handle)
+            self.handle = None
+            self._keep = {}
+
+    def add_set(self, labels: "Labels") -> int:
+        k = C.c_uint32()
+        _check(lib().chl_server_add_set(self.handle, labels.handle, C.byref(k)))
+        self._keep[("set", k.value)] = labels
+        return k.value
+
+    def submit_query(self, set_id: int, pairs) -> int:
+        """Queue host pairs [q,2]; wait() returns the answers."""
+        p = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+        out = np.empty(len(p), np.uint32)
+        t = C.c_uint64()
+        _check(lib().chl_server_submit_query(self.handle, set_id, p.ctypes.data, len(p),
+                                             out.ctypes.data, C.byref(t)))
+        self._keep[t.value] = (p, out)
+        return t.value
+
+    def submit_build(self, g, rank, **opts) -> int:
+        """Queue a build from host arrays; wait() returns its Labels."""
+        csr, rkp, keep = _csr_args(g, rank)
+        o = chl_build_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        t = C.c_uint64()
+        _check(lib().chl_server_submit_build(self.handle, C.byref(csr), rkp, C.byref(o), C.byref(t)))
+        self._keep[t.value] = (csr, keep, o)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """(answers or Labels, latency seconds) of a finished ticket."""
+        built = C.c_void_p()
+        lat = C.c_double()
+        st = lib().chl_server_wait(self.handle, ticket, timeout, C.byref(built), C.byref(lat))
+        kept = self._keep.pop(ticket, None) if st != CHL_ETIMEOUT else None
+        _check(st)
+        if built.value:
+            return Labels(built.value), lat.value
+        return kept[1], lat.value
+
+    def replay(self, arrival_s, set_of, pair_off, pairs):
+        """Open-loop replay; returns (answers, latency seconds per request, wall seconds)."""
+        arr = np.ascontiguousarray(arrival_s, np.float64)
+        so = np.ascontiguousarray(set_of, np.uint32)
+        off = np.ascontiguousarray(pair_off, np.uint64)
+        p = np.ascontiguousarray(pairs, np.uint32).reshape(-1, 2)
+        out = np.empty(len(p), np.uint32)
+        lat = np.empty(len(arr), np.float64)
+        wall = C.c_double()
+        _check(lib().chl_server_replay(self.handle, len(arr), arr.ctypes.data, so.ctypes.data,
+                                       off.ctypes.data, p.ctypes.data, out.ctypes.data,
+                                       lat.ctypes.data, C.byref(wall)))
+        return out, lat, wall.value
+
+    def stats(self) -> dict:
+        st = chl_server_stats()
+        _check(lib().chl_server_stats_get(self.handle, C.byref(st)))
+        return st.as_dict()

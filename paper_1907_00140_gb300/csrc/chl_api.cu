@@ -12,17 +12,6 @@
 
 #include "chl_common.cuh"
 
-struct chl_labels {
-    uint32_t n = 0;
-    uint64_t total = 0;
-    uint64_t *offsets = nullptr;
-    uint32_t *hub = nullptr;
-    uint32_t *hubpos = nullptr;
-    uint32_t *dist = nullptr;
-    uint64_t bytes = 0;
-    chl_build_stats stats{};
-    int device = 0;
-};
 
 namespace chl {
 

@@ -7,6 +7,19 @@
 
 #include "../../include/chl.h"
 
+// the labels object behind the opaque ABI handle
+struct chl_labels {
+    uint32_t n = 0;
+    uint64_t total = 0;
+    uint64_t *offsets = nullptr;
+    uint32_t *hub = nullptr;
+    uint32_t *hubpos = nullptr;
+    uint32_t *dist = nullptr;
+    uint64_t bytes = 0;
+    chl_build_stats stats{};
+    int device = 0;
+};
+
 namespace chl {
 
 // ------------------------------------------------------------------ graph in rank order
@@ -97,6 +110,17 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
 cudaError_t launch_query(uint32_t n, const uint64_t *offsets, const uint32_t *hubpos,
                          const uint32_t *dist, const uint32_t *pairs, uint64_t q, uint32_t *out,
                          int *bad, cudaStream_t s);
+// one resident label set as the query kernels read it
+struct QuerySet {
+    uint32_t n;
+    const uint64_t *offsets;
+    const uint32_t *hubpos;
+    const uint32_t *dist;
+};
+// a batch whose pair i asks set set_of[i] (sets: device array of nsets)
+cudaError_t launch_query_sets(const QuerySet *sets, uint32_t nsets, const uint32_t *pairs,
+                              const uint16_t *set_of, uint64_t q, uint32_t *out, int *bad,
+                              int max_blocks, cudaStream_t s);
 
 // exclusive prefix sum of n uint64 values (out may alias in); chl_graph.cu
 cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,

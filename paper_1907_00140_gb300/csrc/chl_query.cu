@@ -21,6 +21,51 @@ constexpr unsigned FULL = 0xffffffffu;
 
 __device__ __forceinline__ uint64_t min64(uint64_t a, uint64_t b) { return a < b ? a : b; }
 
+// d(u, v) by one warp (all 32 lanes call it with the same u, v)
+__device__ __forceinline__ uint32_t merge_query(const uint64_t *__restrict__ off,
+                                                const uint32_t *__restrict__ hp,
+                                                const uint32_t *__restrict__ dd, uint32_t u,
+                                                uint32_t v) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t a0 = __ldg(&off[u]), la = __ldg(&off[u + 1]) - a0;
+    const uint64_t b0 = __ldg(&off[v]), lb = __ldg(&off[v + 1]) - b0;
+    uint64_t ia = 0, ib = 0;
+    uint64_t best = 0xFFFFFFFFull;
+    while (ia < la && ib < lb) {
+        const bool va = ia + lane < la, vb = ib + lane < lb;
+        const uint32_t x = va ? __ldg(&hp[a0 + ia + lane]) : 0xFFFFFFFFu;
+        const uint32_t y = vb ? __ldg(&hp[b0 + ib + lane]) : 0xFFFFFFFFu;
+        // largest lane l with y[l] <= x (y ascending across lanes)
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int c = o + step;
+            if (__shfl_sync(FULL, y, c) <= x) o = c;
+        }
+        const uint32_t yo = __shfl_sync(FULL, y, o);
+        const bool hit = va && yo == x;
+        const unsigned hits = __ballot_sync(FULL, hit);
+        if (hits) {
+            // fetch both distances only for matching lanes
+            uint64_t s = 0xFFFFFFFFull;
+            if (hit) s = uint64_t(__ldg(&dd[a0 + ia + lane])) + __ldg(&dd[b0 + ib + o]);
+            best = min64(best, s);
+        }
+        const uint32_t lastA = __shfl_sync(FULL, x, int(min64(la - ia, 32) - 1));
+        const uint32_t lastB = __shfl_sync(FULL, y, int(min64(lb - ib, 32) - 1));
+        if (lastA <= lastB) {
+            ia += min64(la - ia, 32);
+            ib += __popc(__ballot_sync(FULL, vb && y <= lastA));
+        } else {
+            ib += min64(lb - ib, 32);
+            ia += __popc(__ballot_sync(FULL, va && x <= lastB));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) best = min64(best, __shfl_xor_sync(FULL, best, o));
+    return uint32_t(min64(best, 0xFFFFFFFFull));
+}
+
 __global__ void query_kernel(uint32_t n, const uint64_t *__restrict__ off,
                              const uint32_t *__restrict__ hp, const uint32_t *__restrict__ dd,
                              const uint32_t *__restrict__ pairs, uint64_t q,
@@ -36,47 +81,45 @@ __global__ void query_kernel(uint32_t n, const uint64_t *__restrict__ off,
             }
             continue;
         }
-        const uint64_t a0 = __ldg(&off[u]), la = __ldg(&off[u + 1]) - a0;
-        const uint64_t b0 = __ldg(&off[v]), lb = __ldg(&off[v + 1]) - b0;
-        uint64_t ia = 0, ib = 0;
-        uint64_t best = 0xFFFFFFFFull;
-        while (ia < la && ib < lb) {
-            const bool va = ia + lane < la, vb = ib + lane < lb;
-            const uint32_t x = va ? __ldg(&hp[a0 + ia + lane]) : 0xFFFFFFFFu;
-            const uint32_t y = vb ? __ldg(&hp[b0 + ib + lane]) : 0xFFFFFFFFu;
-            // largest lane l with y[l] <= x (y ascending across lanes)
-            int o = 0;
-#pragma unroll
-            for (int step = 16; step >= 1; step >>= 1) {
-                const int c = o + step;
-                if (__shfl_sync(FULL, y, c) <= x) o = c;
+        const uint32_t d = merge_query(off, hp, dd, u, v);
+        if (lane == 0) out[i] = d;
+    }
+}
+
+// a batch mixing label sets: pair i asks set set_of[i]
+__global__ void query_sets_kernel(const QuerySet *__restrict__ sets, uint32_t nsets,
+                                  const uint32_t *__restrict__ pairs,
+                                  const uint16_t *__restrict__ set_of, uint64_t q,
+                                  uint32_t *__restrict__ out, int *bad) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t i = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < q; i += warps) {
+        const uint32_t u = __ldg(&pairs[2 * i]), v = __ldg(&pairs[2 * i + 1]);
+        const uint32_t k = __ldg(&set_of[i]);
+        const QuerySet S = sets[k < nsets ? k : 0];
+        if (k >= nsets || u >= S.n || v >= S.n) {
+            if (lane == 0) {
+                out[i] = 0xFFFFFFFFu;
+                atomicExch(bad, 1);
             }
-            const uint32_t yo = __shfl_sync(FULL, y, o);
-            const bool hit = va && yo == x;
-            const unsigned hits = __ballot_sync(FULL, hit);
-            if (hits) {
-                // fetch both distances only for matching lanes
-                uint64_t s = 0xFFFFFFFFull;
-                if (hit) s = uint64_t(__ldg(&dd[a0 + ia + lane])) + __ldg(&dd[b0 + ib + o]);
-                best = min64(best, s);
-            }
-            const uint32_t lastA = __shfl_sync(FULL, x, int(min64(la - ia, 32) - 1));
-            const uint32_t lastB = __shfl_sync(FULL, y, int(min64(lb - ib, 32) - 1));
-            if (lastA <= lastB) {
-                ia += min64(la - ia, 32);
-                ib += __popc(__ballot_sync(FULL, vb && y <= lastA));
-            } else {
-                ib += min64(lb - ib, 32);
-                ia += __popc(__ballot_sync(FULL, va && x <= lastB));
-            }
+            continue;
         }
-#pragma unroll
-        for (int o = 16; o; o >>= 1) best = min64(best, __shfl_xor_sync(FULL, best, o));
-        if (lane == 0) out[i] = uint32_t(min64(best, 0xFFFFFFFFull));
+        const uint32_t d = merge_query(S.offsets, S.hubpos, S.dist, u, v);
+        if (lane == 0) out[i] = d;
     }
 }
 
 }  // namespace
+
+cudaError_t launch_query_sets(const QuerySet *sets, uint32_t nsets, const uint32_t *pairs,
+                              const uint16_t *set_of, uint64_t q, uint32_t *out, int *bad,
+                              int max_blocks, cudaStream_t s) {
+    if (q == 0) return cudaSuccess;
+    uint64_t blocks = (q * 32 + 255) / 256;
+    if (blocks > uint64_t(max_blocks)) blocks = uint64_t(max_blocks);
+    query_sets_kernel<<<unsigned(blocks), 256, 0, s>>>(sets, nsets, pairs, set_of, q, out, bad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_query(uint32_t n, const uint64_t *offsets, const uint32_t *hubpos,
                          const uint32_t *dist, const uint32_t *pairs, uint64_t q, uint32_t *out,

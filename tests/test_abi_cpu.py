@@ -46,6 +46,26 @@ def test_null_arguments_are_einval(lib):
     assert lib.chl_labels_info(None, None, None, None) == chl.CHL_EINVAL
     assert lib.chl_tune(None, None, None, None, None, None) == chl.CHL_EINVAL
     lib.chl_labels_free(None)
+    # serving entry points
+    assert lib.chl_server_create(None, None) == chl.CHL_EINVAL
+    t = C.c_uint64()
+    assert lib.chl_server_add_set(None, None, None) == chl.CHL_EINVAL
+    assert lib.chl_server_submit_query(None, 0, None, 0, None, C.byref(t)) == chl.CHL_EINVAL
+    assert lib.chl_server_submit_build(None, None, None, None, C.byref(t)) == chl.CHL_EINVAL
+    assert lib.chl_server_wait(None, 1, 0.0, None, None) == chl.CHL_EINVAL
+    assert lib.chl_server_replay(None, 0, None, None, None, None, None, None, None) == chl.CHL_EINVAL
+    assert lib.chl_server_stats_get(None, None) == chl.CHL_EINVAL
+    lib.chl_server_destroy(None)
+
+
+def test_bad_server_options_are_einval(lib):
+    h = C.c_void_p()
+    for field, val in [("query_slots", -1), ("query_slots", 17), ("batching", 2),
+                       ("build_workers", 99), ("max_batch", 1 << 27)]:
+        o = chl.chl_server_opts()
+        setattr(o, field, val)
+        assert lib.chl_server_create(C.byref(o), C.byref(h)) == chl.CHL_EINVAL, field
+        assert h.value is None
 
 
 def test_bad_options_are_einval(lib):
