@@ -34,6 +34,10 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the serving leg runs query batches and builds on separate streams: give each
+# stream its own hardware queue (read at context creation), so that a query
+# batch is never queued behind a persistent tree kernel of another stream
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 WORKLOAD_TEXT = {
     "rmat18": "R-MAT scale 18, edge factor 16, a=0.57 b=c=0.19, symmetrised, dedup, LCC; "
@@ -183,6 +187,96 @@ def metric_name(name):
     return f"CHL build labels/s (batched PLaNT, {name}) + PPSD query batch"
 
 
+def make_stream(sets, lam, duration, seed):
+    """Open-loop Poisson query stream at lam queries/s over `duration` seconds:
+    requests of geometric size (mean max(1, lam / 1e6) pairs, so at most about
+    a million requests per second), each on a label set chosen uniformly, its
+    pairs half uniform, half with both endpoints drawn by degree."""
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    mean = max(1.0, lam / 1e6)
+    nreq = max(1, int(round(duration * lam / mean)))
+    arr = np.cumsum(rng.exponential(mean / lam, nreq))
+    sizes = rng.geometric(1.0 / mean, nreq) if mean > 1 else np.ones(nreq, np.int64)
+    set_of = rng.integers(0, len(sets), nreq).astype(np.uint32)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    pairs = np.empty((int(off[-1]), 2), np.uint32)
+    for k, (g, _L) in enumerate(sets):
+        sel = np.repeat(set_of == k, sizes)
+        q = int(sel.sum())
+        if not q:
+            continue
+        half = q // 2
+        pk = np.concatenate([W.uniform_pairs(g.n, half, seed + 17 * k),
+                             W.degree_pairs(g, q - half, seed + 17 * k + 1)])
+        pairs[sel] = pk[rng.permutation(q)]
+    return arr, set_of, off, pairs
+
+
+def run_serving(chl, sets, rates, duration, builds, seed=40):
+    """Serving loop under open-loop Poisson load: continuous batching vs the
+    plain one-launch-per-request server, and a run with the 8 Barabasi-Albert
+    build requests arriving during the stream."""
+    import threading
+    import workloads as W
+    out = {"sets": [g.name for g, _ in sets], "rates": []}
+
+    def one(server, lam, dur, sd):
+        arr, so, off, pairs = make_stream(sets, lam, dur, sd)
+        before = server.stats()
+        ans, lat, wall = server.replay(arr, so, off, pairs)
+        after = server.stats()
+        nb = after["batches"] - before["batches"]
+        return {"offered_qps": lam, "queries": int(off[-1]), "requests": len(arr),
+                "achieved_qps": float(off[-1]) / max(wall, 1e-9), "wall_s": wall,
+                "p50_us": float(np.percentile(lat, 50) * 1e6),
+                "p99_us": float(np.percentile(lat, 99) * 1e6),
+                "p999_us": float(np.percentile(lat, 99.9) * 1e6),
+                "max_us": float(lat.max() * 1e6), "max_at_s": float(arr[int(lat.argmax())]),
+                "batches": int(nb), "mean_batch": float(off[-1]) / max(nb, 1)}, (ans, so, off, pairs)
+
+    S = chl.Server(query_slots=3)
+    for _, L in sets:
+        S.add_set(L)
+    one(S, 1e6, 0.02, seed)  # warm-up
+    for i, lam in enumerate(rates):
+        r, _ = one(S, lam, duration, seed + i)
+        out["rates"].append(r)
+    # builds arriving during a stream at 10M queries/s
+    bgs = [W.serving_ba(i) for i in range(builds)]
+    tickets, lat_b = [], []
+    lam, dur = 1e7, max(duration, 0.5)
+
+    def submit():
+        for i, (g, r) in enumerate(bgs):
+            time.sleep(dur / max(builds, 1))
+            tickets.append(S.submit_build(g, r))
+    th = threading.Thread(target=submit)
+    th.start()
+    r, _ = one(S, lam, dur, seed + 99)
+    th.join()
+    for t in tickets:
+        Lb, lt = S.wait(t)
+        lat_b.append(lt)
+        Lb.free()
+    r["builds"] = {"count": len(tickets), "graphs_n": [g.n for g, _ in bgs],
+                   "latency_s": [round(x, 4) for x in lat_b]}
+    out["with_builds"] = r
+    out["server"] = S.stats()
+    S.close()
+    # plain: one launch per request, each waited for before the next
+    P = chl.Server(batching=1)
+    for _, L in sets:
+        P.add_set(L)
+    plain = []
+    for lam, dur in ((2e4, 0.25), (1e6, 0.02)):
+        r, _ = one(P, lam, dur, seed + 7)
+        plain.append(r)
+    P.close()
+    out["plain"] = plain
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +287,14 @@ def main():
     ap.add_argument("--queries", type=int, default=1_000_000)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/cpu/e2e legs")
+    ap.add_argument("--serve-sets", default="main",
+                    help="label sets resident in the serving run: 'main' (the bench build) "
+                         "and/or workload names, comma separated (e.g. main,rmat21)")
+    ap.add_argument("--serve-duration", type=float, default=0.1,
+                    help="seconds of Poisson arrivals per offered rate")
+    ap.add_argument("--serve-builds", type=int, default=8)
+    ap.add_argument("--serve-only", action="store_true",
+                    help="build the serving sets and run only the serving leg")
     ap.add_argument("--case", default=None,
                     help="profiling case: one build of the roots at rank positions [b, b+count), "
                          "given as b:count; prints its counters and exits")
@@ -248,6 +350,13 @@ def main():
         tune_rep = {"trials": 0, "sample_roots": 0}
     else:
         opts, tune_rep = chl.tune(DG, R)
+    if args.serve_only:
+        L = chl.build_labels(DG, R, **opts)
+        res = {"metric": "serving", "config": {"workload": name, "tuned": opts},
+               "serving": serving_leg(args, chl, g, L, DG, R)}
+        L.free()
+        print(json.dumps(res), flush=True)
+        return
     if args.case:
         b, c = (int(x) for x in args.case.split(":"))
         torch.cuda.synchronize(dev)
@@ -423,10 +532,47 @@ def main():
                                          f"stratified by rank position ({spent_c:.1f} s of CPU "
                                          f"work), scaled by stratum size; est. full build "
                                          f"{est_c:.1f} s"}
+    if not args.no_extras and rank_id == 0:
+        res["serving"] = serving_leg(args, chl, g, L, DG, R)
     L.free()
     print(json.dumps(res), flush=True)
     if pg:
         pg.barrier()
+
+
+def serving_leg(args, chl, g, L, DG, R):
+    """Serving run over the bench's labels and any extra workloads' labels."""
+    import workloads as W
+    sets, extra, builds_info = [], [], []
+    for nm in args.serve_sets.split(","):
+        if nm == "main":
+            sets.append((g, L))
+            continue
+        g2, r2 = W.load(nm)
+        t0 = time.perf_counter()
+        o2, rep2 = chl.tune(g2, r2)
+        t1 = time.perf_counter()
+        L2 = chl.build_labels(g2, r2, **o2)
+        t2 = time.perf_counter()
+        st2 = L2.stats()
+        builds_info.append({"workload": nm, "n": g2.n, "arcs": g2.num_arcs, "tuned": o2,
+                            "tune_s": t1 - t0, "build_wall_s": t2 - t1,
+                            "build_ms": st2["build_ms"], "tree_ms": st2["tree_ms"],
+                            "table_ms": st2["table_ms"], "sort_ms": st2["sort_ms"],
+                            "labels": L2.total, "label_bytes": L2.nbytes,
+                            "expanded": st2["expanded"], "arcs_relaxed": st2["arcs"],
+                            "pruned": st2["pruned"]})
+        extra.append(L2)
+        sets.append((g2, L2))
+    t0 = time.perf_counter()
+    out = run_serving(chl, sets, [1e6, 3e6, 1e7, 3e7, 1e8], args.serve_duration, args.serve_builds)
+    out["leg_s"] = time.perf_counter() - t0
+    out["label_sets"] = [{"workload": gg.name, "n": gg.n, "labels": LL.total, "bytes": LL.nbytes}
+                         for gg, LL in sets]
+    out["extra_builds"] = builds_info
+    for x in extra:
+        x.free()
+    return out
 
 
 if __name__ == "__main__":

@@ -296,6 +296,11 @@ const char *chl_version(void);
  * label sets, with up to `query_slots` batches in flight on their own streams;
  * build requests run on worker threads and streams beside the queries and are
  * admitted in arrival order once their estimated device memory fits.
+ * Streams share the device's hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS,
+ * 8 by default, read when the CUDA context is created): with fewer queues than
+ * streams, a query batch can wait behind a build's persistent tree kernel that
+ * landed in the same queue. Set CUDA_DEVICE_MAX_CONNECTIONS=32 in the
+ * environment before the process first uses CUDA.
  */
 typedef struct chl_server chl_server;
 
@@ -309,9 +314,11 @@ typedef struct chl_server chl_server;
  *                      per request, each waited for before the next (the
  *                      baseline the batching is measured against)
  *   build_workers      builds that may run at once (default 2)
- *   build_slots        tree slots of a build run by the server when the request
- *                      does not set opts.slots (default: SMs - 16, so that
- *                      query batches keep SMs while trees run)
+ *   build_slots        SMs that running builds may hold together: a build
+ *                      whose request sets neither opts.slots nor
+ *                      opts.threads_per_tree runs build_slots / build_workers
+ *                      slots of 1024 threads (one per SM). Default SMs - 16,
+ *                      so that query batches keep SMs while trees run.
  *   build_budget       bytes that running builds may hold by their estimate
  *                      (default: free device memory at creation minus 4 GiB)
  */

@@ -59,7 +59,7 @@ struct Params {
 // bucket rounds.
 Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_t free_bytes) {
     Params p;
-    p.tpt = o.threads_per_tree ? o.threads_per_tree : 256;
+    p.tpt = o.threads_per_tree ? o.threads_per_tree : 1024;
     const double mean_deg = g.n ? double(g.m2) / double(g.n) : 0.0;
     const double dflt = mean_deg >= 8.0 ? g.w_mean / 128.0 : 2.0 * g.w_mean;
     uint32_t d = o.bucket_delta > 0 ? uint32_t(o.bucket_delta) : uint32_t(dflt);

@@ -267,12 +267,14 @@ void chl_server::run_builder() {
     for (;;) {
         Req *r = nullptr;
         {
+            // free memory is read outside the lock: the driver call must not
+            // hold up the batcher
+            size_t fr = 0, tot = 0;
+            cudaMemGetInfo(&fr, &tot);
             std::unique_lock<std::mutex> lk(mu);
             for (;;) {
                 if (!bq.empty()) {
                     Req *h = bq.front();
-                    size_t fr = 0, tot = 0;
-                    cudaMemGetInfo(&fr, &tot);
                     const bool fits_budget = running_est + h->est <= o.build_budget || running_est == 0;
                     const bool fits_free = h->est + (uint64_t(1) << 30) <= fr || running_est == 0;
                     if (fits_budget && fits_free) {
@@ -286,6 +288,9 @@ void chl_server::run_builder() {
                     break;
                 }
                 cv_b.wait_for(lk, std::chrono::milliseconds(1));
+                lk.unlock();
+                cudaMemGetInfo(&fr, &tot);
+                lk.lock();
             }
         }
         if (!r) break;
@@ -415,7 +420,14 @@ extern "C" chl_status chl_server_submit_build(chl_server *S, const chl_csr *g, c
     r->g = *g;
     r->rank = rank;
     if (opts) r->bo = *opts;
-    if (!r->bo.slots) r->bo.slots = S->o.build_slots;
+    // one 1024-thread tree slot per SM; the build workers share build_slots
+    // SMs so that running builds never hold every SM and query batches keep
+    // the rest (tree CTAs are persistent: an SM they hold stays theirs)
+    if (!r->bo.threads_per_tree && !r->bo.slots) r->bo.threads_per_tree = 1024;
+    if (!r->bo.slots) {
+        r->bo.slots = S->o.build_slots / S->o.build_workers;
+        if (r->bo.slots < 1) r->bo.slots = 1;
+    }
     // estimate: inputs and rank-ordered copy, slot state at 32 window buckets,
     // 256 labels per vertex in the build buffer and in the final CSR
     const double n = g->n, m = double(g->num_arcs);
