@@ -175,19 +175,22 @@ __device__ __forceinline__ void atomic_set_key(uint64_t *a, uint64_t v) {
 // only does a load it could have saved.
 extern __shared__ uint32_t fin_bitmap[];
 
+// kv = make_key(dv, lv) of the expanded vertex: the candidate through arc
+// (u, w) is kv + 2w (the clean bit rides along in bit 0). With 4-byte keys
+// the host has proven every tentative distance below the key limit
+// (w_max * n < 2^31 - 1), so only the wide form checks for overflow.
 template <typename K>
-__device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint32_t dv,
-                                      bool lv, uint2 a, Probe<K> &q) {
+__device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot<K> &sl, K kv,
+                                      uint2 a, Probe<K> &q) {
     q.u = a.x;
     q.live = false;
-    const uint64_t nd = uint64_t(dv) + a.y;
-    if (nd > key_dist_limit<K>()) {
+    if (sizeof(K) == 8 && uint64_t(key_dist(kv)) + a.y > key_dist_limit<K>()) {
         atomicExch(&p.flags[0], ERR_DIST_OVERFLOW);
         S.abort = 1;
         return;
     }
     if (q.u < p.fin_bits && ((fin_bitmap[q.u >> 5] >> (q.u & 31)) & 1u)) return;
-    q.cand = make_key<K>(nd, lv);
+    q.cand = kv + (K(a.y) << 1);
     q.seen = __ldcg(&sl.key[q.u]);
     q.live = true;
 }
@@ -297,20 +300,18 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, cons
 // and a thousand short rows alike). Every staged row has at least one arc
 // (a zero-degree vertex is never expanded: it is unreachable or a trivial
 // root), so row starts are distinct flat positions.
-template <int TPB>
+template <int TPB, typename K>
 struct Frontier {
-    uint64_t rs[TPB];
-    uint64_t pre[TPB];
-    uint32_t dv[TPB];
+    uint64_t base[TPB];  // row start minus degree prefix: arc index = base + flat position
+    uint64_t pre[TPB];   // exclusive degree prefix
+    K kv[TPB];           // make_key(distance, liveness) of the row's vertex
     uint32_t wrows[TPB / 32];
     uint64_t wdeg[TPB / 32];
 };
 
-constexpr uint64_t LIVE_BIT = 1ull << 63;
-
 // largest o in [lo, hi) with pre[o] <= j, given pre[lo] <= j
-template <int TPB>
-__device__ __forceinline__ uint32_t owner(const Frontier<TPB> &F, uint64_t j, uint32_t lo,
+template <int TPB, typename K>
+__device__ __forceinline__ uint32_t owner(const Frontier<TPB, K> &F, uint64_t j, uint32_t lo,
                                           uint32_t hi) {
     while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
@@ -349,7 +350,7 @@ __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared 
 }
 
 template <int TPB, typename K>
-__device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, const Slot<K> &sl,
+__device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, const Slot<K> &sl,
                              uint32_t h, unsigned long long &expanded, unsigned long long &arcs,
                              unsigned long long &pruned) {
     constexpr int NW = TPB / 32;
@@ -376,7 +377,6 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, c
                 rs = __ldg(&p.row[v]);
                 deg = __ldg(&p.row[v + 1]) - rs;
                 lv = is_live(k, v, h);
-                if (lv) rs |= LIVE_BIT;
                 if (v < p.fin_bits && uint64_t(dv) < t_lo + p.w_min)
                     atomicOr(&fin_bitmap[v >> 5], 1u << (v & 31));
                 ++expanded;
@@ -425,9 +425,10 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, c
         }
         if (ok) {
             const uint32_t c = rl + __popc(okm & ((1u << lane) - 1));
-            F.rs[c] = rs;
-            F.dv[c] = dv;
-            F.pre[c] = dl + inc - deg;
+            const uint64_t pre = dl + inc - deg;
+            F.base[c] = rs - pre;  // wraps: base + position = rs + (position - pre)
+            F.kv[c] = make_key<K>(dv, lv);
+            F.pre[c] = pre;
         }
         const uint64_t total = da;
         const uint32_t nrows = ra;
@@ -441,52 +442,58 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB> &F, c
             uint32_t oa = owner(F, lo, 0, nrows);
             for (uint64_t i0 = lo; i0 < hi; i0 += STEP) {
                 const uint32_t span = hi - i0 < STEP ? uint32_t(hi - i0) : STEP;  // positions in this step
-                // start positions (1..span-1) of rows oa+1, oa+2, ... inside the step
-                uint32_t wm[UNROLL];
-#pragma unroll
-                for (int k = 0; k < UNROLL; ++k) wm[k] = 0;
-                uint32_t ob = oa;
-                for (;;) {
-                    const uint32_t o = ob + 1 + lane;
-                    uint32_t q = STEP;
-                    if (o < nrows) {
-                        const uint64_t st = F.pre[o];
-                        if (st < i0 + span) q = uint32_t(st - i0);
-                    }
-                    const unsigned m = __ballot_sync(FULL, q < STEP);
-#pragma unroll
-                    for (int k = 0; k < UNROLL; ++k)
-                        wm[k] |= __reduce_or_sync(FULL, (q >> 5) == uint32_t(k) ? 1u << (q & 31) : 0u);
-                    ob += __popc(m);
-                    if (m != FULL) break;
-                }
-                uint32_t cum[UNROLL];
-                cum[0] = 0;
-#pragma unroll
-                for (int k = 1; k < UNROLL; ++k) cum[k] = cum[k - 1] + __popc(wm[k - 1]);
                 uint2 a[UNROLL];
-                uint32_t d[UNROLL];
-                bool lvk[UNROLL];
+                K kv[UNROLL];
+                uint32_t ob = oa;
+                const uint64_t next = oa + 1 < nrows ? F.pre[oa + 1] : ~0ull;
+                if (next >= i0 + span) {
+                    // the whole step lies in row oa (long rows: hubs)
+                    const uint64_t base = F.base[oa] + i0;
+                    const K k0 = F.kv[oa];
 #pragma unroll
-                for (int k = 0; k < UNROLL; ++k) {
-                    const uint32_t q = k * 32 + lane;
-                    if (q < span) {
-                        const uint32_t o = oa + cum[k] + __popc(wm[k] & ((2u << lane) - 1u));
-                        const uint64_t r = F.rs[o];
-                        d[k] = F.dv[o];
-                        lvk[k] = (r & LIVE_BIT) != 0;
-                        a[k] = __ldg(&p.arc[(r & ~LIVE_BIT) + (i0 + q - F.pre[o])]);
+                    for (int k = 0; k < UNROLL; ++k) {
+                        const uint32_t q = k * 32 + lane;
+                        kv[k] = k0;
+                        if (q < span) a[k] = __ldg(&p.arc[base + q]);
+                    }
+                } else {
+                    // start positions (0..span-1) of rows oa+1, oa+2, ... inside the step
+                    uint32_t wm[UNROLL];
+#pragma unroll
+                    for (int k = 0; k < UNROLL; ++k) wm[k] = 0;
+                    for (;;) {
+                        const uint32_t o = ob + 1 + lane;
+                        uint32_t q = STEP;
+                        if (o < nrows) {
+                            const uint64_t st = F.pre[o];
+                            if (st < i0 + span) q = uint32_t(st - i0);
+                        }
+                        const unsigned m = __ballot_sync(FULL, q < STEP);
+#pragma unroll
+                        for (int k = 0; k < UNROLL; ++k)
+                            wm[k] |= __reduce_or_sync(FULL, (q >> 5) == uint32_t(k) ? 1u << (q & 31) : 0u);
+                        ob += __popc(m);
+                        if (m != FULL) break;
+                    }
+                    uint32_t cum = 0;
+#pragma unroll
+                    for (int k = 0; k < UNROLL; ++k) {
+                        const uint32_t q = k * 32 + lane;
+                        if (q < span) {
+                            const uint32_t o = oa + cum + __popc(wm[k] & ((2u << lane) - 1u));
+                            kv[k] = F.kv[o];
+                            a[k] = __ldg(&p.arc[F.base[o] + i0 + q]);
+                        }
+                        cum += __popc(wm[k]);
                     }
                 }
                 Probe<K> pr[UNROLL];
 #pragma unroll
                 for (int k = 0; k < UNROLL; ++k) {
                     pr[k].live = false;
-                    if (uint32_t(k * 32 + lane) < span) {
-                        ++arcs;
-                        probe(p, S, sl, d[k], lvk[k], a[k], pr[k]);
-                    }
+                    if (uint32_t(k * 32 + lane) < span) probe(p, S, sl, kv[k], a[k], pr[k]);
                 }
+                if (lane == 0) arcs += span;
                 commit_step(p, S, sl, h, pr);
                 oa = ob;
             }
@@ -570,7 +577,7 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot<
 template <int TPB, typename K>
 __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch p) {
     __shared__ Shared S;
-    __shared__ Frontier<TPB> F;
+    __shared__ Frontier<TPB, K> F;
     const uint32_t n = p.n;
     const size_t so = size_t(blockIdx.x) * n;
     Slot<K> sl;
