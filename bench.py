@@ -49,6 +49,13 @@ WORKLOAD_TEXT = {
 }
 
 
+# DRAM read + write bytes per relaxed arc of plant_trees_kernel, from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum = 80.7 GB over
+# 5,366,689,567 arcs, rmat18 roots at rank positions [1000, 2216), the same
+# kernel source); the bench scales it by the arcs a step relaxes
+TREE_DRAM_BYTES_PER_ARC = 15.0
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -452,6 +459,16 @@ def main():
         ev1.record(stream)
         ev1.synchronize()
         lat.append(ev0.elapsed_time(ev1) * 1000.0)
+    # algorithmic bytes of the batch: pair 8 + answer 4 + both lists scanned to the end
+    # (hub position 4 + distance 4 per entry), from the label offsets
+    off_h = L.to_numpy()[0].astype(np.int64)
+    lens = off_h[1:] - off_h[:-1]
+    qbytes = 12.0 * args.queries + 8.0 * float(lens[pairs_h[:, 0]].sum() + lens[pairs_h[:, 1]].sum())
+    qach = qbytes / (min(qt) / 1000.0) / 1e9
+    peak_q, _ = load_peaks()
+    res["query_roofline"] = {"bound": "hbm", "achieved": qach, "peak": peak_q, "unit": "GB/s",
+                             "frac": qach / peak_q, "kernel": "query_kernel",
+                             "algorithmic_bytes": qbytes}
     res["queries"] = {"batch": args.queries, "queries_per_s": args.queries / (min(qt) / 1000.0),
                       "batch_ms": min(qt), "single_launch_p50_us": float(np.percentile(lat, 50)),
                       "single_launch_p99_us": float(np.percentile(lat, 99)),
@@ -467,8 +484,15 @@ def main():
     if wu and wu_plain:
         algo = 28.0 * wu["S"] + 16.0 * wu["A"] + 12.0 * wu_plain["T"]
         ach = algo / (float(np.mean(tree_ms)) / 1000.0) / 1e9
+        arcs_step = float(res["explored"]["arcs"])
         res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                           "frac": ach / peak, "traffic": None, "peak_kind": peak_kind,
+                           "frac": ach / peak,
+                           "traffic": TREE_DRAM_BYTES_PER_ARC * arcs_step if arcs_step else None,
+                           "traffic_note": "DRAM bytes per relaxed arc from the ncu capture of the "
+                                           "tree kernel on rmat18 roots [1000, 2216) "
+                                           f"({TREE_DRAM_BYTES_PER_ARC} B), times the arcs one "
+                                           "step relaxes",
+                           "peak_kind": peak_kind,
                            "kernel": "plant_trees_kernel",
                            "algorithmic_bytes": algo,
                            "units": (f"oracle Algorithm 3 pruned by the Common Label Table of {eta} hubs"
