@@ -125,6 +125,13 @@ typedef struct chl_labels chl_labels;
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
    labels are the same either way). */
 #define CHL_FLAG_WIDE_KEYS 1
+/* chl_build_opts.flags: store with every label (h, d) of v the parent of v in
+   the shortest-path tree of h (the next vertex from v towards h; h itself for
+   the label of h), which lets chl_path return shortest paths in time linear in
+   their length (Sec. 4.3, Extensions). Keys become 8 bytes; labels take 16
+   instead of 12 bytes. Among several shortest-path predecessors the one with
+   the highest rank is stored, so the parents are unique for a fixed R. */
+#define CHL_FLAG_PARENTS 2
 
 typedef struct {
     uint32_t root_begin;
@@ -278,6 +285,29 @@ chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint64_t q, uin
  */
 chl_status chl_query_noalloc(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t *out,
                              chl_mem mem, void *stream);
+
+/*
+ * Copy the SPT parent of every label (caller vertex ids, [T], aligned with the
+ * hub/dist arrays of chl_labels_copy) to host or device memory (mem).
+ * CHL_EINVAL when L was built without CHL_FLAG_PARENTS.
+ */
+chl_status chl_labels_parents(const chl_labels *L, uint32_t *parent, chl_mem mem, void *stream);
+
+/*
+ * Shortest paths for q pairs (uint32 [q][2] caller ids). For each pair the
+ * canonical hub H (the highest-ranked hub among those with the minimum
+ * d(u,H) + d(H,v), i.e. the highest-ranked vertex on its shortest paths) is
+ * found by the query merge; the path then follows the stored parents from u
+ * to H and from v to H (Sec. 4.3, Extensions): time linear in its length.
+ *   paths  [q][max_len] vertex ids, u first and v last; entries past the
+ *          path's length (or past max_len) are left untouched
+ *   lens   [q] vertices on the path (1 for u = v, 0 when u and v are not
+ *          connected); a value above max_len means the path was cut there
+ *   mem    where pairs, paths and lens live
+ * Errors: CHL_EINVAL (NULL, id >= n, labels without parents).
+ */
+chl_status chl_path(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t max_len,
+                    uint32_t *paths, uint32_t *lens, chl_mem mem, void *stream);
 
 /* Release the labels object (NULL is allowed). Synchronises its stream. */
 void chl_labels_free(chl_labels *L);

@@ -153,3 +153,67 @@ def count_redundant(L: Labels, rank) -> int:
     rank = _u(rank, np.uint32)
     return int(lib.orc_count_redundant(L.n, L.offsets.ctypes.data, L.hub.ctypes.data,
                                        L.dist.ctypes.data, rank.ctypes.data))
+
+
+# ------------------------------------------------------------------ shortest-path recovery
+def parents(g, rank, L: Labels) -> np.ndarray:
+    """SPT parent of every label, aligned with L.hub/L.dist (Sec. 4.3,
+    Extensions: the parent of v in the tree of h stored with the label).
+    For (h, d) in L_v, v != h: the highest-ranked neighbour p of v on a shortest
+    h-v path, i.e. with d(h, p) + w(p, v) = d. Every vertex of those paths has h
+    as a hub (h ranks highest on SP_{v,h}, hence on each sub-path), so d(h, p)
+    is read from p's own labels. For v = h the parent is h."""
+    n = int(g.n)
+    row = np.asarray(g.row_ptr, np.int64)
+    col = np.asarray(g.col)
+    w = np.asarray(g.w)
+    dist_of = [dict(zip(L.hub[L.offsets[v]:L.offsets[v + 1]].tolist(),
+                        L.dist[L.offsets[v]:L.offsets[v + 1]].tolist())) for v in range(n)]
+    out = np.empty(L.total, np.uint32)
+    for v in range(n):
+        for k in range(int(L.offsets[v]), int(L.offsets[v + 1])):
+            h, d = int(L.hub[k]), int(L.dist[k])
+            if h == v:
+                out[k] = v
+                continue
+            best = None
+            for e in range(row[v], row[v + 1]):
+                p = int(col[e])
+                dp = dist_of[p].get(h)
+                if dp is not None and dp + int(w[e]) == d and (best is None or rank[p] > rank[best]):
+                    best = p
+            out[k] = best
+    return out
+
+
+def paths(L: Labels, rank, par: np.ndarray, pairs) -> list:
+    """Shortest u-v path for each pair (list of vertex lists; [] when u and v
+    share no hub): the canonical hub H of the pair (minimum d(u,h) + d(v,h),
+    then the highest rank), then parents from u up to H and from v up to H."""
+    res = []
+    for u, v in np.asarray(pairs).tolist():
+        Lu = dict(zip(L.hub[L.offsets[u]:L.offsets[u + 1]].tolist(),
+                      range(int(L.offsets[u]), int(L.offsets[u + 1]))))
+        best = None
+        for k in range(int(L.offsets[v]), int(L.offsets[v + 1])):
+            h = int(L.hub[k])
+            if h in Lu:
+                key = (int(L.dist[Lu[h]]) + int(L.dist[k]), -int(rank[h]))
+                if best is None or key < best[0]:
+                    best = (key, h)
+        if best is None:
+            res.append([])
+            continue
+        H = best[1]
+
+        def up(x):
+            walk = [x]
+            while x != H:
+                a, b = int(L.offsets[x]), int(L.offsets[x + 1])
+                k = a + int(np.nonzero(L.hub[a:b] == H)[0][0])
+                x = int(par[k])
+                walk.append(x)
+            return walk
+        a, b = up(u), up(v)
+        res.append(a + b[::-1][1:])
+    return res

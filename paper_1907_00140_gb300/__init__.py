@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "build", "lib", "Server", "CHL_OK", "CHL_EINVAL", "CHL_ENOMEM", "CHL_ECUDA", "CHL_ETIMEOUT",
-    "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "ChlError", "chl_csr", "chl_build_opts",
+    "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "CHL_FLAG_PARENTS", "ChlError", "chl_csr", "chl_build_opts",
     "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
     "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
     "chl_query_noalloc", "chl_tune", "chl_tune_report", "tune",
@@ -42,6 +42,7 @@ ARCH_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CHL_OK, CHL_EINVAL, CHL_ENOMEM, CHL_ECUDA, CHL_ETIMEOUT, CHL_EOVERFLOW = range(6)
 CHL_MEM_DEVICE, CHL_MEM_HOST = 0, 1
 CHL_FLAG_WIDE_KEYS = 1
+CHL_FLAG_PARENTS = 2
 _NAMES = {0: "CHL_OK", 1: "CHL_EINVAL", 2: "CHL_ENOMEM", 3: "CHL_ECUDA", 4: "CHL_ETIMEOUT",
           5: "CHL_EOVERFLOW"}
 
@@ -166,6 +167,10 @@ def lib():
             L.chl_last_error.restype = C.c_char_p
             L.chl_version.argtypes = []
             L.chl_version.restype = C.c_char_p
+            L.chl_labels_parents.argtypes = [vp, vp, i32, vp]
+            L.chl_labels_parents.restype = i32
+            L.chl_path.argtypes = [vp, vp, u64, u32, vp, vp, i32, vp]
+            L.chl_path.restype = i32
             L.chl_server_create.argtypes = [C.POINTER(chl_server_opts), C.POINTER(vp)]
             L.chl_server_add_set.argtypes = [vp, vp, C.POINTER(u32)]
             L.chl_server_submit_query.argtypes = [vp, u32, vp, u64, vp, C.POINTER(u64)]
@@ -326,6 +331,25 @@ class Labels:
                         dist.ctypes.data if T else None, CHL_MEM_HOST,
                         _current_stream() if stream is None else stream)
         return off, hub, dist
+
+    def parents(self, stream: int | None = None) -> np.ndarray:
+        """SPT parent of every label (host uint32[T], aligned with to_numpy()'s hub/dist)."""
+        T = chl_labels_info(self.handle)[1]
+        par = np.empty(max(T, 1), np.uint32)
+        _check(lib().chl_labels_parents(self.handle, par.ctypes.data, CHL_MEM_HOST,
+                                        _current_stream() if stream is None else stream))
+        return par[:T]
+
+    def paths(self, pairs, max_len: int = 64, stream: int | None = None):
+        """Shortest paths of host pairs [q,2]: (paths uint32[q,max_len], lens uint32[q])."""
+        p = np.ascontiguousarray(pairs, dtype=np.uint32).reshape(-1, 2)
+        q = len(p)
+        out = np.zeros((q, max_len), np.uint32)
+        lens = np.zeros(q, np.uint32)
+        _check(lib().chl_path(self.handle, p.ctypes.data, q, max_len, out.ctypes.data,
+                              lens.ctypes.data, CHL_MEM_HOST,
+                              _current_stream() if stream is None else stream))
+        return out, lens
 
     def query(self, pairs, out=None, stream: int | None = None):
         """Distances for pairs [q,2] (numpy -> numpy, CUDA tensor -> CUDA tensor)."""

@@ -68,7 +68,8 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     // 4-byte keys hold distances up to 2^31 - 2; every tentative distance of a
     // tree search is at most w_max * n (a simple path plus one arc)
     const bool narrow_fits = double(g.w_max) * double(g.n) <= double(0x7FFFFFFE);
-    p.kb = (narrow_fits && !(o.flags & CHL_FLAG_WIDE_KEYS)) ? 4 : 8;
+    // parents ride in the low 31 bits of an 8-byte key
+    p.kb = (narrow_fits && !(o.flags & (CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS))) ? 4 : 8;
     p.fin_words = plant_fin_words(p.tpt, g.n);
     {
         const int want = o.common_hubs == 0 ? 16 : o.common_hubs;  // the paper's eta = 16
@@ -265,7 +266,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
         return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
     if (o.bucket_delta < 0 || o.slots < 0) return set_error(CHL_EINVAL, "negative option");
-    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS)) return set_error(CHL_EINVAL, "unknown bit in flags");
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS))
+        return set_error(CHL_EINVAL, "unknown bit in flags");
 
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;
@@ -275,7 +277,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const uint64_t m2 = g->num_arcs;
     const uint64_t *d_row = g->row_ptr;
     const uint32_t *d_col = g->col, *d_w = g->w, *d_rank = rank;
-    DevBuf b_row, b_col, b_w, b_rank, b_ctl, b_ov, b_oh, b_od, b_fail, b_roots;
+    DevBuf b_row, b_col, b_w, b_rank, b_ctl, b_ov, b_oh, b_od, b_op, b_fail, b_roots;
+    const bool parents = (o.flags & CHL_FLAG_PARENTS) != 0;
+    uint32_t *csr_parent = nullptr;
     SlotState slot;
     CommonTable table;
     RankGraph rg;
@@ -300,7 +304,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventRecord(ev[0], s));
     b_row.s = b_col.s = b_w.s = b_rank.s = b_ctl.s = s;
-    b_ov.s = b_oh.s = b_od.s = b_fail.s = b_roots.s = s;
+    b_ov.s = b_oh.s = b_od.s = b_op.s = b_fail.s = b_roots.s = s;
 
     // inputs on the device
     if (g->mem == CHL_MEM_HOST) {
@@ -361,6 +365,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     CUDA_TRY(cudaMallocAsync(&b_ov.p, cap * 4, s));
     CUDA_TRY(cudaMallocAsync(&b_oh.p, cap * 4, s));
     CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
+    if (parents) CUDA_TRY(cudaMallocAsync(&b_op.p, cap * 4, s));
 
     CUDA_TRY(cudaEventRecord(ev[1], s));
     // the table is needed when some requested tree lies outside it
@@ -381,6 +386,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         tl.out_v = (uint32_t *)b_ov.p;
         tl.out_h = (uint32_t *)b_oh.p;
         tl.out_d = (uint32_t *)b_od.p;
+        tl.out_p = (uint32_t *)b_op.p;
         tl.out_cap = cap;
         tl.out_count = &ctl->out_count;
         tl.next_root = &ctl->next_root;
@@ -474,6 +480,13 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             CUDA_TRY(cudaMemcpyAsync(nv, b_ov.p, T * 4, cudaMemcpyDeviceToDevice, s));
             CUDA_TRY(cudaMemcpyAsync(nh, b_oh.p, T * 4, cudaMemcpyDeviceToDevice, s));
             CUDA_TRY(cudaMemcpyAsync(nd, b_od.p, T * 4, cudaMemcpyDeviceToDevice, s));
+            if (parents) {
+                void *np = nullptr;
+                CUDA_TRY(cudaMallocAsync(&np, ncap * 4, s));
+                CUDA_TRY(cudaMemcpyAsync(np, b_op.p, T * 4, cudaMemcpyDeviceToDevice, s));
+                cudaFreeAsync(b_op.p, s);
+                b_op.p = np;
+            }
             cudaFreeAsync(b_ov.p, s);
             cudaFreeAsync(b_oh.p, s);
             cudaFreeAsync(b_od.p, s);
@@ -494,6 +507,11 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         st = set_error(CHL_EOVERFLOW, "a vertex holds more labels than the segment sorter supports");
         goto done;
     }
+    if (parents) {
+        CUDA_TRY(cudaMallocAsync(&csr_parent, (T ? T : 1) * 4, s));
+        CUDA_TRY(place_parents(T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
+                               (const uint32_t *)b_op.p, csr, csr_parent, s, &launches));
+    }
     CUDA_TRY(cudaEventRecord(ev[3], s));
     CUDA_TRY(cudaEventSynchronize(ev[3]));
     cudaEventElapsedTime(&ms_total, ev[0], ev[3]);
@@ -512,7 +530,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     L->hub = csr.hub;
     L->hubpos = csr.hubpos;
     L->dist = csr.dist;
-    L->bytes = (uint64_t(n) + 1) * 8 + T * 12;
+    L->parent = csr_parent;
+    csr_parent = nullptr;
+    L->bytes = (uint64_t(n) + 1) * 8 + T * (L->parent ? 16 : 12);
     L->device = dev;
     L->stats.trees = agg[3];
     L->stats.labels = T;
@@ -530,6 +550,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     csr = LabelCSR{};
     *out = L;
 done:
+    if (csr_parent) cudaFreeAsync(csr_parent, s);
     if (csr.offsets) cudaFreeAsync(csr.offsets, s);
     if (csr.hub) cudaFreeAsync(csr.hub, s);
     if (csr.hubpos) cudaFreeAsync(csr.hubpos, s);
@@ -619,7 +640,65 @@ extern "C" void chl_labels_free(chl_labels *L) {
     cudaFree(L->hub);
     cudaFree(L->hubpos);
     cudaFree(L->dist);
+    if (L->parent) cudaFree(L->parent);
     delete L;
+}
+
+extern "C" chl_status chl_labels_parents(const chl_labels *L, uint32_t *parent, chl_mem mem,
+                                         void *stream) {
+    g_err[0] = 0;
+    if (!L || !parent) return set_error(CHL_EINVAL, "labels or parent is NULL");
+    if (!L->parent) return set_error(CHL_EINVAL, "labels were built without CHL_FLAG_PARENTS");
+    if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
+    cudaStream_t s = (cudaStream_t)stream;
+    chl_status st = CHL_OK;
+    if (L->total) {
+        CUDA_TRY(cudaMemcpyAsync(parent, L->parent, L->total * 4,
+                                 mem == CHL_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+done:
+    return st;
+}
+
+extern "C" chl_status chl_path(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t max_len,
+                               uint32_t *paths, uint32_t *lens, chl_mem mem, void *stream) {
+    g_err[0] = 0;
+    if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    if (!L->parent) return set_error(CHL_EINVAL, "labels were built without CHL_FLAG_PARENTS");
+    if (q == 0) return CHL_OK;
+    if (!pairs || !lens || (max_len && !paths)) return set_error(CHL_EINVAL, "NULL argument");
+    if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
+    cudaStream_t s = (cudaStream_t)stream;
+    chl_status st = CHL_OK;
+    DevBuf b_p, b_path, b_len, b_bad;
+    b_p.s = b_path.s = b_len.s = b_bad.s = s;
+    const uint32_t *dp = pairs;
+    uint32_t *dpath = paths, *dlen = lens;
+    int hbad = 0;
+    CUDA_TRY(cudaMallocAsync(&b_bad.p, sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(b_bad.p, 0, sizeof(int), s));
+    if (mem == CHL_MEM_HOST) {
+        CUDA_TRY(cudaMallocAsync(&b_p.p, q * 8, s));
+        CUDA_TRY(cudaMallocAsync(&b_path.p, q * max_len * 4 + 4, s));
+        CUDA_TRY(cudaMallocAsync(&b_len.p, q * 4, s));
+        CUDA_TRY(cudaMemcpyAsync(b_p.p, pairs, q * 8, cudaMemcpyHostToDevice, s));
+        dp = (const uint32_t *)b_p.p;
+        dpath = (uint32_t *)b_path.p;
+        dlen = (uint32_t *)b_len.p;
+    }
+    CUDA_TRY(launch_paths(L->n, L->offsets, L->hubpos, L->dist, L->hub, L->parent, dp, q, max_len,
+                          dpath, dlen, (int *)b_bad.p, s));
+    if (mem == CHL_MEM_HOST) {
+        if (max_len) CUDA_TRY(cudaMemcpyAsync(paths, dpath, q * max_len * 4, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(lens, dlen, q * 4, cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(cudaMemcpyAsync(&hbad, b_bad.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad == 1) st = set_error(CHL_EINVAL, "a query vertex id is >= n");
+    else if (hbad) st = set_error(CHL_ECUDA, "a parent chain did not reach its hub");
+done:
+    return st;
 }
 
 // ------------------------------------------------------------------ queries without allocation
@@ -780,7 +859,8 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     if (o.mode != 0) return set_error(CHL_EINVAL, "chl_tune tunes the batched mode (mode 0)");
     if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
         return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
-    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS)) return set_error(CHL_EINVAL, "unknown bit in flags");
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS))
+        return set_error(CHL_EINVAL, "unknown bit in flags");
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;
     const uint32_t n = g->n;

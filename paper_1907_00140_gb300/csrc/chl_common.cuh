@@ -15,6 +15,7 @@ struct chl_labels {
     uint32_t *hub = nullptr;
     uint32_t *hubpos = nullptr;
     uint32_t *dist = nullptr;
+    uint32_t *parent = nullptr;  // SPT parent per label (caller id), or null
     uint64_t bytes = 0;
     chl_build_stats stats{};
     int device = 0;
@@ -69,6 +70,7 @@ struct TreeLaunch {
     uint32_t *out_v;    // caller vertex id of the labelled vertex
     uint32_t *out_h;    // hub pos id
     uint32_t *out_d;    // distance
+    uint32_t *out_p;    // SPT parent (caller vertex id), or null: no parents
     unsigned long long out_cap;
     unsigned long long *out_count;
     // control
@@ -105,11 +107,21 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
                             const uint32_t *in_d, const uint32_t *vert_at, LabelCSR &out,
                             int *too_long, cudaStream_t s, int *launches);
 
+// parents of label records into the slots of the assembled CSR (parent[T])
+cudaError_t place_parents(uint64_t T, const uint32_t *in_v, const uint32_t *in_h, const uint32_t *in_p,
+                          const LabelCSR &csr, uint32_t *parent, cudaStream_t s, int *launches);
+
 // queries (chl_query.cu)
 // bad is set to 1 when a pair holds a vertex id >= n (that answer is UINT32_MAX)
 cudaError_t launch_query(uint32_t n, const uint64_t *offsets, const uint32_t *hubpos,
                          const uint32_t *dist, const uint32_t *pairs, uint64_t q, uint32_t *out,
                          int *bad, cudaStream_t s);
+// shortest paths from parents stored with the labels; bad = 1 for an id >= n,
+// 2 for a broken parent chain
+cudaError_t launch_paths(uint32_t n, const uint64_t *offsets, const uint32_t *hubpos,
+                         const uint32_t *dist, const uint32_t *hub, const uint32_t *parent,
+                         const uint32_t *pairs, uint64_t q, uint32_t max_len, uint32_t *paths,
+                         uint32_t *lens, int *bad, cudaStream_t s);
 // one resident label set as the query kernels read it
 struct QuerySet {
     uint32_t n;

@@ -211,4 +211,34 @@ done:
     return e;
 }
 
+namespace {
+
+// record i's parent goes to the slot of its hub in its vertex's sorted list
+// (hub positions are unique within a list)
+__global__ void place_parents_kernel(uint64_t T, const uint32_t *in_v, const uint32_t *in_h,
+                                     const uint32_t *in_p, const uint64_t *off,
+                                     const uint32_t *hubpos, uint32_t *parent) {
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < T;
+         i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t v = in_v[i], hp = in_h[i];
+        uint64_t lo = off[v], hi = off[v + 1];  // hubpos[lo..hi) ascending, contains hp
+        while (hi - lo > 1) {
+            const uint64_t mid = (lo + hi) >> 1;
+            if (hubpos[mid] <= hp) lo = mid; else hi = mid;
+        }
+        parent[lo] = in_p[i];
+    }
+}
+
+}  // namespace
+
+cudaError_t place_parents(uint64_t T, const uint32_t *in_v, const uint32_t *in_h, const uint32_t *in_p,
+                          const LabelCSR &csr, uint32_t *parent, cudaStream_t s, int *launches) {
+    if (!T) return cudaSuccess;
+    place_parents_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, in_h, in_p, csr.offsets,
+                                                           csr.hubpos, parent);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
 }  // namespace chl

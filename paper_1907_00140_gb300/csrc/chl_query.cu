@@ -86,6 +86,125 @@ __global__ void query_kernel(uint32_t n, const uint64_t *__restrict__ off,
     }
 }
 
+// The best common hub of u and v: the smallest (d(u,h) + d(v,h), hub position)
+// packed as sum << 31 | position (all ones: no common hub). At equal sums the
+// highest-ranked hub wins, the canonical hub of the pair (the max-rank vertex
+// on its shortest paths). All 32 lanes call it; every lane gets the result.
+__device__ __forceinline__ uint64_t merge_best(const uint64_t *__restrict__ off,
+                                               const uint32_t *__restrict__ hp,
+                                               const uint32_t *__restrict__ dd, uint32_t u, uint32_t v) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t a0 = __ldg(&off[u]), la = __ldg(&off[u + 1]) - a0;
+    const uint64_t b0 = __ldg(&off[v]), lb = __ldg(&off[v + 1]) - b0;
+    uint64_t ia = 0, ib = 0;
+    uint64_t best = ~0ull;
+    while (ia < la && ib < lb) {
+        const bool va = ia + lane < la, vb = ib + lane < lb;
+        const uint32_t x = va ? __ldg(&hp[a0 + ia + lane]) : 0xFFFFFFFFu;
+        const uint32_t y = vb ? __ldg(&hp[b0 + ib + lane]) : 0xFFFFFFFFu;
+        int o = 0;
+#pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+            const int c = o + step;
+            if (__shfl_sync(FULL, y, c) <= x) o = c;
+        }
+        const uint32_t yo = __shfl_sync(FULL, y, o);
+        const bool hit = va && yo == x;
+        if (__ballot_sync(FULL, hit) && hit) {
+            const uint64_t sum = uint64_t(__ldg(&dd[a0 + ia + lane])) + __ldg(&dd[b0 + ib + o]);
+            best = min64(best, (sum << 31) | x);
+        }
+        const uint32_t lastA = __shfl_sync(FULL, x, int(min64(la - ia, 32) - 1));
+        const uint32_t lastB = __shfl_sync(FULL, y, int(min64(lb - ib, 32) - 1));
+        if (lastA <= lastB) {
+            ia += min64(la - ia, 32);
+            ib += __popc(__ballot_sync(FULL, vb && y <= lastA));
+        } else {
+            ib += min64(lb - ib, 32);
+            ia += __popc(__ballot_sync(FULL, va && x <= lastB));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) best = min64(best, __shfl_xor_sync(FULL, best, o));
+    return best;
+}
+
+// entry of hub position hpos in w's list (ascending hub positions), or ~0
+__device__ __forceinline__ uint64_t find_hub(const uint64_t *__restrict__ off,
+                                             const uint32_t *__restrict__ hp, uint32_t w,
+                                             uint32_t hpos) {
+    uint64_t lo = __ldg(&off[w]), hi = __ldg(&off[w + 1]);
+    if (lo == hi) return ~0ull;
+    while (hi - lo > 1) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (__ldg(&hp[mid]) <= hpos) lo = mid; else hi = mid;
+    }
+    return __ldg(&hp[lo]) == hpos ? lo : ~0ull;
+}
+
+// Shortest paths by following the SPT parents stored with the labels (Sec. 4.3
+// Extensions): from u and from v towards their canonical hub H, each step the
+// parent stored with w's label of H. One warp per pair (merge), lane 0 walks.
+__global__ void paths_kernel(uint32_t n, const uint64_t *__restrict__ off,
+                             const uint32_t *__restrict__ hp, const uint32_t *__restrict__ dd,
+                             const uint32_t *__restrict__ hub, const uint32_t *__restrict__ par,
+                             const uint32_t *__restrict__ pairs, uint64_t q, uint32_t max_len,
+                             uint32_t *__restrict__ paths, uint32_t *__restrict__ lens, int *bad) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t i = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < q; i += warps) {
+        const uint32_t u = __ldg(&pairs[2 * i]), v = __ldg(&pairs[2 * i + 1]);
+        if (u >= n || v >= n) {
+            if (lane == 0) {
+                lens[i] = 0;
+                atomicExch(bad, 1);
+            }
+            continue;
+        }
+        const uint64_t best = merge_best(off, hp, dd, u, v);
+        if (lane != 0) continue;
+        if (best == ~0ull) {  // different components
+            lens[i] = 0;
+            continue;
+        }
+        const uint32_t hpos = uint32_t(best & 0x7FFFFFFFu);
+        uint32_t *out = paths + i * uint64_t(max_len);
+        bool ok = true;
+        // u side: u, parent, ..., H at positions 0 .. lu - 1
+        uint32_t lu = 0, w = u;
+        for (uint32_t guard = 0; guard <= n; ++guard) {
+            if (lu < max_len) out[lu] = w;
+            ++lu;
+            const uint64_t j = find_hub(off, hp, w, hpos);
+            if (j == ~0ull) { ok = false; break; }
+            if (__ldg(&hub[j]) == w) break;
+            w = __ldg(&par[j]);
+        }
+        // v side: count, then write v at the end back to the vertex after H
+        uint32_t lv = 0;
+        w = v;
+        for (uint32_t guard = 0; ok && guard <= n; ++guard) {
+            ++lv;
+            const uint64_t j = find_hub(off, hp, w, hpos);
+            if (j == ~0ull) { ok = false; break; }
+            if (__ldg(&hub[j]) == w) break;
+            w = __ldg(&par[j]);
+        }
+        if (!ok) {
+            lens[i] = 0;
+            atomicExch(bad, 2);
+            continue;
+        }
+        const uint32_t total = lu + lv - 1;
+        w = v;
+        for (uint32_t pos = total - 1; pos >= lu; --pos) {
+            if (pos < max_len) out[pos] = w;
+            w = __ldg(&par[find_hub(off, hp, w, hpos)]);
+        }
+        lens[i] = total;
+    }
+}
+
 // a batch mixing label sets: pair i asks set set_of[i]
 __global__ void query_sets_kernel(const QuerySet *__restrict__ sets, uint32_t nsets,
                                   const uint32_t *__restrict__ pairs,
@@ -118,6 +237,18 @@ cudaError_t launch_query_sets(const QuerySet *sets, uint32_t nsets, const uint32
     uint64_t blocks = (q * 32 + 255) / 256;
     if (blocks > uint64_t(max_blocks)) blocks = uint64_t(max_blocks);
     query_sets_kernel<<<unsigned(blocks), 256, 0, s>>>(sets, nsets, pairs, set_of, q, out, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_paths(uint32_t n, const uint64_t *offsets, const uint32_t *hubpos,
+                         const uint32_t *dist, const uint32_t *hub, const uint32_t *parent,
+                         const uint32_t *pairs, uint64_t q, uint32_t max_len, uint32_t *paths,
+                         uint32_t *lens, int *bad, cudaStream_t s) {
+    if (q == 0) return cudaSuccess;
+    uint64_t blocks = (q * 32 + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    paths_kernel<<<unsigned(blocks), 256, 0, s>>>(n, offsets, hubpos, dist, hub, parent, pairs, q,
+                                                   max_len, paths, lens, bad);
     return cudaGetLastError();
 }
 

@@ -70,18 +70,41 @@ constexpr uint32_t CLT_MAX = 64;  // largest Common Label Table (hubs)
 // equal-distance branch of Algorithm 3; Sec. 4.2's example, a[v5] = v1).
 // v is live (would get the label (h, d)) iff clean and v >= h, and the bit
 // it passes on to its out-neighbours is exactly its own liveness.
-// K = uint32_t when every tentative distance is provably below 2^31 - 1 (the
-// host checks w_max * n), else uint64_t. All ones is "unreached".
+// Three layouts (K below is one of these traits; K::T is the stored word):
+//   KeyN  uint32  dist << 1 | clean            when every tentative distance is
+//                                              provably below 2^31 - 1 (the host
+//                                              checks w_max * n)
+//   KeyW  uint64  dist << 1 | clean            otherwise
+//   KeyP  uint64  dist << 32 | clean << 31 | parent, for path recovery (the
+//                 SPT parent stored with each label, Sec. 4.3 Extensions):
+//                 among equal (dist, clean) the smallest parent id wins, so
+//                 the parent is the lowest-numbered tight predecessor, a
+//                 deterministic choice. A candidate carries its source
+//                 vertex in the parent field.
+// All ones is "unreached".
+struct KeyN { using T = uint32_t; static constexpr int S = 1; };
+struct KeyW { using T = uint64_t; static constexpr int S = 1; };
+struct KeyP { using T = uint64_t; static constexpr int S = 32; };
+
 template <typename K>
-__device__ __forceinline__ K key_inf() { return ~K(0); }
+__device__ __forceinline__ typename K::T key_inf() { return ~typename K::T(0); }
 template <typename K>
-__device__ __forceinline__ K make_key(uint64_t dist, bool clean) { return (K(dist) << 1) | K(clean); }
+__device__ __forceinline__ typename K::T make_key(uint64_t dist, bool clean, uint32_t parent) {
+    using KS = typename K::T;
+    return (KS(dist) << K::S) | (KS(clean) << (K::S - 1)) | (K::S > 1 ? KS(parent) : KS(0));
+}
 template <typename K>
-__device__ __forceinline__ uint32_t key_dist(K k) { return uint32_t(k >> 1); }
-// largest distance a key of type K holds below key_inf
+__device__ __forceinline__ uint32_t key_dist(typename K::T k) { return uint32_t(k >> K::S); }
+template <typename K>
+__device__ __forceinline__ bool key_clean(typename K::T k) { return (k >> (K::S - 1)) & 1; }
+template <typename K>
+__device__ __forceinline__ uint32_t key_parent(typename K::T k) {
+    return K::S > 1 ? uint32_t(k & 0x7FFFFFFFu) : 0u;
+}
+// largest distance a key holds below key_inf
 template <typename K>
 __device__ __forceinline__ uint64_t key_dist_limit() {
-    return sizeof(K) == 4 ? 0x7FFFFFFEull : 0xFFFFFFFEull;
+    return sizeof(typename K::T) == 4 ? 0x7FFFFFFEull : 0xFFFFFFFEull;
 }
 
 struct Shared {
@@ -109,14 +132,14 @@ struct Shared {
 
 template <typename K>
 struct Slot {
-    K *key;
+    typename K::T *key;
     uint32_t *rtag;
     uint32_t *l0, *l1, *far, *touch, *sub;  // sub: nwin lists of n entries
 };
 
 template <typename K>
-__device__ __forceinline__ bool is_live(K k, uint32_t v, uint32_t h) {
-    return (k & 1) && v >= h;
+__device__ __forceinline__ bool is_live(typename K::T k, uint32_t v, uint32_t h) {
+    return key_clean<K>(k) && v >= h;
 }
 
 // warp-aggregated append to a list counted by a shared-memory counter
@@ -150,8 +173,8 @@ __device__ __forceinline__ void sub_append(Shared &S, const Slot<K> &sl, uint32_
 //           for the bucket it now falls in
 template <typename K>
 struct Probe {
-    K cand;
-    K seen;
+    typename K::T cand;
+    typename K::T seen;
     uint32_t u;
     bool live;  // still worth committing
 };
@@ -180,17 +203,18 @@ extern __shared__ uint32_t fin_bitmap[];
 // the host has proven every tentative distance below the key limit
 // (w_max * n < 2^31 - 1), so only the wide form checks for overflow.
 template <typename K>
-__device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot<K> &sl, K kv,
-                                      uint2 a, Probe<K> &q) {
+__device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
+                                      typename K::T kv, uint2 a, Probe<K> &q) {
+    using KS = typename K::T;
     q.u = a.x;
     q.live = false;
-    if (sizeof(K) == 8 && uint64_t(key_dist(kv)) + a.y > key_dist_limit<K>()) {
+    if (sizeof(KS) == 8 && uint64_t(key_dist<K>(kv)) + a.y > key_dist_limit<K>()) {
         atomicExch(&p.flags[0], ERR_DIST_OVERFLOW);
         S.abort = 1;
         return;
     }
     if (q.u < p.fin_bits && ((fin_bitmap[q.u >> 5] >> (q.u & 31)) & 1u)) return;
-    q.cand = kv + (K(a.y) << 1);
+    q.cand = kv + (KS(a.y) << K::S);
     q.seen = __ldcg(&sl.key[q.u]);
     q.live = true;
 }
@@ -203,9 +227,10 @@ __device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot
 template <typename K>
 __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
                                             uint32_t h, const Probe<K> (&q)[UNROLL]) {
+    using KS = typename K::T;
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1;
-    K old[UNROLL];
+    KS old[UNROLL];
     bool imp[UNROLL];
 #pragma unroll
     for (int k = 0; k < UNROLL; ++k) {
@@ -230,14 +255,14 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, cons
         if (imp[k]) {
             const uint32_t u = q[k].u;
             const bool unreached = old[k] == key_inf<K>();
-            const uint32_t nb = key_dist(q[k].cand) / p.delta;
-            const bool f_new = nb > S.bcur && is_live(q[k].cand, u, h);
-            const bool f_old = !unreached && key_dist(old[k]) / p.delta > S.bcur && is_live(old[k], u, h);
+            const uint32_t nb = key_dist<K>(q[k].cand) / p.delta;
+            const bool f_new = nb > S.bcur && is_live<K>(q[k].cand, u, h);
+            const bool f_old = !unreached && key_dist<K>(old[k]) / p.delta > S.bcur && is_live<K>(old[k], u, h);
             dcnt += int(f_new) - int(f_old);
             if (nb == S.bcur) {
                 if (atomicExch(&sl.rtag[u], S.rid) != S.rid) cls[k] = 1;
-            } else if (key_dist(q[k].cand) < S.w_hi) {
-                if (unreached || key_dist(old[k]) / p.delta != nb) {
+            } else if (key_dist<K>(q[k].cand) < S.w_hi) {
+                if (unreached || key_dist<K>(old[k]) / p.delta != nb) {
                     cls[k] = 2;
                     sx[k] = nb - S.win_base;
                 }
@@ -304,7 +329,7 @@ template <int TPB, typename K>
 struct Frontier {
     uint64_t base[TPB];  // row start minus degree prefix: arc index = base + flat position
     uint64_t pre[TPB];   // exclusive degree prefix
-    K kv[TPB];           // make_key(distance, liveness) of the row's vertex
+    typename K::T kv[TPB];  // make_key(distance, liveness, vertex) of the row's vertex
     uint32_t wrows[TPB / 32];
     uint64_t wdeg[TPB / 32];
 };
@@ -353,6 +378,7 @@ template <int TPB, typename K>
 __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, const Slot<K> &sl,
                              uint32_t h, unsigned long long &expanded, unsigned long long &arcs,
                              unsigned long long &pruned) {
+    using KS = typename K::T;
     constexpr int NW = TPB / 32;
     constexpr uint32_t STEP = 32 * UNROLL;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -367,16 +393,17 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
         // ---- stage the chunk: rows, distances, liveness, degree prefix
         const uint32_t i = cb + threadIdx.x;
         uint64_t deg = 0, rs = 0;
-        uint32_t dv = 0;
+        uint32_t dv = 0, vid = 0;
         bool lv = false, ok = false;
         if (i < n_cur) {
             const uint32_t v = cur[i];
-            const K k = __ldcg(&sl.key[v]);
-            if (key_dist(k) >= t_lo) {  // else stale: expanded in an earlier bucket
-                dv = key_dist(k);
+            const KS k = __ldcg(&sl.key[v]);
+            vid = v;
+            if (key_dist<K>(k) >= t_lo) {  // else stale: expanded in an earlier bucket
+                dv = key_dist<K>(k);
                 rs = __ldg(&p.row[v]);
                 deg = __ldg(&p.row[v + 1]) - rs;
-                lv = is_live(k, v, h);
+                lv = is_live<K>(k, v, h);
                 if (v < p.fin_bits && uint64_t(dv) < t_lo + p.w_min)
                     atomicOr(&fin_bitmap[v >> 5], 1u << (v & 31));
                 ++expanded;
@@ -385,7 +412,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                     // v gets no label and is not expanded (Sec. 4.3)
                     ++pruned;
                     deg = 0;
-                    if (k & 1) atomic_min_key(&sl.key[v], make_key<K>(dv, false));
+                    if (key_clean<K>(k)) atomic_min_key(&sl.key[v], make_key<K>(dv, false, 0));
                 }
                 ok = deg != 0;
             }
@@ -427,7 +454,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
             const uint32_t c = rl + __popc(okm & ((1u << lane) - 1));
             const uint64_t pre = dl + inc - deg;
             F.base[c] = rs - pre;  // wraps: base + position = rs + (position - pre)
-            F.kv[c] = make_key<K>(dv, lv);
+            F.kv[c] = make_key<K>(dv, lv, vid);
             F.pre[c] = pre;
         }
         const uint64_t total = da;
@@ -443,13 +470,13 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
             for (uint64_t i0 = lo; i0 < hi; i0 += STEP) {
                 const uint32_t span = hi - i0 < STEP ? uint32_t(hi - i0) : STEP;  // positions in this step
                 uint2 a[UNROLL];
-                K kv[UNROLL];
+                KS kv[UNROLL];
                 uint32_t ob = oa;
                 const uint64_t next = oa + 1 < nrows ? F.pre[oa + 1] : ~0ull;
                 if (next >= i0 + span) {
                     // the whole step lies in row oa (long rows: hubs)
                     const uint64_t base = F.base[oa] + i0;
-                    const K k0 = F.kv[oa];
+                    const KS k0 = F.kv[oa];
 #pragma unroll
                     for (int k = 0; k < UNROLL; ++k) {
                         const uint32_t q = k * 32 + lane;
@@ -532,7 +559,7 @@ __device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint
         uint32_t u = 0;
         if (i < n_in) {
             u = sl.far[i];
-            const uint32_t b = key_dist(__ldcg(&sl.key[u])) / p.delta;
+            const uint32_t b = key_dist<K>(__ldcg(&sl.key[u])) / p.delta;
             if (b < drop_below) {
                 // stale: lowered into the window (and listed there) or expanded
             } else if (move && b < win_end) {
@@ -565,8 +592,8 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot<
     int c = 0;
     for (uint32_t i = threadIdx.x; i < cnt; i += TPB) {
         const uint32_t u = lst[i];
-        const K k = __ldcg(&sl.key[u]);
-        c += (key_dist(k) / p.delta == b && is_live(k, u, h));
+        const typename K::T k = __ldcg(&sl.key[u]);
+        c += (key_dist<K>(k) / p.delta == b && is_live<K>(k, u, h));
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
@@ -581,7 +608,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     const uint32_t n = p.n;
     const size_t so = size_t(blockIdx.x) * n;
     Slot<K> sl;
-    sl.key = (K *)p.key + so;
+    sl.key = (typename K::T *)p.key + so;
     sl.rtag = p.rtag + so;
     uint32_t *lb = p.lists + so * (4 + p.nwin);
     sl.l0 = lb;
@@ -626,6 +653,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 S.out_n = 1;
                 sl.l0[0] = h;
                 sl.l1[0] = 0;
+                sl.far[0] = h;  // the root is its own parent
             }
             __syncthreads();
             nlab = 1;
@@ -658,7 +686,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 S.fuse_live = 0;
                 sl.l0[0] = h;
                 sl.touch[0] = h;
-                atomic_set_key(&sl.key[h], make_key<K>(0, true));
+                atomic_set_key(&sl.key[h], make_key<K>(0, true, h));
             }
             __syncthreads();
             uint32_t rounds = 0;
@@ -750,12 +778,13 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             for (uint32_t base = 0; base < nt; base += TPB) {
                 const uint32_t i = base + threadIdx.x;
                 bool lv = false;
-                uint32_t u = 0, d = 0;
+                uint32_t u = 0, d = 0, par = 0;
                 if (i < nt) {
                     u = sl.touch[i];
-                    const K k = __ldcg(&sl.key[u]);
-                    lv = is_live(k, u, h);
-                    d = key_dist(k);
+                    const typename K::T k = __ldcg(&sl.key[u]);
+                    lv = is_live<K>(k, u, h);
+                    d = key_dist<K>(k);
+                    par = key_parent<K>(k);
                 }
                 const unsigned m = __ballot_sync(FULL, lv);
                 if (m) {
@@ -767,6 +796,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                         const uint32_t o = b + __popc(m & ((1u << lane) - 1));
                         sl.l0[o] = u;
                         sl.l1[o] = d;
+                        if (p.out_p) sl.far[o] = par;  // far is free once the tree stopped
                     }
                 }
             }
@@ -804,6 +834,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 p.out_v[b + i] = __ldg(&p.vert_at[sl.l0[i]]);
                 p.out_h[b + i] = h;
                 p.out_d[b + i] = sl.l1[i];
+                if (p.out_p) p.out_p[b + i] = __ldg(&p.vert_at[sl.far[i]]);
             }
         }
         __syncthreads();
@@ -844,8 +875,9 @@ cudaError_t allow_smem() {
     int dev = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (!e) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    if (!e) e = allow_smem_of(plant_trees_kernel<TPB, uint32_t>, optin);
-    if (!e) e = allow_smem_of(plant_trees_kernel<TPB, uint64_t>, optin);
+    if (!e) e = allow_smem_of(plant_trees_kernel<TPB, KeyN>, optin);
+    if (!e) e = allow_smem_of(plant_trees_kernel<TPB, KeyW>, optin);
+    if (!e) e = allow_smem_of(plant_trees_kernel<TPB, KeyP>, optin);
     return e;
 }
 
@@ -854,24 +886,28 @@ cudaError_t launch_t(const TreeLaunch &p, int slots, cudaStream_t s) {
     cudaError_t e = allow_smem<TPB>();
     if (e) return e;
     const size_t smem = size_t(p.fin_words) * 4;
-    if (p.key_bytes == 4)
-        plant_trees_kernel<TPB, uint32_t><<<slots, TPB, smem, s>>>(p);
+    if (p.out_p)
+        plant_trees_kernel<TPB, KeyP><<<slots, TPB, smem, s>>>(p);
+    else if (p.key_bytes == 4)
+        plant_trees_kernel<TPB, KeyN><<<slots, TPB, smem, s>>>(p);
     else if (p.key_bytes == 8)
-        plant_trees_kernel<TPB, uint64_t><<<slots, TPB, smem, s>>>(p);
+        plant_trees_kernel<TPB, KeyW><<<slots, TPB, smem, s>>>(p);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
-// CTAs per SM with `words` bitmap words; both key widths are built under the
+// CTAs per SM with `words` bitmap words; all key layouts are built under the
 // same register cap, the smaller of the two is returned
 template <int TPB>
 int occ(uint32_t words) {
     if (allow_smem<TPB>()) return 0;
-    int b = 0, b4 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB, uint64_t>, TPB, size_t(words) * 4);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, plant_trees_kernel<TPB, uint32_t>, TPB, size_t(words) * 4);
-    return b < b4 ? b : b4;
+    int b = 0, b4 = 0, bp = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB, KeyW>, TPB, size_t(words) * 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, plant_trees_kernel<TPB, KeyN>, TPB, size_t(words) * 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, plant_trees_kernel<TPB, KeyP>, TPB, size_t(words) * 4);
+    b = b < b4 ? b : b4;
+    return b < bp ? b : bp;
 }
 
 // the largest bitmap (<= want words) that keeps the register-limited number

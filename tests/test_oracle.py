@@ -416,3 +416,51 @@ def test_common_label_table_root_subset():
         keep = np.isin(full.hub, roots)
         assert np.array_equal(part.hub, full.hub[keep])
         assert np.array_equal(part.dist, full.dist[keep])
+
+
+# ------------------------------------------------------------------ shortest-path recovery (Sec. 4.3, Extensions)
+def brute_parent(g, rank, D, v, h, d):
+    """Highest-ranked neighbour p of v with D[h, p] + w(p, v) = d, from the
+    all-pairs distances (no labels involved)."""
+    best = None
+    for e in range(int(g.row_ptr[v]), int(g.row_ptr[v + 1])):
+        p = int(g.col[e])
+        if D[h, p] + int(g.w[e]) == d and (best is None or rank[p] > rank[best]):
+            best = p
+    return best
+
+
+@pytest.mark.parametrize("name,g,rank", tiny_cases()[::3], ids=[c[0] for c in tiny_cases()[::3]])
+def test_parents_brute_force(name, g, rank):
+    D = apsp(g)
+    L = O.build_labels(g, rank, "canonical")
+    par = O.parents(g, rank, L)
+    for v in range(g.n):
+        for k in range(int(L.offsets[v]), int(L.offsets[v + 1])):
+            h, d = int(L.hub[k]), int(L.dist[k])
+            want = v if h == v else brute_parent(g, rank, D, v, h, d)
+            assert int(par[k]) == want, (v, h)
+
+
+@pytest.mark.parametrize("name,g,rank", tiny_cases()[::3], ids=[c[0] for c in tiny_cases()[::3]])
+def test_paths_are_canonical_shortest_paths(name, g, rank):
+    """Every recovered path is a walk over edges of total weight D[u, v] that
+    passes the highest-ranked vertex of SP_{u,v}; disconnected pairs give []."""
+    D = apsp(g)
+    n = g.n
+    L = O.build_labels(g, rank, "plant")
+    par = O.parents(g, rank, L)
+    wt = {}
+    for v in range(n):
+        for e in range(int(g.row_ptr[v]), int(g.row_ptr[v + 1])):
+            wt[(v, int(g.col[e]))] = int(g.w[e])
+    pairs = [(u, v) for u in range(n) for v in range(n)]
+    for (u, v), path in zip(pairs, O.paths(L, rank, par, pairs)):
+        if not np.isfinite(D[u, v]):
+            assert path == []
+            continue
+        assert path[0] == u and path[-1] == v
+        assert sum(wt[(a, b)] for a, b in zip(path, path[1:])) == D[u, v]
+        on_sp = np.where(D[u, :] + D[:, v] == D[u, v])[0]
+        top = int(on_sp[np.argmax(rank[on_sp])])
+        assert top in path
