@@ -62,8 +62,10 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     p.tpt = o.threads_per_tree ? o.threads_per_tree : 1024;
     const double mean_deg = g.n ? double(g.m2) / double(g.n) : 0.0;
     const double dflt = mean_deg >= 8.0 ? g.w_mean / 128.0 : 2.0 * g.w_mean;
-    uint32_t d = o.bucket_delta > 0 ? uint32_t(o.bucket_delta) : uint32_t(dflt);
-    p.delta = d < 1 ? 1 : d;
+    uint32_t d = 1;  // default: the power of two nearest to dflt
+    while (double(d) * 1.5 < dflt && d < (1u << 30)) d <<= 1;
+    if (o.bucket_delta > 0) d = uint32_t(o.bucket_delta);
+    p.delta = d;
     p.nwin = o.window_buckets > 0 ? uint32_t(o.window_buckets) : 32;
     // 4-byte keys hold distances up to 2^31 - 2; every tentative distance of a
     // tree search is at most w_max * n (a simple path plus one arc)
@@ -121,6 +123,9 @@ struct SlotState {
     }
     void fill(const Params &P, uint32_t n, TreeLaunch &tl) const {
         tl.delta = P.delta;
+        tl.delta_shift = -1;
+        for (int b = 0; b < 32; ++b)
+            if (P.delta == (1u << b)) tl.delta_shift = b;
         tl.nwin = P.nwin;
         tl.key = key.p;
         tl.key_bytes = P.kb;
@@ -930,8 +935,9 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
         } else {
             const double f[] = {0.0, 1.0 / 64, 1.0 / 16, 1.0 / 4, 1.0, 2.0};
             for (double x : f) {
-                uint32_t d = uint32_t(wm * x);
-                if (d < 1) d = 1;
+                // powers of two: the kernel then finds buckets with a shift
+                uint32_t d = 1;
+                while (double(d) * 1.5 < wm * x && d < (1u << 30)) d <<= 1;
                 bool seen = false;
                 for (uint32_t e : deltas) seen |= (e == d);
                 if (!seen) deltas.push_back(d);

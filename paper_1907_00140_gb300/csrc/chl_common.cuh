@@ -50,6 +50,7 @@ struct TreeLaunch {
     uint32_t root_count;
     // search parameters
     uint32_t delta;
+    int delta_shift;    // log2(delta) when delta is a power of two, else -1
     uint32_t nwin;
     uint32_t w_min;     // lightest arc weight
     uint32_t fin_words; // settled-filter bitmap words in dynamic shared memory

@@ -130,6 +130,11 @@ struct Shared {
     uint32_t sub_n[NWIN_MAX];
 };
 
+// bucket of a distance: a shift when the width is a power of two
+__device__ __forceinline__ uint32_t bucket_of(const TreeLaunch &p, uint32_t d) {
+    return p.delta_shift >= 0 ? d >> p.delta_shift : d / p.delta;
+}
+
 template <typename K>
 struct Slot {
     typename K::T *key;
@@ -255,14 +260,15 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, cons
         if (imp[k]) {
             const uint32_t u = q[k].u;
             const bool unreached = old[k] == key_inf<K>();
-            const uint32_t nb = key_dist<K>(q[k].cand) / p.delta;
+            const uint32_t nb = bucket_of(p, key_dist<K>(q[k].cand));
+            const uint32_t ob = unreached ? NONE : bucket_of(p, key_dist<K>(old[k]));
             const bool f_new = nb > S.bcur && is_live<K>(q[k].cand, u, h);
-            const bool f_old = !unreached && key_dist<K>(old[k]) / p.delta > S.bcur && is_live<K>(old[k], u, h);
+            const bool f_old = !unreached && ob > S.bcur && is_live<K>(old[k], u, h);
             dcnt += int(f_new) - int(f_old);
             if (nb == S.bcur) {
                 if (atomicExch(&sl.rtag[u], S.rid) != S.rid) cls[k] = 1;
             } else if (key_dist<K>(q[k].cand) < S.w_hi) {
-                if (unreached || key_dist<K>(old[k]) / p.delta != nb) {
+                if (ob != nb) {
                     cls[k] = 2;
                     sx[k] = nb - S.win_base;
                 }
@@ -272,16 +278,28 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, cons
             if (unreached) cls[k] |= 4;
         }
     }
-    const int dsum = __reduce_add_sync(FULL, dcnt);
-    if (lane == 0 && dsum) atomicAdd(&S.cnt, dsum);
+    // which (list, k) pairs occur anywhere in the warp: the rest is skipped
+    uint32_t bits = dcnt ? 0x10000u : 0u;
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        if (cls[k] & 4) bits |= 1u << k;
+        if ((cls[k] & 3) == 1) bits |= 1u << (4 + k);
+        if ((cls[k] & 3) == 3) bits |= 1u << (8 + k);
+        if ((cls[k] & 3) == 2) bits |= 1u << (12 + k);
+    }
+    const uint32_t seen = __reduce_or_sync(FULL, bits);
+    if (seen & 0x10000u) {
+        const int dsum = __reduce_add_sync(FULL, dcnt);
+        if (lane == 0 && dsum) atomicAdd(&S.cnt, dsum);
+    }
     // touched (first finite key), nxt and far: one reservation per list
     unsigned mt[UNROLL], mn[UNROLL], mf[UNROLL];
     uint32_t ct = 0, cn = 0, cf = 0;
 #pragma unroll
     for (int k = 0; k < UNROLL; ++k) {
-        mt[k] = __ballot_sync(FULL, (cls[k] & 4) != 0);
-        mn[k] = __ballot_sync(FULL, (cls[k] & 3) == 1);
-        mf[k] = __ballot_sync(FULL, (cls[k] & 3) == 3);
+        mt[k] = (seen >> k) & 1 ? __ballot_sync(FULL, (cls[k] & 4) != 0) : 0u;
+        mn[k] = (seen >> (4 + k)) & 1 ? __ballot_sync(FULL, (cls[k] & 3) == 1) : 0u;
+        mf[k] = (seen >> (8 + k)) & 1 ? __ballot_sync(FULL, (cls[k] & 3) == 3) : 0u;
         ct += __popc(mt[k]);
         cn += __popc(mn[k]);
         cf += __popc(mf[k]);
@@ -305,7 +323,7 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, cons
         bt += __popc(mt[k]);
         bn += __popc(mn[k]);
         bf += __popc(mf[k]);
-        if (__any_sync(FULL, (cls[k] & 3) == 2)) {
+        if ((seen >> (12 + k)) & 1) {
             // lanes joining the same window bucket share one counter update
             const unsigned g = __match_any_sync(FULL, sx[k]);
             const int ld = __ffs(g) - 1;
@@ -559,7 +577,7 @@ __device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint
         uint32_t u = 0;
         if (i < n_in) {
             u = sl.far[i];
-            const uint32_t b = key_dist<K>(__ldcg(&sl.key[u])) / p.delta;
+            const uint32_t b = bucket_of(p, key_dist<K>(__ldcg(&sl.key[u])));
             if (b < drop_below) {
                 // stale: lowered into the window (and listed there) or expanded
             } else if (move && b < win_end) {
@@ -593,7 +611,7 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot<
     for (uint32_t i = threadIdx.x; i < cnt; i += TPB) {
         const uint32_t u = lst[i];
         const typename K::T k = __ldcg(&sl.key[u]);
-        c += (key_dist<K>(k) / p.delta == b && is_live<K>(k, u, h));
+        c += (bucket_of(p, key_dist<K>(k)) == b && is_live<K>(k, u, h));
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
