@@ -130,8 +130,9 @@ struct QuerySet {
     const uint32_t *hubpos;
     const uint32_t *dist;
 };
-// a batch whose pair i asks set set_of[i] (sets: device array of nsets)
-cudaError_t launch_query_sets(const QuerySet *sets, uint32_t nsets, const uint32_t *pairs,
+// a batch whose pair i asks set set_of[i] (sets: device array, *nsets in device
+// memory; set id 0xFFFF = padding, skipped)
+cudaError_t launch_query_sets(const QuerySet *sets, const uint32_t *nsets, const uint32_t *pairs,
                               const uint16_t *set_of, uint64_t q, uint32_t *out, int *bad,
                               int max_blocks, cudaStream_t s);
 

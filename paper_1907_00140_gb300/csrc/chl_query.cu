@@ -206,15 +206,19 @@ __global__ void paths_kernel(uint32_t n, const uint64_t *__restrict__ off,
 }
 
 // a batch mixing label sets: pair i asks set set_of[i]
-__global__ void query_sets_kernel(const QuerySet *__restrict__ sets, uint32_t nsets,
+// (the set count is read from device memory, so a captured launch stays valid
+// as sets are added; set id 0xFFFF marks padding that is skipped)
+__global__ void query_sets_kernel(const QuerySet *__restrict__ sets, const uint32_t *nsets_p,
                                   const uint32_t *__restrict__ pairs,
                                   const uint16_t *__restrict__ set_of, uint64_t q,
                                   uint32_t *__restrict__ out, int *bad) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    const uint32_t nsets = *nsets_p;
     for (uint64_t i = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < q; i += warps) {
-        const uint32_t u = __ldg(&pairs[2 * i]), v = __ldg(&pairs[2 * i + 1]);
         const uint32_t k = __ldg(&set_of[i]);
+        if (k == 0xFFFFu) continue;
+        const uint32_t u = __ldg(&pairs[2 * i]), v = __ldg(&pairs[2 * i + 1]);
         const QuerySet S = sets[k < nsets ? k : 0];
         if (k >= nsets || u >= S.n || v >= S.n) {
             if (lane == 0) {
@@ -230,7 +234,7 @@ __global__ void query_sets_kernel(const QuerySet *__restrict__ sets, uint32_t ns
 
 }  // namespace
 
-cudaError_t launch_query_sets(const QuerySet *sets, uint32_t nsets, const uint32_t *pairs,
+cudaError_t launch_query_sets(const QuerySet *sets, const uint32_t *nsets, const uint32_t *pairs,
                               const uint16_t *set_of, uint64_t q, uint32_t *out, int *bad,
                               int max_blocks, cudaStream_t s) {
     if (q == 0) return cudaSuccess;

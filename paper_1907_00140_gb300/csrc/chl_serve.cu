@@ -20,6 +20,7 @@
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <mutex>
@@ -63,16 +64,24 @@ struct Part {
     Clock::time_point arrive;
 };
 
+// A batch slot. A batch of up to B pairs (B a bucket size) travels as one
+// pinned block [pairs B x 8 bytes][set ids B x 2 bytes] copied in, and one
+// block [answers B x 4][bad flag] copied out; unused set ids are 0xFFFF
+// (skipped). Per bucket size the memset of the flag, the two copies and the
+// query launch are captured once as a CUDA graph, so a batch costs one graph
+// launch and one event record.
 struct Slot {
     cudaStream_t s = nullptr;
     cudaEvent_t ev = nullptr;
-    uint32_t *h_pairs = nullptr, *h_out = nullptr;
-    uint16_t *h_set = nullptr;
-    uint32_t *d_pairs = nullptr, *d_out = nullptr;
-    uint16_t *d_set = nullptr;
-    int *d_bad = nullptr;
+    uint8_t *h_in = nullptr;   // pinned: pairs, then set ids
+    uint32_t *h_out = nullptr; // pinned: answers, then the flag
+    uint16_t *h_set = nullptr; // host scratch of set ids while a batch forms
+    uint8_t *d_in = nullptr;
+    uint32_t *d_out = nullptr;
+    std::vector<uint64_t> bucket;            // batch sizes with a captured graph
+    std::vector<cudaGraphExec_t> graph;      // one per bucket size
     std::vector<Part> parts;
-    uint64_t count = 0;
+    uint64_t count = 0, cap = 0;             // pairs in the batch, its bucket size
     bool busy = false;
 };
 
@@ -108,6 +117,7 @@ struct chl_server {
     uint64_t next_id = 1;
     std::vector<chl::QuerySet> sets;
     chl::QuerySet *d_sets = nullptr;
+    uint32_t *d_nsets = nullptr;  // set count read by the (captured) query launches
     std::vector<Slot> slots;
     Replay rp;
     std::mutex replay_mu;  // one replay at a time
@@ -132,8 +142,8 @@ bool chl_server::retire(Slot &sl, bool block) {
     }
     const Clock::time_point now = Clock::now();
     int bad = 0;
-    // the flag was copied out with the answers (last 4 bytes after them)
-    std::memcpy(&bad, sl.h_out + sl.count, sizeof(int));
+    // the flag was copied out with the answers (4 bytes after the bucket)
+    std::memcpy(&bad, sl.h_out + sl.cap, sizeof(int));
     std::vector<Req *> finished;
     uint64_t replayed = 0;
     for (const Part &pt : sl.parts) {
@@ -189,7 +199,7 @@ bool chl_server::launch(Slot &sl) {
                 const uint64_t c = rp.off[i + 1] - rp.off[i];
                 if (used + c > cap && used) break;
                 Part pt{rp.out + rp.off[i], c, used, nullptr, rp.lat + i, rp.at(i)};
-                std::memcpy(sl.h_pairs + 2 * used, rp.pairs + 2 * rp.off[i], c * 8);
+                std::memcpy(sl.h_in + 8 * used, rp.pairs + 2 * rp.off[i], c * 8);
                 std::fill(sl.h_set + used, sl.h_set + used + c, uint16_t(rp.set_of[i]));
                 sl.parts.push_back(pt);
                 used += c;
@@ -197,7 +207,7 @@ bool chl_server::launch(Slot &sl) {
             } else {
                 if (used + r->count > cap && used) break;
                 Part pt{r->out, r->count, used, r, nullptr, r->t_arrive};
-                std::memcpy(sl.h_pairs + 2 * used, r->pairs, r->count * 8);
+                std::memcpy(sl.h_in + 8 * used, r->pairs, r->count * 8);
                 std::fill(sl.h_set + used, sl.h_set + used + r->count, uint16_t(r->set));
                 sl.parts.push_back(pt);
                 used += r->count;
@@ -206,16 +216,17 @@ bool chl_server::launch(Slot &sl) {
         }
     }
     if (sl.parts.empty()) return false;
+    (void)nsets;
+    // the smallest captured bucket that holds the batch
+    size_t b = 0;
+    while (sl.bucket[b] < used) ++b;
+    const uint64_t B = sl.bucket[b];
+    uint16_t *set_in = reinterpret_cast<uint16_t *>(sl.h_in + 8 * B);
+    std::memcpy(set_in, sl.h_set, used * 2);
+    std::fill(set_in + used, set_in + B, uint16_t(0xFFFF));
     sl.count = used;
-    cudaMemsetAsync(sl.d_bad, 0, sizeof(int), sl.s);
-    if (used) {
-        cudaMemcpyAsync(sl.d_pairs, sl.h_pairs, used * 8, cudaMemcpyHostToDevice, sl.s);
-        cudaMemcpyAsync(sl.d_set, sl.h_set, used * 2, cudaMemcpyHostToDevice, sl.s);
-        chl::launch_query_sets(d_sets, nsets, sl.d_pairs, sl.d_set, used, sl.d_out,
-                               sl.d_bad, sms * 64, sl.s);
-        cudaMemcpyAsync(sl.h_out, sl.d_out, used * 4, cudaMemcpyDeviceToHost, sl.s);
-    }
-    cudaMemcpyAsync(sl.h_out + used, sl.d_bad, sizeof(int), cudaMemcpyDeviceToHost, sl.s);
+    sl.cap = B;
+    cudaGraphLaunch(sl.graph[b], sl.s);
     cudaEventRecord(sl.ev, sl.s);
     sl.busy = true;
     {
@@ -339,6 +350,8 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
     }
     S->o = o;
     if (!e) e = cudaMalloc(&S->d_sets, MAX_SETS * sizeof(QuerySet));
+    if (!e) e = cudaMalloc(&S->d_nsets, sizeof(uint32_t));
+    if (!e) e = cudaMemset(S->d_nsets, 0, sizeof(uint32_t));
     int lo = 0, hi = 0;
     if (!e) e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
     S->slots.resize(o.query_slots);
@@ -347,13 +360,36 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
         const uint64_t mb = o.max_batch;
         e = cudaStreamCreateWithPriority(&sl.s, cudaStreamNonBlocking, hi);
         if (!e) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
-        if (!e) e = cudaMallocHost(&sl.h_pairs, mb * 8);
+        if (!e) e = cudaMallocHost(&sl.h_in, mb * 10 + 16);
         if (!e) e = cudaMallocHost(&sl.h_out, mb * 4 + 16);
-        if (!e) e = cudaMallocHost(&sl.h_set, mb * 2);
-        if (!e) e = cudaMalloc(&sl.d_pairs, mb * 8);
-        if (!e) e = cudaMalloc(&sl.d_out, mb * 4);
-        if (!e) e = cudaMalloc(&sl.d_set, mb * 2);
-        if (!e) e = cudaMalloc(&sl.d_bad, sizeof(int));
+        if (!e) sl.h_set = static_cast<uint16_t *>(std::malloc(mb * 2));
+        if (!e && !sl.h_set) e = cudaErrorMemoryAllocation;
+        if (!e) e = cudaMalloc(&sl.d_in, mb * 10 + 16);
+        if (!e) e = cudaMalloc(&sl.d_out, mb * 4 + 16);
+        // bucket sizes 32, 64, ... up to max_batch, each captured as a graph
+        for (uint64_t B = 32; !e; B *= 2) {
+            if (B > mb) B = mb;
+            cudaGraph_t gph = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            e = cudaStreamBeginCapture(sl.s, cudaStreamCaptureModeThreadLocal);
+            if (!e) {
+                uint32_t *flag = sl.d_out + B;
+                cudaMemsetAsync(flag, 0, sizeof(int), sl.s);
+                cudaMemcpyAsync(sl.d_in, sl.h_in, B * 10, cudaMemcpyHostToDevice, sl.s);
+                launch_query_sets(S->d_sets, S->d_nsets, reinterpret_cast<const uint32_t *>(sl.d_in),
+                                  reinterpret_cast<const uint16_t *>(sl.d_in + 8 * B), B, sl.d_out,
+                                  reinterpret_cast<int *>(flag), S->sms * 64, sl.s);
+                cudaMemcpyAsync(sl.h_out, sl.d_out, B * 4 + 4, cudaMemcpyDeviceToHost, sl.s);
+                e = cudaStreamEndCapture(sl.s, &gph);
+            }
+            if (!e) e = cudaGraphInstantiate(&ex, gph, 0);
+            if (gph) cudaGraphDestroy(gph);
+            if (!e) {
+                sl.bucket.push_back(B);
+                sl.graph.push_back(ex);
+            }
+            if (B == mb) break;
+        }
     }
     if (e) {
         chl_server_destroy(S);
@@ -372,8 +408,10 @@ extern "C" chl_status chl_server_add_set(chl_server *S, const chl_labels *L, uin
     if (S->sets.size() >= MAX_SETS) return set_error(CHL_EINVAL, "too many label sets");
     QuerySet q{L->n, L->offsets, L->hubpos, L->dist};
     const uint32_t k = uint32_t(S->sets.size());
+    const uint32_t k1 = k + 1;
     // published before any query on it can be submitted (the id is returned after)
     cudaError_t e = cudaMemcpy(S->d_sets + k, &q, sizeof(q), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(S->d_nsets, &k1, sizeof(k1), cudaMemcpyHostToDevice);
     if (e) return set_error(CHL_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
     S->sets.push_back(q);
     *set_id = k;
@@ -535,16 +573,16 @@ extern "C" void chl_server_destroy(chl_server *S) {
     }
     for (Slot &sl : S->slots) {
         if (sl.s) cudaStreamSynchronize(sl.s);
-        cudaFreeHost(sl.h_pairs);
+        for (cudaGraphExec_t ex : sl.graph) cudaGraphExecDestroy(ex);
+        cudaFreeHost(sl.h_in);
         cudaFreeHost(sl.h_out);
-        cudaFreeHost(sl.h_set);
-        cudaFree(sl.d_pairs);
+        std::free(sl.h_set);
+        cudaFree(sl.d_in);
         cudaFree(sl.d_out);
-        cudaFree(sl.d_set);
-        cudaFree(sl.d_bad);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.s) cudaStreamDestroy(sl.s);
     }
     cudaFree(S->d_sets);
+    cudaFree(S->d_nsets);
     delete S;
 }
