@@ -132,6 +132,14 @@ typedef struct chl_labels chl_labels;
    instead of 12 bytes. Among several shortest-path predecessors the one with
    the highest rank is stored, so the parents are unique for a fixed R. */
 #define CHL_FLAG_PARENTS 2
+/* chl_build_opts.flags: run a build that starts at the top root as a single
+   phase (no hybrid pruning). By default such a build runs its roots in phases
+   of doubling size, and the trees of each phase also skip a vertex whose
+   distance query over all labels of the earlier phases is at most its
+   distance (the PLaNT-to-label-pruning hybrid of Sec. 4.3, on one GPU: the
+   earlier phases' hubs form a rank-closed set, so the labels stay canonical
+   and no cleaning pass is needed). */
+#define CHL_FLAG_NO_HYBRID 4
 
 typedef struct {
     uint32_t root_begin;

@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "build", "lib", "Server", "CHL_OK", "CHL_EINVAL", "CHL_ENOMEM", "CHL_ECUDA", "CHL_ETIMEOUT",
-    "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "CHL_FLAG_PARENTS", "ChlError", "chl_csr", "chl_build_opts",
+    "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "CHL_FLAG_PARENTS", "CHL_FLAG_NO_HYBRID", "ChlError", "chl_csr", "chl_build_opts",
     "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
     "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
     "chl_query_noalloc", "chl_tune", "chl_tune_report", "tune",
@@ -43,6 +43,7 @@ CHL_OK, CHL_EINVAL, CHL_ENOMEM, CHL_ECUDA, CHL_ETIMEOUT, CHL_EOVERFLOW = range(6
 CHL_MEM_DEVICE, CHL_MEM_HOST = 0, 1
 CHL_FLAG_WIDE_KEYS = 1
 CHL_FLAG_PARENTS = 2
+CHL_FLAG_NO_HYBRID = 4
 _NAMES = {0: "CHL_OK", 1: "CHL_EINVAL", 2: "CHL_ENOMEM", 3: "CHL_ECUDA", 4: "CHL_ETIMEOUT",
           5: "CHL_EOVERFLOW"}
 

@@ -144,6 +144,18 @@ struct SlotState {
     }
 };
 
+// expansions per label of a phase above which the next phases prune with the
+// label table of the earlier ones
+constexpr double PSI_TH = 16.0;
+
+void free_csr(LabelCSR &c, cudaStream_t s) {
+    if (c.offsets) cudaFreeAsync(c.offsets, s);
+    if (c.hub) cudaFreeAsync(c.hub, s);
+    if (c.hubpos) cudaFreeAsync(c.hubpos, s);
+    if (c.dist) cudaFreeAsync(c.dist, s);
+    c = LabelCSR{};
+}
+
 // Common Label Table (Sec. 4.3): all labels of the `hubs` most important
 // vertices, as a dense [n][stride] table of distances (all ones = no label).
 struct CommonTable {
@@ -271,7 +283,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
         return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
     if (o.bucket_delta < 0 || o.slots < 0) return set_error(CHL_EINVAL, "negative option");
-    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS))
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS | CHL_FLAG_NO_HYBRID))
         return set_error(CHL_EINVAL, "unknown bit in flags");
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -301,6 +313,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     chl_labels *L = nullptr;
     unsigned long long agg[7] = {0, 0, 0, 0, 0, 0, 0};
     std::vector<uint32_t> pending;  // roots still to build (after a full buffer)
+    std::vector<std::pair<uint32_t, uint32_t>> phases;
+    LabelCSR lt;  // labels of earlier phases (hybrid)
+    bool use_lt = false, hybrid = false;
     uint32_t claimed_upto = 0;
     bool first = true;
 
@@ -380,6 +395,20 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         with_table = true;
     }
     CUDA_TRY(cudaEventRecord(ev[4], s));
+    // Hybrid phases (Sec. 4.3): a build that starts at the top root runs its
+    // roots in phases of doubling size; the trees of a phase also prune with
+    // every label of all earlier phases (a rank-closed hub set, so the labels
+    // stay canonical). Other builds run as one phase.
+    // The next phase doubles (at least two trees per slot) while the table is
+    // used, so that it stays fresh; before the switch it grows fourfold.
+    hybrid = rb == 0 && P.eta && !(o.flags & CHL_FLAG_NO_HYBRID) && re > P.eta;
+    phases.clear();
+    phases.push_back(hybrid ? std::make_pair(0u, P.eta) : std::make_pair(rb, re));
+    for (size_t ph = 0; ph < phases.size(); ++ph) {
+    const uint32_t pb = phases[ph].first, pe = phases[ph].second;
+    const uint64_t exp0 = agg[0], T0 = T;
+    first = true;
+    pending.clear();
     for (int attempt = 0;; ++attempt) {
         TreeLaunch tl{};
         tl.n = n;
@@ -388,6 +417,12 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         tl.vert_at = rg.vert_at;
         slot.fill(P, n, tl);
         table.fill(tl);
+        if (lt.offsets) {
+            tl.lt_off = lt.offsets;
+            tl.lt_hp = lt.hubpos;
+            tl.lt_d = lt.dist;
+            tl.lt_hubs = pb;
+        }
         tl.out_v = (uint32_t *)b_ov.p;
         tl.out_h = (uint32_t *)b_oh.p;
         tl.out_d = (uint32_t *)b_od.p;
@@ -402,8 +437,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         uint32_t count = 0;
         if (first) {
             tl.root_list = nullptr;
-            tl.root_begin = rb;
-            count = re - rb;
+            tl.root_begin = pb;
+            count = pe - pb;
         } else {
             CUDA_TRY(cudaMemcpyAsync(b_roots.p, pending.data(), pending.size() * 4,
                                      cudaMemcpyHostToDevice, s));
@@ -466,12 +501,12 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
                 claimed_upto = count;
                 if (!failed.empty()) {
                     for (uint32_t i = 0; i < count; ++i)
-                        if ((first ? rb + i : prev[i]) == failed[0]) { claimed_upto = i + 1; break; }
+                        if ((first ? pb + i : prev[i]) == failed[0]) { claimed_upto = i + 1; break; }
                 }
             }
             pending = failed;
             for (uint32_t i = claimed_upto; i < count; ++i)
-                pending.push_back(first ? rb + i : prev[i]);
+                pending.push_back(first ? pb + i : prev[i]);
             first = false;
             if (attempt > 40) {
                 st = set_error(CHL_ENOMEM, "label buffer cannot grow further");
@@ -501,6 +536,28 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             cap = ncap;
         }
     }
+    // The switch of Sec. 4.3: label pruning starts once a phase's trees explore
+    // many vertices per label (Psi = expansions / labels above PSI_TH); before
+    // that, the per-vertex table query would cost more than it saves.
+    if (hybrid && !use_lt && T > T0 && double(agg[0] - exp0) / double(T - T0) > PSI_TH) use_lt = true;
+    if (hybrid && pe < re) {
+        const uint64_t step_min = uint64_t(P.slots) * 2;
+        const uint64_t nx = std::max<uint64_t>(uint64_t(pe) * (use_lt ? 2 : 4), pe + step_min);
+        phases.push_back({pe, uint32_t(std::min<uint64_t>(nx, re))});
+    }
+    if (use_lt && ph + 1 < phases.size()) {
+        // every label so far, as CSR, for the next phase's pruning
+        free_csr(lt, s);
+        int tl_long = 0;
+        CUDA_TRY(assemble_labels(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
+                                 (const uint32_t *)b_od.p, rg.vert_at, lt, &tl_long, s, &launches));
+        if (tl_long) {
+            st = set_error(CHL_EOVERFLOW, "a vertex holds more labels than the segment sorter supports");
+            goto done;
+        }
+    }
+    }  // phases
+    free_csr(lt, s);
     CUDA_TRY(cudaEventRecord(ev[2], s));
     // slot state and table are no longer needed: release them before assembly
     slot.release();
@@ -555,6 +612,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     csr = LabelCSR{};
     *out = L;
 done:
+    free_csr(lt, s);
     if (csr_parent) cudaFreeAsync(csr_parent, s);
     if (csr.offsets) cudaFreeAsync(csr.offsets, s);
     if (csr.hub) cudaFreeAsync(csr.hub, s);
@@ -864,7 +922,7 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     if (o.mode != 0) return set_error(CHL_EINVAL, "chl_tune tunes the batched mode (mode 0)");
     if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
         return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
-    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS))
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS | CHL_FLAG_NO_HYBRID))
         return set_error(CHL_EINVAL, "unknown bit in flags");
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;

@@ -61,6 +61,13 @@ struct TreeLaunch {
     const uint32_t *hc;
     uint32_t hc_hubs;
     uint32_t hc_stride;
+    // label table of the earlier phases of a hybrid build, or lt_off = null:
+    // all labels of the hubs of rank position < lt_hubs, CSR by caller vertex
+    // id (offsets [n+1]) with ascending hub positions lt_hp and distances lt_d
+    const uint64_t *lt_off;
+    const uint32_t *lt_hp;
+    const uint32_t *lt_d;
+    uint32_t lt_hubs;
     // slot state: slot s owns [s*n, (s+1)*n) of each array
     void *key;          // tree keys, all ones when idle (see chl_tree.cu)
     int key_bytes;      // 4 (distances provably < 2^31 - 1) or 8

@@ -56,6 +56,8 @@ constexpr uint32_t NWIN_MAX = 64;
 constexpr int UNROLL = 4;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t CLT_MAX = 64;  // largest Common Label Table (hubs)
+constexpr uint32_t LTH_SLOTS = 1024;  // hash of the root's labels in the label table
+constexpr uint32_t LTH_MAX = 512;     // most root labels the hash holds
 
 // ------------------------------------------------------------------ keys
 // Vertices are numbered by rank position (pos 0 = most important), so in the
@@ -125,7 +127,11 @@ struct Shared {
     int live_sum;
     int fuse_live;         // the current list's first stage also counts its live entries
     int prune;             // this tree prunes by the Common Label Table
+    int lt_prune;          // ... and by the label table of earlier phases
     uint32_t hch[CLT_MAX]; // table row of the root: d(h, c) per table hub c
+    // the root's labels in the label table, hashed by hub position (key + 1)
+    uint32_t lth_key[LTH_SLOTS];
+    uint32_t lth_val[LTH_SLOTS];
     unsigned long long base;
     uint32_t sub_n[NWIN_MAX];
 };
@@ -392,6 +398,37 @@ __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared 
     return best;
 }
 
+// Label table of earlier phases (hybrid pruning): every label of every hub of
+// rank position below p.lt_hubs, as CSR by caller vertex id with hub
+// positions ascending. min over shared hubs c of d(h,c) + d(c,v) <= dv means a
+// vertex outranking h lies on a shortest h-v path, as for the Common Label
+// Table: the table is complete for a rank-closed set of hubs (Sec. 4.3). The
+// query must see every table label of h and of v: a vertex reached only past a
+// pruned one is left with a wrong distance and ancestor unless it is pruned
+// too, which the complete query guarantees (a partial one would not). A tree
+// whose root has more table labels than the hash holds does not use the table.
+__device__ __forceinline__ uint32_t lth_slot(uint32_t hp) { return (hp * 2654435761u) >> 22; }
+
+__device__ __forceinline__ bool lt_prunes(const TreeLaunch &p, const Shared &S, uint32_t v,
+                                          uint32_t dv) {
+    const uint32_t cv = __ldg(&p.vert_at[v]);
+    const uint64_t a = __ldg(&p.lt_off[cv]), b = __ldg(&p.lt_off[cv + 1]);
+    for (uint64_t j = a; j < b; ++j) {
+        const uint32_t c = __ldg(&p.lt_hp[j]);
+        const uint32_t dcv = __ldg(&p.lt_d[j]);
+        if (dcv > dv) continue;
+        for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
+            const uint32_t key = S.lth_key[sx];
+            if (key == 0) break;
+            if (key == c + 1) {
+                if (uint64_t(S.lth_val[sx]) + dcv <= dv) return true;
+                break;
+            }
+        }
+    }
+    return false;
+}
+
 template <int TPB, typename K>
 __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, const Slot<K> &sl,
                              uint32_t h, unsigned long long &expanded, unsigned long long &arcs,
@@ -425,7 +462,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                 if (v < p.fin_bits && uint64_t(dv) < t_lo + p.w_min)
                     atomicOr(&fin_bitmap[v >> 5], 1u << (v & 31));
                 ++expanded;
-                if (S.prune && clt_query(p, S, v) <= dv) {
+                if ((S.prune && clt_query(p, S, v) <= dv) || (S.lt_prune && lt_prunes(p, S, v, dv))) {
                     // a table hub, which outranks h, lies on a shortest h-v path:
                     // v gets no label and is not expanded (Sec. 4.3)
                     ++pruned;
@@ -686,6 +723,31 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 for (uint32_t c = threadIdx.x; c < p.hc_stride; c += TPB)
                     S.hch[c] = __ldg(&p.hc[size_t(h) * p.hc_stride + c]);
             if (threadIdx.x == 0) S.prune = prune;
+            // the label table of earlier phases: hash the root's labels in it
+            bool lt_prune = p.lt_off && h >= p.lt_hubs;
+            uint64_t lt_a = 0, lt_b = 0;
+            if (lt_prune) {
+                const uint32_t ch = __ldg(&p.vert_at[h]);
+                lt_a = __ldg(&p.lt_off[ch]);
+                lt_b = __ldg(&p.lt_off[ch + 1]);
+                lt_prune = lt_b - lt_a <= LTH_MAX;  // uniform: every thread reads the same
+            }
+            if (lt_prune) {
+                for (uint32_t i = threadIdx.x; i < LTH_SLOTS; i += TPB) S.lth_key[i] = 0;
+                __syncthreads();
+                const uint64_t a = lt_a;
+                const uint32_t cnt = uint32_t(lt_b - lt_a);
+                for (uint32_t i = threadIdx.x; i < cnt; i += TPB) {
+                    const uint32_t c = __ldg(&p.lt_hp[a + i]);
+                    for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
+                        if (atomicCAS(&S.lth_key[sx], 0u, c + 1) == 0u) {
+                            S.lth_val[sx] = __ldg(&p.lt_d[a + i]);
+                            break;
+                        }
+                    }
+                }
+            }
+            if (threadIdx.x == 0) S.lt_prune = lt_prune;
             if (threadIdx.x == 0) {
                 S.cur_n = 1;
                 S.nxt_n = 0;
