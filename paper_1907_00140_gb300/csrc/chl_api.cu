@@ -315,7 +315,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     std::vector<uint32_t> pending;  // roots still to build (after a full buffer)
     std::vector<std::pair<uint32_t, uint32_t>> phases;
     LabelCSR lt;  // labels of earlier phases (hybrid)
-    bool use_lt = false, hybrid = false;
+    bool use_lt = false, hybrid = false, hybrid_off = false;
     uint32_t claimed_upto = 0;
     bool first = true;
 
@@ -403,7 +403,11 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     // used, so that it stays fresh; before the switch it grows fourfold.
     hybrid = rb == 0 && P.eta && !(o.flags & CHL_FLAG_NO_HYBRID) && re > P.eta;
     phases.clear();
-    phases.push_back(hybrid ? std::make_pair(0u, P.eta) : std::make_pair(rb, re));
+    // the first phase holds the Common Label Table's own trees (unpruned) and
+    // enough others to fill the slots
+    phases.push_back(hybrid ? std::make_pair(0u, uint32_t(std::min<uint64_t>(
+                                                     re, uint64_t(P.eta) + uint64_t(P.slots) * 2)))
+                            : std::make_pair(rb, re));
     for (size_t ph = 0; ph < phases.size(); ++ph) {
     const uint32_t pb = phases[ph].first, pe = phases[ph].second;
     const uint64_t exp0 = agg[0], T0 = T;
@@ -539,10 +543,16 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     // The switch of Sec. 4.3: label pruning starts once a phase's trees explore
     // many vertices per label (Psi = expansions / labels above PSI_TH); before
     // that, the per-vertex table query would cost more than it saves.
-    if (hybrid && !use_lt && T > T0 && double(agg[0] - exp0) / double(T - T0) > PSI_TH) use_lt = true;
+    if (hybrid && !use_lt && T > T0) {
+        const double psi = double(agg[0] - exp0) / double(T - T0);
+        if (psi > PSI_TH) use_lt = true;
+        // far down the ranking and still cheap trees: the rest is one phase
+        else if (pe >= uint64_t(P.slots) * 8 && psi < PSI_TH / 2) hybrid_off = true;
+    }
     if (hybrid && pe < re) {
         const uint64_t step_min = uint64_t(P.slots) * 2;
-        const uint64_t nx = std::max<uint64_t>(uint64_t(pe) * (use_lt ? 2 : 4), pe + step_min);
+        const uint64_t nx = hybrid_off ? re
+                                       : std::max<uint64_t>(uint64_t(pe) * (use_lt ? 2 : 4), pe + step_min);
         phases.push_back({pe, uint32_t(std::min<uint64_t>(nx, re))});
     }
     if (use_lt && ph + 1 < phases.size()) {
