@@ -436,7 +436,8 @@ def main():
         "labels": int(T), "als": T / g.n,
         "trees_per_s": g.n / (float(np.mean(build_ms)) / 1000.0),
         "explored": {"expanded": stats["expanded"], "arcs": stats["arcs"],
-                     "trivial": stats["trivial"]},
+                     "trivial": stats["trivial"], "pruned": stats["pruned"],
+                     "phases": stats["phases"], "label_table_phases": stats["label_table_phases"]},
         "gpu_launches": int(max(launches)),
         "clocks": clk,
     }
@@ -481,24 +482,47 @@ def main():
     eta = 16 if eta == 0 else eta
     wu_plain = work_units(name)
     wu = work_units(f"{name}/clt{eta}") if eta > 0 else wu_plain
+    hybrid = stats.get("label_table_phases", 0) > 0
+    if hybrid:
+        # the label-pruned build: credited with sequential Algorithm 1's work,
+        # its floor (batched phases see staler tables; that overhead is not credited)
+        wu = work_units(f"{name}/pll")
     if wu and wu_plain:
         algo = 28.0 * wu["S"] + 16.0 * wu["A"] + 12.0 * wu_plain["T"]
         ach = algo / (float(np.mean(tree_ms)) / 1000.0) / 1e9
         arcs_step = float(res["explored"]["arcs"])
         res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                            "frac": ach / peak,
-                           "traffic": TREE_DRAM_BYTES_PER_ARC * arcs_step if arcs_step else None,
-                           "traffic_note": "DRAM bytes per relaxed arc from the ncu capture of the "
-                                           "tree kernel on rmat18 roots [1000, 2216) "
-                                           f"({TREE_DRAM_BYTES_PER_ARC} B), times the arcs one "
-                                           "step relaxes",
+                           "traffic": (TREE_DRAM_BYTES_PER_ARC * arcs_step
+                                       if arcs_step and not hybrid else None),
+                           "traffic_note": ("null: the per-arc capture is of the build "
+                                            "without label pruning" if hybrid else
+                                            "DRAM bytes per relaxed arc from the ncu capture of the "
+                                            "tree kernel on rmat18 roots [1000, 2216) "
+                                            f"({TREE_DRAM_BYTES_PER_ARC} B), times the arcs one "
+                                            "step relaxes"),
                            "peak_kind": peak_kind,
                            "kernel": "plant_trees_kernel",
                            "algorithmic_bytes": algo,
-                           "units": (f"oracle Algorithm 3 pruned by the Common Label Table of {eta} hubs"
+                           "units": ("oracle sequential Algorithm 1 (the label-pruned build's floor)"
+                                     if hybrid else
+                                     f"oracle Algorithm 3 pruned by the Common Label Table of {eta} hubs"
                                      if eta > 0 else "oracle Algorithm 3")}
 
-    if not args.no_extras:
+    if not args.no_extras and stats.get("label_table_phases", 0) > 0:
+        # ---- plain form of the hybrid build: the whole build, one launch per root
+        torch.cuda.synchronize(dev)
+        Lp = chl.build_labels(DG, R, mode=1, **{k: v for k, v in opts.items() if k != "slots"})
+        torch.cuda.synchronize(dev)
+        s = Lp.stats()
+        Lp.free()
+        res["plain"] = {"tree_s": s["tree_ms"] / 1000.0, "roots_timed": g.n,
+                        "batched_tree_s": float(np.mean(tree_ms)) / 1000.0,
+                        "speedup_batched_vs_plain": s["tree_ms"] / float(np.mean(tree_ms)),
+                        "phases": s["phases"], "label_table_phases": s["label_table_phases"],
+                        "how": "mode=1 (one CTA per launch, one launch per root) over every root, "
+                               "with the same hybrid phases and pruning"}
+    elif not args.no_extras:
         # ---- plain one-root-per-launch form on stratified samples
         n = g.n
         est, timed, table = 0.0, 0, 0.0

@@ -173,6 +173,9 @@ typedef struct {
  *   pruned         expansions cut by the Common Label Table (all trees)
  *   table_ms       device time of building the Common Label Table (its trees
  *                  and the table fill; part of tree_ms), 0 without a table
+ *   phases         tree phases run (1 unless the build is hybrid)
+ *   label_table_phases  phases whose trees pruned with the label table of the
+ *                  earlier ones (0: the switch threshold was never passed)
  */
 typedef struct {
     uint64_t trees;
@@ -188,6 +191,8 @@ typedef struct {
     uint64_t buckets;
     uint64_t pruned;
     double table_ms;
+    uint64_t phases;
+    uint64_t label_table_phases;
 } chl_build_stats;
 
 /*
@@ -214,7 +219,9 @@ chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opt
  * of about four roots per tree slot (every (n/K)-th rank position, so the
  * sample has the build's mix of large and small trees) for candidate bucket
  * widths, then block sizes, then window sizes (coordinate search), and the
- * fastest is kept.
+ * fastest is kept. For a whole build (no root range set in base) the block
+ * size is then settled by two whole builds (512 and 1024 threads), since the
+ * hybrid phases prune later trees far below the sample's sizes.
  *   g, rank, stream   as for chl_build
  *   base              fields set (non-zero) are kept fixed; NULL = tune all
  *   best              receives base with threads_per_tree, bucket_delta and

@@ -18,7 +18,11 @@ With the Common Label Table (Sec. 4.3) the trees explore less; the entry
 "<workload>/clt<eta>" holds S and A of Algorithm 3 pruned by the table of the
 eta most important hubs (the table's own trees included), same sampling.
 
-Usage:  python oracle/work_units.py [workload[/clt<eta>] ...]   (writes oracle/work_units.json)
+The entry "<workload>/pll" holds S and A of sequential Algorithm 1 (every
+tree pruned by distance queries over all labels of the hubs ranked above its
+root): the work floor of the label-pruned (hybrid) build, exact.
+
+Usage:  python oracle/work_units.py [workload[/clt<eta>|/pll] ...]   (writes oracle/work_units.json)
 """
 import json
 import os
@@ -96,14 +100,27 @@ def units(name, per_stratum=96, threads=None, exact_below=5000, seed=1, pll_belo
     return out
 
 
+def pll_units(name):
+    g, rank = W.load(name)
+    L, st = O.build_labels(g, rank, "pll", with_stats=True)
+    return {"n": int(g.n), "arcs": int(g.num_arcs), "T": int(L.total), "T_exact": True,
+            "S": float(st[:, 0].sum()), "A": float(st[:, 1].sum()), "S_stderr": 0.0, "A_stderr": 0.0,
+            "roots_sampled": int(g.n), "exact": True,
+            "method": "sequential Algorithm 1 over all roots (pruned Dijkstra with rank and "
+                      "distance queries over all higher-ranked labels)"}
+
+
 def main(names):
     data = {}
     if os.path.exists(OUT):
         data = json.load(open(OUT))
     for name in names:
         t = time.time()
-        base, _, clt = name.partition("/clt")
-        data[name] = units(base, eta=int(clt) if clt else 0)
+        if name.endswith("/pll"):
+            data[name] = pll_units(name[:-4])
+        else:
+            base, _, clt = name.partition("/clt")
+            data[name] = units(base, eta=int(clt) if clt else 0)
         data[name]["seconds"] = round(time.time() - t, 1)
         print(name, json.dumps(data[name]), flush=True)
         with open(OUT, "w") as f:

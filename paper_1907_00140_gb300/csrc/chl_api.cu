@@ -316,6 +316,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     std::vector<std::pair<uint32_t, uint32_t>> phases;
     LabelCSR lt;  // labels of earlier phases (hybrid)
     bool use_lt = false, hybrid = false, hybrid_off = false;
+    uint64_t lt_phases = 0;
     uint32_t claimed_upto = 0;
     bool first = true;
 
@@ -411,6 +412,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     for (size_t ph = 0; ph < phases.size(); ++ph) {
     const uint32_t pb = phases[ph].first, pe = phases[ph].second;
     const uint64_t exp0 = agg[0], T0 = T;
+    if (lt.offsets) ++lt_phases;
     first = true;
     pending.clear();
     for (int attempt = 0;; ++attempt) {
@@ -618,6 +620,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     L->stats.tree_ms = ms_tree;
     L->stats.sort_ms = ms_sort;
     L->stats.table_ms = ms_table;
+    L->stats.phases = phases.size();
+    L->stats.label_table_phases = lt_phases;
     L->stats.launches = uint64_t(launches);
     csr = LabelCSR{};
     *out = L;
@@ -1067,6 +1071,24 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     best->bucket_delta = int32_t(bestP.delta);
     best->window_buckets = int32_t(bestP.nwin);
     best->slots = o.slots;  // 0 keeps the memory-budgeted default at build time
+    // A whole build runs in hybrid phases whose pruned trees are far smaller
+    // than the sample's: the block size is settled by whole builds.
+    if (!o.threads_per_tree && !o.root_begin && !o.root_end && !(o.flags & CHL_FLAG_NO_HYBRID)) {
+        double best_build = -1.0;
+        int best_tpt = bestP.tpt;
+        for (int t : {512, 1024}) {
+            chl_build_opts q = *best;
+            q.threads_per_tree = t;
+            chl_labels *Lt = nullptr;
+            st = chl_build(g, rank, &q, stream, &Lt);
+            if (st != CHL_OK) goto done;
+            const double ms = Lt->stats.tree_ms;
+            chl_labels_free(Lt);
+            ++trials;
+            if (best_build < 0 || ms < best_build) { best_build = ms; best_tpt = t; }
+        }
+        best->threads_per_tree = best_tpt;
+    }
     if (report) {
         report->trials = trials;
         report->sample_roots = K;
