@@ -489,6 +489,9 @@ def main():
         wu = work_units(f"{name}/pll")
     if wu and wu_plain:
         algo = 28.0 * wu["S"] + 16.0 * wu["A"] + 12.0 * wu_plain["T"]
+        if hybrid:
+            # plus the label entries (hub, dist: 8 B) its distance queries read
+            algo += 8.0 * wu.get("Q", 0.0)
         ach = algo / (float(np.mean(tree_ms)) / 1000.0) / 1e9
         arcs_step = float(res["explored"]["arcs"])
         res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -546,6 +549,7 @@ def main():
                         "speedup_batched_vs_plain": est / (float(np.mean(tree_ms)) / 1000.0),
                         "how": "mode=1 (one CTA per launch, one launch per root) on 8 "
                                "consecutive roots per rank-position stratum, scaled by stratum size"}
+    if not args.no_extras:
         # ---- e2e through the C ABI with host buffers
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
 

@@ -102,8 +102,9 @@ def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
     roots: None = every vertex in descending rank; else only labels with hub
     in `roots` are produced (each tree is independent, Sec. 4.2).
     tie_seed != 0 randomises the pop order of equal-distance vertices.
-    Returns Labels, or (Labels, stats[k,3] = settled, arcs scanned, labels per
-    root) when with_stats.
+    Returns Labels, or (Labels, stats[k,4] = settled, arcs scanned, labels per
+    root, label entries read by the distance queries (Algorithm 1 only)) when
+    with_stats.
     """
     lib = _load()
     n = int(g.n)
@@ -114,7 +115,7 @@ def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
     else:
         rarr = _u(roots, np.uint32)
         nroots, rptr = len(rarr), rarr.ctypes.data
-    stats = np.zeros((nroots, 3), np.uint64) if with_stats else None
+    stats = np.zeros((nroots, 4), np.uint64) if with_stats else None
     out = _Labels()
     rc = lib.orc_build(n, row.ctypes.data, col.ctypes.data, w.ctypes.data, rank.ctypes.data,
                        METHODS[method], rptr, nroots if rarr is not None else 0,

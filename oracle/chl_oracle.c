@@ -234,7 +234,9 @@ typedef struct {
     uint32_t eta;
 } graph;
 
-typedef struct { uint64_t settled, arcs, labels; } root_stats;
+/* per root: vertices settled, arcs scanned, labels, and (Algorithm 1 only) label
+   entries read by its distance queries */
+typedef struct { uint64_t settled, arcs, labels, qentries; } root_stats;
 
 static int emit(workspace *ws, uint32_t v, uint32_t h, uint64_t d) {
     if (d >= UINT32_MAX) { ws->overflow = 1; d = UINT32_MAX - 1; }
@@ -385,7 +387,7 @@ static int build_pll(const graph *g, const uint32_t *roots, uint64_t nroots, uin
     for (uint64_t ri = 0; ri < nroots && !rc; ++ri) {
         const uint32_t h = roots[ri];
         const uint32_t Rh = g->rank[h];
-        uint64_t settled = 0, arcs = 0, nl = 0;
+        uint64_t settled = 0, arcs = 0, nl = 0, qe = L[h].len;
         /* line 1: LR = hash(L_h) */
         for (uint32_t i = 0; i < L[h].len; ++i) LR[L[h].hub[i]] = L[h].dist[i];
         uint64_t *delta = ws.dist;
@@ -400,6 +402,7 @@ static int build_pll(const graph *g, const uint32_t *roots, uint64_t nroots, uin
             /* line 6: DQ(v, h, delta_v, LR, L_v) */
             int dq = 0;
             for (uint32_t i = 0; i < L[v].len && !dq; ++i) {
+                ++qe;
                 uint64_t dh = LR[L[v].hub[i]];
                 if (dh != INF64 && (uint64_t)L[v].dist[i] + dh <= delta[v]) dq = 1;
             }
@@ -421,7 +424,10 @@ static int build_pll(const graph *g, const uint32_t *roots, uint64_t nroots, uin
         }
         for (uint32_t i = 0; i < L[h].len; ++i) LR[L[h].hub[i]] = INF64;
         ws_reset(&ws);
-        if (stats) { stats[ri].settled = settled; stats[ri].arcs = arcs; stats[ri].labels = nl; }
+        if (stats) {
+            stats[ri].settled = settled; stats[ri].arcs = arcs; stats[ri].labels = nl;
+            stats[ri].qentries = qe;
+        }
     }
     for (uint32_t v = 0; v < n && !rc; ++v)
         for (uint32_t i = 0; i < L[v].len; ++i)

@@ -20,7 +20,9 @@ eta most important hubs (the table's own trees included), same sampling.
 
 The entry "<workload>/pll" holds S and A of sequential Algorithm 1 (every
 tree pruned by distance queries over all labels of the hubs ranked above its
-root): the work floor of the label-pruned (hybrid) build, exact.
+root): the work floor of the label-pruned (hybrid) build, exact; Q counts the
+label entries its distance queries read (the root's list once per tree, then
+the settled vertex's list up to the first witness).
 
 Usage:  python oracle/work_units.py [workload[/clt<eta>|/pll] ...]   (writes oracle/work_units.json)
 """
@@ -104,7 +106,8 @@ def pll_units(name):
     g, rank = W.load(name)
     L, st = O.build_labels(g, rank, "pll", with_stats=True)
     return {"n": int(g.n), "arcs": int(g.num_arcs), "T": int(L.total), "T_exact": True,
-            "S": float(st[:, 0].sum()), "A": float(st[:, 1].sum()), "S_stderr": 0.0, "A_stderr": 0.0,
+            "S": float(st[:, 0].sum()), "A": float(st[:, 1].sum()), "Q": float(st[:, 3].sum()),
+            "S_stderr": 0.0, "A_stderr": 0.0,
             "roots_sampled": int(g.n), "exact": True,
             "method": "sequential Algorithm 1 over all roots (pruned Dijkstra with rank and "
                       "distance queries over all higher-ranked labels)"}

@@ -549,7 +549,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         const double psi = double(agg[0] - exp0) / double(T - T0);
         if (psi > PSI_TH) use_lt = true;
         // far down the ranking and still cheap trees: the rest is one phase
-        else if (pe >= uint64_t(P.slots) * 8 && psi < PSI_TH / 2) hybrid_off = true;
+        else if (pe >= std::max<uint64_t>(uint64_t(P.slots) * 8, 8192) && psi < PSI_TH / 2)
+            hybrid_off = true;
     }
     if (hybrid && pe < re) {
         const uint64_t step_min = uint64_t(P.slots) * 2;

@@ -271,3 +271,26 @@ def test_query_rejects_bad_vertex(ba2k):
     with pytest.raises(chl.ChlError) as e:
         L.query(np.array([[0, g.n]], np.uint32))
     assert e.value.status == chl.CHL_EINVAL
+
+
+def test_hybrid_phases_are_exact():
+    """A scale-free build deep enough to pass the Psi switch prunes its later
+    phases with the label table of the earlier ones (Sec. 4.3) and still equals
+    the oracle; the single-phase build gives the same labels with more work."""
+    g = W.rmat(14, 16, seed=14, wlo=1, whi=255)
+    rank = W.degree_rank(g)
+    ref = O.build_labels(g, rank, "plant", threads=16)
+    G, R = DG(g), dev(rank)
+    for opts in (dict(), dict(threads_per_tree=256), dict(threads_per_tree=1024, bucket_delta=2)):
+        L = chl.build_labels(G, R, **opts)
+        st = L.stats()
+        assert st["phases"] > 1 and st["label_table_phases"] >= 1, st
+        assert_same(ref, *L.to_numpy())
+    one = chl.build_labels(G, R, flags=chl.CHL_FLAG_NO_HYBRID)
+    s1 = one.stats()
+    assert s1["phases"] == 1 and s1["label_table_phases"] == 0
+    assert s1["arcs"] > st["arcs"]
+    assert_same(ref, *one.to_numpy())
+    # a root range that does not start at the top runs as one phase
+    part = chl.build_labels(G, R, root_begin=10, root_end=3000)
+    assert part.stats()["phases"] == 1
