@@ -120,6 +120,17 @@ typedef struct chl_labels chl_labels;
  *                          eta = 16; negative = no table; at most
  *                          CHL_MAX_COMMON_HUBS. Requested trees of the eta
  *                          most important roots are built unpruned.
+ *   pruned_bucket_delta    bucket width of the hybrid phases that prune with
+ *                          the labels of earlier phases (their trees are
+ *                          small, so wide buckets save rounds); 0 = the power
+ *                          of two nearest twice the mean arc weight
+ *   psi_threshold          Psi_th of the hybrid switch (Sec. 4.3): once a
+ *                          phase expands more than Psi_th vertices per label it
+ *                          generates, the later phases prune with the labels of
+ *                          the earlier ones. 0 = 16 (the paper's 16-node runs
+ *                          use 100 on scale-free and 500 on road networks,
+ *                          where the switch also costs communication);
+ *                          must not be negative
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
@@ -140,6 +151,11 @@ typedef struct chl_labels chl_labels;
    earlier phases' hubs form a rank-closed set, so the labels stay canonical
    and no cleaning pass is needed). */
 #define CHL_FLAG_NO_HYBRID 4
+/* chl_build_opts.flags: in the phases that prune with the labels of earlier
+   phases, keep every root's labels in a per-slot array indexed by hub (by
+   default only roots with more than 512 such labels do; the others hash them
+   in shared memory). The labels are the same either way. */
+#define CHL_FLAG_DENSE_ROOT_LABELS 8
 
 typedef struct {
     uint32_t root_begin;
@@ -152,6 +168,8 @@ typedef struct {
     int32_t flags;
     uint64_t label_capacity;
     int32_t common_hubs;
+    int32_t pruned_bucket_delta;
+    float psi_threshold;
 } chl_build_opts;
 
 #define CHL_MAX_COMMON_HUBS 64

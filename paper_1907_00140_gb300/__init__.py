@@ -24,7 +24,7 @@ import numpy as np
 
 __all__ = [
     "build", "lib", "Server", "CHL_OK", "CHL_EINVAL", "CHL_ENOMEM", "CHL_ECUDA", "CHL_ETIMEOUT",
-    "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "CHL_FLAG_PARENTS", "CHL_FLAG_NO_HYBRID", "ChlError", "chl_csr", "chl_build_opts",
+    "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "CHL_FLAG_PARENTS", "CHL_FLAG_NO_HYBRID", "CHL_FLAG_DENSE_ROOT_LABELS", "ChlError", "chl_csr", "chl_build_opts",
     "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
     "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
     "chl_query_noalloc", "chl_tune", "chl_tune_report", "tune",
@@ -44,6 +44,7 @@ CHL_MEM_DEVICE, CHL_MEM_HOST = 0, 1
 CHL_FLAG_WIDE_KEYS = 1
 CHL_FLAG_PARENTS = 2
 CHL_FLAG_NO_HYBRID = 4
+CHL_FLAG_DENSE_ROOT_LABELS = 8
 _NAMES = {0: "CHL_OK", 1: "CHL_EINVAL", 2: "CHL_ENOMEM", 3: "CHL_ECUDA", 4: "CHL_ETIMEOUT",
           5: "CHL_EOVERFLOW"}
 
@@ -94,7 +95,8 @@ class chl_build_opts(C.Structure):
     _fields_ = [("root_begin", C.c_uint32), ("root_end", C.c_uint32),
                 ("threads_per_tree", C.c_int32), ("bucket_delta", C.c_int32),
                 ("window_buckets", C.c_int32), ("slots", C.c_int32), ("mode", C.c_int32),
-                ("flags", C.c_int32), ("label_capacity", C.c_uint64), ("common_hubs", C.c_int32)]
+                ("flags", C.c_int32), ("label_capacity", C.c_uint64), ("common_hubs", C.c_int32),
+                ("pruned_bucket_delta", C.c_int32), ("psi_threshold", C.c_float)]
 
 
 class chl_tune_report(C.Structure):

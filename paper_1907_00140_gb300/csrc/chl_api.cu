@@ -2,6 +2,7 @@
 // memory, the build driver (graph preparation, persistent tree launch with
 // retry on a full label buffer, label assembly) and the query entry point.
 #include <algorithm>
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -30,18 +31,51 @@ cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cu
 
 namespace {
 
-// device control block of one tree launch
+// device control block of one tree launch; the two counters every tree
+// updates sit on cache lines of their own
 struct Control {
-    unsigned int next_root;
-    unsigned int failed_count;
+    alignas(128) unsigned int next_root;
+    alignas(128) unsigned long long out_count;
+    unsigned long long out_valid;
+    alignas(128) unsigned int failed_count;
+    unsigned int list_n;  // roots listed by the trivial-root split
     int flags[2];
-    unsigned long long out_count;
     unsigned long long stats[7];
 };
+
+void bind_control(TreeLaunch &tl, Control *ctl) {
+    tl.out_count = &ctl->out_count;
+    tl.out_valid = &ctl->out_valid;
+    tl.next_root = &ctl->next_root;
+    tl.failed_count = &ctl->failed_count;
+    tl.flags = ctl->flags;
+    tl.stats = ctl->stats;
+}
+
+// records of an attempt that are whole trees
+uint64_t records_kept(const Control &c) { return c.flags[1] ? c.out_valid : c.out_count; }
+
+// label record buffers (vertex, hub, distance, optional parent): moved to a
+// capacity of ncap records, keeping the first T
+cudaError_t grow_records(void **bufs, int nbufs, uint64_t T, uint64_t ncap, cudaStream_t s) {
+    for (int k = 0; k < nbufs; ++k) {
+        void *nb = nullptr;
+        cudaError_t e = cudaMallocAsync(&nb, ncap * 4, s);
+        if (!e && T) e = cudaMemcpyAsync(nb, bufs[k], T * 4, cudaMemcpyDeviceToDevice, s);
+        if (e) {
+            if (nb) cudaFreeAsync(nb, s);
+            return e;
+        }
+        cudaFreeAsync(bufs[k], s);
+        bufs[k] = nb;
+    }
+    return cudaSuccess;
+}
 
 struct Params {
     int tpt;
     uint32_t delta;
+    uint32_t delta_lt;  // bucket width of the phases that prune with the label table
     uint32_t nwin;
     int slots;
     int kb;  // bytes per tree key: 4 or 8
@@ -66,6 +100,9 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     while (double(d) * 1.5 < dflt && d < (1u << 30)) d <<= 1;
     if (o.bucket_delta > 0) d = uint32_t(o.bucket_delta);
     p.delta = d;
+    uint32_t dl = 1;
+    while (double(dl) * 1.5 < 2.0 * g.w_mean && dl < (1u << 30)) dl <<= 1;
+    p.delta_lt = o.pruned_bucket_delta > 0 ? uint32_t(o.pruned_bucket_delta) : dl;
     p.nwin = o.window_buckets > 0 ? uint32_t(o.window_buckets) : 32;
     // 4-byte keys hold distances up to 2^31 - 2; every tentative distance of a
     // tree search is at most w_max * n (a simple path plus one arc)
@@ -82,8 +119,9 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words);
     if (per_sm < 1) per_sm = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
-    // slot state per vertex: key + round tag 4 + (4 + nwin) lists of 4 bytes
-    const double per_slot = (p.kb + 4.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
+    // slot state per vertex: key + round tag 4 + (4 + nwin) lists of 4 bytes,
+    // + 4 for the root's labels of a hybrid build
+    const double per_slot = (p.kb + 8.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
     const double budget = 0.35 * double(free_bytes);
     long long cap = (long long)(budget / per_slot);
     if (o.slots <= 0 && slots > cap) slots = cap;
@@ -104,6 +142,13 @@ struct DevBuf {
     }
 };
 
+void set_delta(TreeLaunch &tl, uint32_t delta) {
+    tl.delta = delta;
+    tl.delta_shift = -1;
+    for (int b = 0; b < 32; ++b)
+        if (delta == (1u << b)) tl.delta_shift = b;
+}
+
 // Per-slot search state of the tree kernel, in its idle form: keys all ones
 // (unreached), tags and instance counters 0.
 struct SlotState {
@@ -122,10 +167,7 @@ struct SlotState {
         return cudaSuccess;
     }
     void fill(const Params &P, uint32_t n, TreeLaunch &tl) const {
-        tl.delta = P.delta;
-        tl.delta_shift = -1;
-        for (int b = 0; b < 32; ++b)
-            if (P.delta == (1u << b)) tl.delta_shift = b;
+        set_delta(tl, P.delta);
         tl.nwin = P.nwin;
         tl.key = key.p;
         tl.key_bytes = P.kb;
@@ -144,8 +186,8 @@ struct SlotState {
     }
 };
 
-// expansions per label of a phase above which the next phases prune with the
-// label table of the earlier ones
+// default expansions per label of a phase above which the next phases prune
+// with the label table of the earlier ones
 constexpr double PSI_TH = 16.0;
 
 void free_csr(LabelCSR &c, cudaStream_t s) {
@@ -223,12 +265,8 @@ chl_status build_common_table(const RankGraph &rg, const Params &P, const SlotSt
     tl.out_h = (uint32_t *)b_oh.p;
     tl.out_d = (uint32_t *)b_od.p;
     tl.out_cap = cap;
-    tl.out_count = &ctl->out_count;
-    tl.next_root = &ctl->next_root;
+    bind_control(tl, ctl);
     tl.failed = (uint32_t *)b_fail.p;
-    tl.failed_count = &ctl->failed_count;
-    tl.flags = ctl->flags;
-    tl.stats = ctl->stats;
     CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
     ++*launches;
     CUDA_TRY(cudaMemcpyAsync(&hc, ctl, sizeof(Control), cudaMemcpyDeviceToHost, s));
@@ -282,8 +320,10 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
     if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
         return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
-    if (o.bucket_delta < 0 || o.slots < 0) return set_error(CHL_EINVAL, "negative option");
-    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS | CHL_FLAG_NO_HYBRID))
+    if (o.bucket_delta < 0 || o.slots < 0 || o.pruned_bucket_delta < 0 || !(o.psi_threshold >= 0.0f))
+        return set_error(CHL_EINVAL, "negative option");
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS | CHL_FLAG_NO_HYBRID |
+                           CHL_FLAG_DENSE_ROOT_LABELS))
         return set_error(CHL_EINVAL, "unknown bit in flags");
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -294,7 +334,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const uint64_t m2 = g->num_arcs;
     const uint64_t *d_row = g->row_ptr;
     const uint32_t *d_col = g->col, *d_w = g->w, *d_rank = rank;
-    DevBuf b_row, b_col, b_w, b_rank, b_ctl, b_ov, b_oh, b_od, b_op, b_fail, b_roots;
+    DevBuf b_row, b_col, b_w, b_rank, b_ctl, b_ov, b_oh, b_od, b_op, b_fail, b_roots, b_ltroot;
     const bool parents = (o.flags & CHL_FLAG_PARENTS) != 0;
     uint32_t *csr_parent = nullptr;
     SlotState slot;
@@ -317,15 +357,27 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     LabelCSR lt;  // labels of earlier phases (hybrid)
     bool use_lt = false, hybrid = false, hybrid_off = false;
     uint64_t lt_phases = 0;
+    const double psi_th = o.psi_threshold > 0.0f ? double(o.psi_threshold) : PSI_TH;
     uint32_t claimed_upto = 0;
     bool first = true;
+    bool listed = false;             // the current attempt runs from the device root list
+    std::vector<uint32_t> list_h;    // ... whose host copy, when needed
+    uint32_t list_n = 0;
+    // CHL_TRACE=1 prints one line per phase to stderr (host clock around the
+    // stream synchronisations the build already makes)
+    const bool trace = std::getenv("CHL_TRACE") && std::getenv("CHL_TRACE")[0] == '1';
+    auto now_ms = [] {
+        return std::chrono::duration<double, std::milli>(
+                   std::chrono::steady_clock::now().time_since_epoch()).count();
+    };
+    double t_ph = 0;
 
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     for (auto &e : ev) CUDA_TRY(cudaEventCreate(&e));
     CUDA_TRY(cudaEventRecord(ev[0], s));
     b_row.s = b_col.s = b_w.s = b_rank.s = b_ctl.s = s;
-    b_ov.s = b_oh.s = b_od.s = b_op.s = b_fail.s = b_roots.s = s;
+    b_ov.s = b_oh.s = b_od.s = b_op.s = b_fail.s = b_roots.s = b_ltroot.s = s;
 
     // inputs on the device
     if (g->mem == CHL_MEM_HOST) {
@@ -411,7 +463,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
                             : std::make_pair(rb, re));
     for (size_t ph = 0; ph < phases.size(); ++ph) {
     const uint32_t pb = phases[ph].first, pe = phases[ph].second;
-    const uint64_t exp0 = agg[0], T0 = T;
+    const uint64_t exp0 = agg[0], T0 = T, arc0 = agg[1];
+    const int ph_lt = lt.offsets ? 1 : 0;
+    if (trace) t_ph = now_ms();
     if (lt.offsets) ++lt_phases;
     first = true;
     pending.clear();
@@ -428,20 +482,50 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             tl.lt_hp = lt.hubpos;
             tl.lt_d = lt.dist;
             tl.lt_hubs = pb;
+            tl.lt_root = (uint32_t *)b_ltroot.p;
+            tl.lt_hash_max = (o.flags & CHL_FLAG_DENSE_ROOT_LABELS) ? 0 : 0xFFFFFFFFu;
+            set_delta(tl, P.delta_lt);
+        }
+        // the batched form first writes the labels of the phase's trivial
+        // roots and lists the others: room for one record per root
+        const bool split = first && o.mode == 0 && pe > pb;
+        if (split && cap < T + (pe - pb)) {
+            uint64_t ncap = cap;
+            while (ncap < T + (pe - pb)) ncap *= 2;
+            void *bufs[4] = {b_ov.p, b_oh.p, b_od.p, b_op.p};
+            CUDA_TRY(grow_records(bufs, parents ? 4 : 3, T, ncap, s));
+            b_ov.p = bufs[0];
+            b_oh.p = bufs[1];
+            b_od.p = bufs[2];
+            b_op.p = bufs[3];
+            cap = ncap;
         }
         tl.out_v = (uint32_t *)b_ov.p;
         tl.out_h = (uint32_t *)b_oh.p;
         tl.out_d = (uint32_t *)b_od.p;
         tl.out_p = (uint32_t *)b_op.p;
         tl.out_cap = cap;
-        tl.out_count = &ctl->out_count;
-        tl.next_root = &ctl->next_root;
+        bind_control(tl, ctl);
         tl.failed = (uint32_t *)b_fail.p;
-        tl.failed_count = &ctl->failed_count;
-        tl.flags = ctl->flags;
-        tl.stats = ctl->stats;
+        // reset the control block but keep the running output count
+        {
+            Control c0{};
+            c0.out_count = T;
+            CUDA_TRY(cudaMemcpyAsync(ctl, &c0, sizeof(Control), cudaMemcpyHostToDevice, s));
+        }
         uint32_t count = 0;
-        if (first) {
+        listed = !first;
+        if (split) {
+            CUDA_TRY(launch_split_trivial(tl, pb, pe - pb, (uint32_t *)b_roots.p, &ctl->list_n, s));
+            ++launches;
+            CUDA_TRY(cudaMemcpyAsync(&list_n, &ctl->list_n, 4, cudaMemcpyDeviceToHost, s));
+            CUDA_TRY(cudaStreamSynchronize(s));
+            tl.root_list = (const uint32_t *)b_roots.p;
+            tl.root_begin = 0;
+            count = list_n;
+            listed = true;
+            list_h.clear();  // fetched if this attempt fails
+        } else if (first) {
             tl.root_list = nullptr;
             tl.root_begin = pb;
             count = pe - pb;
@@ -451,14 +535,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             tl.root_list = (const uint32_t *)b_roots.p;
             tl.root_begin = 0;
             count = uint32_t(pending.size());
+            list_h = pending;
         }
         tl.root_count = count;
-        // reset the control block but keep the running output count
-        {
-            Control c0{};
-            c0.out_count = T;
-            CUDA_TRY(cudaMemcpyAsync(ctl, &c0, sizeof(Control), cudaMemcpyHostToDevice, s));
-        }
         if (count) {
             if (o.mode == 1) {
                 // plain form: one launch per root, one CTA per launch; the claim
@@ -487,11 +566,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             st = set_error(CHL_ETIMEOUT, "a tree exceeded its round limit");
             goto done;
         }
-        if (hc.flags[0] == ERR_RESERVE_LIMIT) {
-            st = set_error(CHL_ETIMEOUT, "label buffer reservation did not converge");
-            goto done;
-        }
-        T = hc.out_count;
+        T = records_kept(hc);
         if (!hc.flags[1]) break;  // every root of this attempt fit
         // collect roots that failed or were never claimed, grow the buffer, go again
         {
@@ -499,57 +574,47 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             if (hc.failed_count)
                 CUDA_TRY(cudaMemcpyAsync(failed.data(), b_fail.p, size_t(hc.failed_count) * 4,
                                          cudaMemcpyDeviceToHost, s));
-            std::vector<uint32_t> prev = pending;
+            if (split) {
+                list_h.resize(count);
+                if (count)
+                    CUDA_TRY(cudaMemcpyAsync(list_h.data(), b_roots.p, size_t(count) * 4,
+                                             cudaMemcpyDeviceToHost, s));
+            }
             CUDA_TRY(cudaStreamSynchronize(s));
+            auto root_at = [&](uint32_t i) { return listed ? list_h[i] : pb + i; };
             claimed_upto = hc.next_root < count ? hc.next_root : count;
             if (o.mode == 1) {
                 // launches after the first failure claimed nothing: resume after it
                 claimed_upto = count;
                 if (!failed.empty()) {
                     for (uint32_t i = 0; i < count; ++i)
-                        if ((first ? pb + i : prev[i]) == failed[0]) { claimed_upto = i + 1; break; }
+                        if (root_at(i) == failed[0]) { claimed_upto = i + 1; break; }
                 }
             }
             pending = failed;
-            for (uint32_t i = claimed_upto; i < count; ++i)
-                pending.push_back(first ? pb + i : prev[i]);
+            for (uint32_t i = claimed_upto; i < count; ++i) pending.push_back(root_at(i));
             first = false;
             if (attempt > 40) {
                 st = set_error(CHL_ENOMEM, "label buffer cannot grow further");
                 goto done;
             }
-            uint64_t ncap = cap * 2;
-            void *nv = nullptr, *nh = nullptr, *nd = nullptr;
-            CUDA_TRY(cudaMallocAsync(&nv, ncap * 4, s));
-            CUDA_TRY(cudaMallocAsync(&nh, ncap * 4, s));
-            CUDA_TRY(cudaMallocAsync(&nd, ncap * 4, s));
-            CUDA_TRY(cudaMemcpyAsync(nv, b_ov.p, T * 4, cudaMemcpyDeviceToDevice, s));
-            CUDA_TRY(cudaMemcpyAsync(nh, b_oh.p, T * 4, cudaMemcpyDeviceToDevice, s));
-            CUDA_TRY(cudaMemcpyAsync(nd, b_od.p, T * 4, cudaMemcpyDeviceToDevice, s));
-            if (parents) {
-                void *np = nullptr;
-                CUDA_TRY(cudaMallocAsync(&np, ncap * 4, s));
-                CUDA_TRY(cudaMemcpyAsync(np, b_op.p, T * 4, cudaMemcpyDeviceToDevice, s));
-                cudaFreeAsync(b_op.p, s);
-                b_op.p = np;
-            }
-            cudaFreeAsync(b_ov.p, s);
-            cudaFreeAsync(b_oh.p, s);
-            cudaFreeAsync(b_od.p, s);
-            b_ov.p = nv;
-            b_oh.p = nh;
-            b_od.p = nd;
-            cap = ncap;
+            void *bufs[4] = {b_ov.p, b_oh.p, b_od.p, b_op.p};
+            CUDA_TRY(grow_records(bufs, parents ? 4 : 3, T, cap * 2, s));
+            b_ov.p = bufs[0];
+            b_oh.p = bufs[1];
+            b_od.p = bufs[2];
+            b_op.p = bufs[3];
+            cap *= 2;
         }
     }
     // The switch of Sec. 4.3: label pruning starts once a phase's trees explore
-    // many vertices per label (Psi = expansions / labels above PSI_TH); before
+    // many vertices per label (Psi = expansions / labels above psi_th); before
     // that, the per-vertex table query would cost more than it saves.
     if (hybrid && !use_lt && T > T0) {
         const double psi = double(agg[0] - exp0) / double(T - T0);
-        if (psi > PSI_TH) use_lt = true;
+        if (psi > psi_th) use_lt = true;
         // far down the ranking and still cheap trees: the rest is one phase
-        else if (pe >= std::max<uint64_t>(uint64_t(P.slots) * 8, 8192) && psi < PSI_TH / 2)
+        else if (pe >= std::max<uint64_t>(uint64_t(P.slots) * 8, 8192) && psi < psi_th / 2)
             hybrid_off = true;
     }
     if (hybrid && pe < re) {
@@ -558,9 +623,14 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
                                        : std::max<uint64_t>(uint64_t(pe) * (use_lt ? 2 : 4), pe + step_min);
         phases.push_back({pe, uint32_t(std::min<uint64_t>(nx, re))});
     }
+    double t_tree = trace ? now_ms() - t_ph : 0;
     if (use_lt && ph + 1 < phases.size()) {
         // every label so far, as CSR, for the next phase's pruning
         free_csr(lt, s);
+        if (!b_ltroot.p) {
+            CUDA_TRY(cudaMallocAsync(&b_ltroot.p, size_t(P.slots) * n * 4, s));
+            CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, size_t(P.slots) * n * 4, s));
+        }
         int tl_long = 0;
         CUDA_TRY(assemble_labels(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
                                  (const uint32_t *)b_od.p, rg.vert_at, lt, &tl_long, s, &launches));
@@ -569,12 +639,22 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             goto done;
         }
     }
+    if (trace) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        std::fprintf(stderr,
+                     "chl phase %zu roots [%u, %u) table %d trees %.3f ms assemble %.3f ms "
+                     "expanded %llu arcs %llu labels %llu\n",
+                     ph, pb, pe, ph_lt, t_tree, now_ms() - t_ph - t_tree,
+                     (unsigned long long)(agg[0] - exp0), (unsigned long long)(agg[1] - arc0),
+                     (unsigned long long)(T - T0));
+    }
     }  // phases
     free_csr(lt, s);
     CUDA_TRY(cudaEventRecord(ev[2], s));
     // slot state and table are no longer needed: release them before assembly
     slot.release();
     table.buf.release();
+    b_ltroot.release();
 
     CUDA_TRY(assemble_labels(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
                              (const uint32_t *)b_od.p, rg.vert_at, csr, &too_long, s, &launches));
@@ -896,12 +976,8 @@ chl_status tree_trial(const RankGraph &rg, const Params &P, const CommonTable &t
     tl.out_h = (uint32_t *)b_oh.p;
     tl.out_d = (uint32_t *)b_od.p;
     tl.out_cap = cap;
-    tl.out_count = &ctl->out_count;
-    tl.next_root = &ctl->next_root;
+    bind_control(tl, ctl);
     tl.failed = (uint32_t *)b_fail.p;
-    tl.failed_count = &ctl->failed_count;
-    tl.flags = ctl->flags;
-    tl.stats = ctl->stats;
     CUDA_TRY(cudaEventRecord(e0, s));
     CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
     CUDA_TRY(cudaEventRecord(e1, s));
@@ -937,7 +1013,8 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     if (o.mode != 0) return set_error(CHL_EINVAL, "chl_tune tunes the batched mode (mode 0)");
     if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
         return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
-    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS | CHL_FLAG_NO_HYBRID))
+    if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS | CHL_FLAG_NO_HYBRID |
+                           CHL_FLAG_DENSE_ROOT_LABELS))
         return set_error(CHL_EINVAL, "unknown bit in flags");
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;

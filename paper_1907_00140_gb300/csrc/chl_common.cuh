@@ -68,6 +68,10 @@ struct TreeLaunch {
     const uint32_t *lt_hp;
     const uint32_t *lt_d;
     uint32_t lt_hubs;
+    // per slot [n], all ones when idle, or null: the root's table labels by
+    // hub position, for roots with more of them than the shared-memory hash holds
+    uint32_t *lt_root;
+    uint32_t lt_hash_max;  // roots with more table labels than this use lt_root
     // slot state: slot s owns [s*n, (s+1)*n) of each array
     void *key;          // tree keys, all ones when idle (see chl_tree.cu)
     int key_bytes;      // 4 (distances provably < 2^31 - 1) or 8
@@ -80,7 +84,8 @@ struct TreeLaunch {
     uint32_t *out_d;    // distance
     uint32_t *out_p;    // SPT parent (caller vertex id), or null: no parents
     unsigned long long out_cap;
-    unsigned long long *out_count;
+    unsigned long long *out_count;  // next free record (may pass out_cap once a tree failed)
+    unsigned long long *out_valid;  // records written, set by the first tree that failed
     // control
     unsigned int *next_root;
     uint32_t *failed;          // roots whose labels did not fit
@@ -89,12 +94,17 @@ struct TreeLaunch {
     unsigned long long *stats; // [0] expanded [1] arcs [2] trivial [3] trees [4] rounds [5] buckets [6] pruned
 };
 
-enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2, ERR_RESERVE_LIMIT = 3 };
+enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2 };
 
 // launches (defined in chl_tree.cu)
 cudaError_t launch_plant_trees(const TreeLaunch &p, int threads_per_tree, int slots,
                                cudaStream_t s);
 int plant_max_slots_per_sm(int threads_per_tree, uint32_t fin_words);
+// roots [begin, begin + count): the label of every trivial root is written to
+// the output (p.out_*, p.out_count; the caller guarantees room for count
+// records), the other roots are appended to list (*list_n of them)
+cudaError_t launch_split_trivial(const TreeLaunch &p, uint32_t begin, uint32_t count, uint32_t *list,
+                                 unsigned int *list_n, cudaStream_t s);
 // settled-filter words for n vertices that keep the CTAs per SM of fin_words = 0
 uint32_t plant_fin_words(int threads_per_tree, uint32_t n);
 // Common Label Table entries from label records of the table's trees

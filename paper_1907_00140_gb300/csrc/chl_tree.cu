@@ -39,9 +39,12 @@
 // end are final, so the tree stops when cnt = 0: exact at bucket granularity.
 //
 // Labels: after a tree stops, every touched vertex whose key is live gets
-// (vertex, root, dist); the tree reserves its output range with one CAS
-// (all-or-nothing, so a full buffer loses no partial tree), and the host
-// rebuilds failed roots after growing the buffer.
+// (vertex, root, dist); the tree reserves its output range with one
+// atomicAdd. Ranges are handed out in increasing order, so those that fit the
+// buffer are a prefix of it: the first range that does not fit records where
+// that prefix ends, and it and every later tree give up their labels whole
+// (no partial tree is kept); the host rebuilds those roots after growing the
+// buffer.
 #include <cstdio>
 
 #include "chl_common.cuh"
@@ -51,7 +54,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t MAX_ROUNDS_PER_TREE = 1u << 26;
-constexpr uint32_t RESERVE_TRIES = 1u << 20;
 constexpr uint32_t NWIN_MAX = 64;
 constexpr int UNROLL = 4;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
@@ -128,6 +130,8 @@ struct Shared {
     int fuse_live;         // the current list's first stage also counts its live entries
     int prune;             // this tree prunes by the Common Label Table
     int lt_prune;          // ... and by the label table of earlier phases
+    int lt_dense;          // the root's table labels are in p.lt_root, not the hash
+    uint32_t qn;           // table queries queued by the current chunk
     uint32_t hch[CLT_MAX]; // table row of the root: d(h, c) per table hub c
     // the root's labels in the label table, hashed by hub position (key + 1)
     uint32_t lth_key[LTH_SLOTS];
@@ -405,26 +409,41 @@ __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared 
 // Table: the table is complete for a rank-closed set of hubs (Sec. 4.3). The
 // query must see every table label of h and of v: a vertex reached only past a
 // pruned one is left with a wrong distance and ancestor unless it is pruned
-// too, which the complete query guarantees (a partial one would not). A tree
-// whose root has more table labels than the hash holds does not use the table.
+// too, which the complete query guarantees (a partial one would not). The
+// root's table labels are hashed in shared memory, or, when more than the hash
+// holds, written into the slot's dense array p.lt_root by hub position.
 __device__ __forceinline__ uint32_t lth_slot(uint32_t hp) { return (hp * 2654435761u) >> 22; }
 
-__device__ __forceinline__ bool lt_prunes(const TreeLaunch &p, const Shared &S, uint32_t v,
-                                          uint32_t dv) {
+// One warp answers the query of one vertex: each lane takes every 32nd table
+// label of v (coalesced), looks its hub up in the root's hash, and the warp
+// stops at the first step where some lane found a witness.
+__device__ __forceinline__ bool lt_prunes_warp(const TreeLaunch &p, const Shared &S,
+                                               const uint32_t *rootd, uint32_t v, uint32_t dv,
+                                               int lane) {
     const uint32_t cv = __ldg(&p.vert_at[v]);
     const uint64_t a = __ldg(&p.lt_off[cv]), b = __ldg(&p.lt_off[cv + 1]);
-    for (uint64_t j = a; j < b; ++j) {
-        const uint32_t c = __ldg(&p.lt_hp[j]);
-        const uint32_t dcv = __ldg(&p.lt_d[j]);
-        if (dcv > dv) continue;
-        for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
-            const uint32_t key = S.lth_key[sx];
-            if (key == 0) break;
-            if (key == c + 1) {
-                if (uint64_t(S.lth_val[sx]) + dcv <= dv) return true;
-                break;
+    for (uint64_t j0 = a; j0 < b; j0 += 32) {
+        const uint64_t j = j0 + lane;
+        bool hit = false;
+        if (j < b) {
+            const uint32_t dcv = __ldg(&p.lt_d[j]);
+            if (dcv <= dv && rootd) {
+                // written by this CTA at tree start: a plain load
+                const uint32_t dhc = rootd[__ldg(&p.lt_hp[j])];
+                hit = dhc != NONE && uint64_t(dhc) + dcv <= dv;
+            } else if (dcv <= dv) {
+                const uint32_t c = __ldg(&p.lt_hp[j]);
+                for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
+                    const uint32_t key = S.lth_key[sx];
+                    if (key == 0) break;
+                    if (key == c + 1) {
+                        hit = uint64_t(S.lth_val[sx]) + dcv <= dv;
+                        break;
+                    }
+                }
             }
         }
+        if (__any_sync(0xffffffffu, hit)) return true;
     }
     return false;
 }
@@ -449,7 +468,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
         const uint32_t i = cb + threadIdx.x;
         uint64_t deg = 0, rs = 0;
         uint32_t dv = 0, vid = 0;
-        bool lv = false, ok = false;
+        bool lv = false, clean = false, cut = false, ask = false;
         if (i < n_cur) {
             const uint32_t v = cur[i];
             const KS k = __ldcg(&sl.key[v]);
@@ -459,19 +478,50 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                 rs = __ldg(&p.row[v]);
                 deg = __ldg(&p.row[v + 1]) - rs;
                 lv = is_live<K>(k, v, h);
+                clean = key_clean<K>(k);
                 if (v < p.fin_bits && uint64_t(dv) < t_lo + p.w_min)
                     atomicOr(&fin_bitmap[v >> 5], 1u << (v & 31));
                 ++expanded;
-                if ((S.prune && clt_query(p, S, v) <= dv) || (S.lt_prune && lt_prunes(p, S, v, dv))) {
-                    // a table hub, which outranks h, lies on a shortest h-v path:
-                    // v gets no label and is not expanded (Sec. 4.3)
-                    ++pruned;
-                    deg = 0;
-                    if (key_clean<K>(k)) atomic_min_key(&sl.key[v], make_key<K>(dv, false, 0));
+                cut = S.prune && clt_query(p, S, v) <= dv;
+                // a hub of the label table meets the root at the top vertex of
+                // their shortest paths, which outranks v and so is a table hub
+                // too: the complete query would find it
+                if (!cut && S.lt_prune) {
+                    if (v < p.lt_hubs) cut = true;
+                    else ask = true;
                 }
-                ok = deg != 0;
             }
         }
+        if (S.lt_prune) {  // uniform over the CTA
+            // queue the table queries; then each warp answers whole queries
+            const unsigned qm = __ballot_sync(FULL, ask);
+            uint32_t qs = 0;
+            if (qm) {
+                const int leader = __ffs(qm) - 1;
+                if (lane == leader) qs = atomicAdd(&S.qn, uint32_t(__popc(qm)));
+                qs = __shfl_sync(FULL, qs, leader) + __popc(qm & ((1u << lane) - 1));
+                if (ask) F.base[qs] = (uint64_t(vid) << 32) | dv;
+            }
+            __syncthreads();
+            const uint32_t qn = S.qn;
+            const uint32_t *rootd = S.lt_dense ? p.lt_root + size_t(blockIdx.x) * p.n : nullptr;
+            for (uint32_t q = warp; q < qn; q += NW) {
+                const uint64_t e = F.base[q];
+                const bool hit = lt_prunes_warp(p, S, rootd, uint32_t(e >> 32), uint32_t(e), lane);
+                if (lane == 0) F.pre[q] = hit;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) S.qn = 0;  // read again only after the chunk's next barrier
+            if (ask) cut = F.pre[qs] != 0;
+        }
+        if (cut) {
+            // a table hub, which outranks h, lies on a shortest h-v path:
+            // v gets no label and is not expanded (Sec. 4.3)
+            ++pruned;
+            deg = 0;
+            if (clean) atomic_min_key(&sl.key[vid], make_key<K>(dv, false, 0));
+        }
+        const bool ok = deg != 0;
         const unsigned okm = __ballot_sync(FULL, ok);
         if (fuse) {
             const int c = __popc(__ballot_sync(FULL, lv));
@@ -723,16 +773,23 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 for (uint32_t c = threadIdx.x; c < p.hc_stride; c += TPB)
                     S.hch[c] = __ldg(&p.hc[size_t(h) * p.hc_stride + c]);
             if (threadIdx.x == 0) S.prune = prune;
-            // the label table of earlier phases: hash the root's labels in it
+            // the label table of earlier phases: the root's labels in it, hashed
+            // or (more than the hash holds) in the slot's dense array
             bool lt_prune = p.lt_off && h >= p.lt_hubs;
+            bool lt_dense = false;
             uint64_t lt_a = 0, lt_b = 0;
             if (lt_prune) {
                 const uint32_t ch = __ldg(&p.vert_at[h]);
                 lt_a = __ldg(&p.lt_off[ch]);
                 lt_b = __ldg(&p.lt_off[ch + 1]);
-                lt_prune = lt_b - lt_a <= LTH_MAX;  // uniform: every thread reads the same
+                lt_dense = lt_b - lt_a > min(LTH_MAX, p.lt_hash_max);  // uniform over the CTA
+                lt_prune = !lt_dense || p.lt_root;
+                lt_dense = lt_dense && lt_prune;
             }
-            if (lt_prune) {
+            if (lt_dense) {
+                uint32_t *rootd = p.lt_root + so;
+                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) rootd[__ldg(&p.lt_hp[j])] = __ldg(&p.lt_d[j]);
+            } else if (lt_prune) {
                 for (uint32_t i = threadIdx.x; i < LTH_SLOTS; i += TPB) S.lth_key[i] = 0;
                 __syncthreads();
                 const uint64_t a = lt_a;
@@ -747,7 +804,10 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                     }
                 }
             }
-            if (threadIdx.x == 0) S.lt_prune = lt_prune;
+            if (threadIdx.x == 0) {
+                S.lt_prune = lt_prune;
+                S.lt_dense = lt_dense;
+            }
             if (threadIdx.x == 0) {
                 S.cur_n = 1;
                 S.nxt_n = 0;
@@ -764,6 +824,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 S.w_hi = uint64_t(p.delta) * p.nwin;
                 S.abort = 0;
                 S.fuse_live = 0;
+                S.qn = 0;
                 sl.l0[0] = h;
                 sl.touch[0] = h;
                 atomic_set_key(&sl.key[h], make_key<K>(0, true, h));
@@ -845,6 +906,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             if (S.abort) {
                 // reset and give up on this tree; the host reports the error
                 for (uint32_t i = threadIdx.x; i < S.touch_n; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
+                if (lt_dense)
+                    for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_hp[j])] = NONE;
                 __threadfence();
                 __syncthreads();
                 break;
@@ -884,6 +947,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             nlab = S.out_n;
             // reset exactly what this tree modified
             for (uint32_t i = threadIdx.x; i < nt; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
+            if (lt_dense)
+                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_hp[j])] = NONE;
             // the next tree reads keys with L2 loads and L2 atomics: the plain
             // reset stores must be visible there first, not only inside the CTA
             __threadfence();
@@ -891,18 +956,12 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
 
         // ---- reserve an all-or-nothing output range and copy the labels out
         if (threadIdx.x == 0) {
-            S.ok = 0;
-            unsigned long long old = *((volatile unsigned long long *)p.out_count);
-            uint32_t t = 0;
-            for (; t < RESERVE_TRIES; ++t) {
-                if (old + nlab > p.out_cap) break;
-                const unsigned long long prev = atomicCAS(p.out_count, old, old + nlab);
-                if (prev == old) { S.ok = 1; break; }
-                old = prev;
-            }
-            if (t == RESERVE_TRIES) atomicExch(&p.flags[0], ERR_RESERVE_LIMIT);
+            const unsigned long long old = atomicAdd(p.out_count, (unsigned long long)nlab);
+            S.ok = old + nlab <= p.out_cap;
             S.base = old;
             if (!S.ok) {
+                // nlab >= 1, so only the first range past the end starts within it
+                if (old <= p.out_cap) *p.out_valid = old;
                 p.failed[atomicAdd(p.failed_count, 1u)] = h;
                 atomicExch(&p.flags[1], 1);
             }
@@ -1069,6 +1128,61 @@ cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const 
     unsigned long long blocks = (count + 255) / 256;
     if (blocks > 152ull * 32) blocks = 152ull * 32;
     clt_fill_kernel<<<unsigned(blocks), 256, 0, s>>>(out_v, out_h, out_d, count, pos_of, hc, stride);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// A root all of whose neighbours outrank it is a trivial tree: once the root
+// is popped no queued vertex has it as ancestor (Algorithm 3 stops), so its
+// only label is (h, h, 0). One thread per root of [begin, begin + count):
+// trivial roots get that label here (one output reservation per warp), the
+// others are listed for the tree launch.
+__global__ void split_trivial_kernel(TreeLaunch p, uint32_t begin, uint32_t count, uint32_t *list,
+                                     unsigned int *list_n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
+    bool triv = false;
+    const uint32_t h = begin + i;
+    if (i < count) {
+        triv = true;
+        const uint64_t rs = __ldg(&p.row[h]), re = __ldg(&p.row[h + 1]);
+        for (uint64_t e = rs; e < re && triv; ++e) triv = __ldg(&p.arc[e]).x <= h;
+    }
+    const unsigned tm = __ballot_sync(0xffffffffu, triv);
+    const unsigned om = __ballot_sync(0xffffffffu, i < count && !triv);
+    const unsigned below = (1u << lane) - 1;
+    if (tm) {
+        unsigned long long b = 0;
+        if (lane == 0) {
+            b = atomicAdd(p.out_count, (unsigned long long)__popc(tm));
+            atomicAdd(&p.stats[2], (unsigned long long)__popc(tm));
+            atomicAdd(&p.stats[3], (unsigned long long)__popc(tm));
+        }
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (triv) {
+            const unsigned long long o = b + __popc(tm & below);
+            const uint32_t cv = __ldg(&p.vert_at[h]);
+            p.out_v[o] = cv;
+            p.out_h[o] = h;
+            p.out_d[o] = 0;
+            if (p.out_p) p.out_p[o] = cv;  // the root is its own parent
+        }
+    }
+    if (om) {
+        unsigned b = 0;
+        if (lane == 0) b = atomicAdd(list_n, unsigned(__popc(om)));
+        b = __shfl_sync(0xffffffffu, b, 0);
+        if (i < count && !triv) list[b + __popc(om & below)] = h;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_split_trivial(const TreeLaunch &p, uint32_t begin, uint32_t count, uint32_t *list,
+                                 unsigned int *list_n, cudaStream_t s) {
+    if (!count) return cudaSuccess;
+    split_trivial_kernel<<<(count + 255) / 256, 256, 0, s>>>(p, begin, count, list, list_n);
     return cudaGetLastError();
 }
 

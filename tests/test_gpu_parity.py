@@ -281,7 +281,9 @@ def test_hybrid_phases_are_exact():
     rank = W.degree_rank(g)
     ref = O.build_labels(g, rank, "plant", threads=16)
     G, R = DG(g), dev(rank)
-    for opts in (dict(), dict(threads_per_tree=256), dict(threads_per_tree=1024, bucket_delta=2)):
+    for opts in (dict(), dict(threads_per_tree=256), dict(threads_per_tree=1024, bucket_delta=2),
+                 dict(flags=chl.CHL_FLAG_DENSE_ROOT_LABELS), dict(pruned_bucket_delta=1),
+                 dict(pruned_bucket_delta=4096, flags=chl.CHL_FLAG_PARENTS)):
         L = chl.build_labels(G, R, **opts)
         st = L.stats()
         assert st["phases"] > 1 and st["label_table_phases"] >= 1, st
