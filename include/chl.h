@@ -127,10 +127,12 @@ typedef struct chl_labels chl_labels;
  *   psi_threshold          Psi_th of the hybrid switch (Sec. 4.3): once a
  *                          phase expands more than Psi_th vertices per label it
  *                          generates, the later phases prune with the labels of
- *                          the earlier ones. 0 = 16 (the paper's 16-node runs
- *                          use 100 on scale-free and 500 on road networks,
- *                          where the switch also costs communication);
- *                          must not be negative
+ *                          the earlier ones. 0 = 16, and the switch also fires
+ *                          once the Common Label Table pruned at least 10% of
+ *                          a phase's expansions; a value set here uses Psi
+ *                          alone (the paper's 16-node runs use 100 on
+ *                          scale-free and 500 on road networks, where the
+ *                          switch also costs communication). Not negative.
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the

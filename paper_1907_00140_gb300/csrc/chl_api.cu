@@ -189,6 +189,10 @@ struct SlotState {
 // default expansions per label of a phase above which the next phases prune
 // with the label table of the earlier ones
 constexpr double PSI_TH = 16.0;
+// ... or the share of a phase's expansions that the Common Label Table pruned
+// above which they do: where the top 16 hubs already cut that much, the labels
+// of every earlier hub cut far more and the per-vertex query pays
+constexpr double CLT_PRUNE_TH = 0.10;
 
 void free_csr(LabelCSR &c, cudaStream_t s) {
     if (c.offsets) cudaFreeAsync(c.offsets, s);
@@ -283,7 +287,25 @@ chl_status build_common_table(const RankGraph &rg, const Params &P, const SlotSt
         for (int k = 0; k < 7; ++k) agg[k] += hc.stats[k];
     CUDA_TRY(launch_clt_fill((const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
                              (const uint32_t *)b_od.p, hc.out_count, rg.pos_of, (uint32_t *)t.buf.p,
-                             t.stride, s));
+                             t.stride, t.hubs, s));
+    ++*launches;
+done:
+    return st;
+}
+
+// the same table from the records of a build whose first trees were the
+// table's roots (every label of hubs below eta is among the count records)
+chl_status table_from_records(const RankGraph &rg, const Params &P, const uint32_t *ov,
+                              const uint32_t *oh, const uint32_t *od, uint64_t count,
+                              cudaStream_t s, CommonTable &t, int *launches) {
+    chl_status st = CHL_OK;
+    const uint32_t n = rg.n;
+    t.buf.s = s;
+    t.hubs = P.eta;
+    t.stride = (P.eta + 3) & ~3u;
+    CUDA_TRY(cudaMallocAsync(&t.buf.p, size_t(n) * t.stride * 4, s));
+    CUDA_TRY(cudaMemsetAsync(t.buf.p, 0xFF, size_t(n) * t.stride * 4, s));
+    CUDA_TRY(launch_clt_fill(ov, oh, od, count, rg.pos_of, (uint32_t *)t.buf.p, t.stride, t.hubs, s));
     ++*launches;
 done:
     return st;
@@ -347,7 +369,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     uint64_t cap = 0;
     uint64_t T = 0;
     int too_long = 0;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev[7] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     float ms_total = 0, ms_tree = 0, ms_sort = 0, ms_table = 0;
     bool with_table = false;
     chl_labels *L = nullptr;
@@ -441,29 +463,28 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (parents) CUDA_TRY(cudaMallocAsync(&b_op.p, cap * 4, s));
 
     CUDA_TRY(cudaEventRecord(ev[1], s));
-    // the table is needed when some requested tree lies outside it
-    if (P.eta && re > P.eta) {
+    // Hybrid phases (Sec. 4.3): a build that starts at the top root runs its
+    // roots in phases; the trees of a phase also prune with every label of all
+    // earlier phases (a rank-closed hub set, so the labels stay canonical)
+    // once the switch has fired. Other builds run as one phase.
+    hybrid = rb == 0 && P.eta && !(o.flags & CHL_FLAG_NO_HYBRID) && re > P.eta;
+    // the Common Label Table is needed when some requested tree lies outside
+    // it; a hybrid build takes it from its first phase instead
+    if (P.eta && re > P.eta && !hybrid) {
         st = build_common_table(rg, P, slot, s, table, &launches, nullptr);
         if (st != CHL_OK) goto done;
         with_table = true;
     }
     CUDA_TRY(cudaEventRecord(ev[4], s));
-    // Hybrid phases (Sec. 4.3): a build that starts at the top root runs its
-    // roots in phases of doubling size; the trees of a phase also prune with
-    // every label of all earlier phases (a rank-closed hub set, so the labels
-    // stay canonical). Other builds run as one phase.
-    // The next phase doubles (at least two trees per slot) while the table is
-    // used, so that it stays fresh; before the switch it grows fourfold.
-    hybrid = rb == 0 && P.eta && !(o.flags & CHL_FLAG_NO_HYBRID) && re > P.eta;
     phases.clear();
-    // the first phase holds the Common Label Table's own trees (unpruned) and
-    // enough others to fill the slots
+    // a hybrid build's first phase is one tree per slot (at least the table's
+    // roots), built without any table
     phases.push_back(hybrid ? std::make_pair(0u, uint32_t(std::min<uint64_t>(
-                                                     re, uint64_t(P.eta) + uint64_t(P.slots) * 2)))
+                                                     re, std::max<uint64_t>(P.eta, uint64_t(P.slots)))))
                             : std::make_pair(rb, re));
     for (size_t ph = 0; ph < phases.size(); ++ph) {
     const uint32_t pb = phases[ph].first, pe = phases[ph].second;
-    const uint64_t exp0 = agg[0], T0 = T, arc0 = agg[1];
+    const uint64_t exp0 = agg[0], T0 = T, arc0 = agg[1], pr0 = agg[6];
     const int ph_lt = lt.offsets ? 1 : 0;
     if (trace) t_ph = now_ms();
     if (lt.offsets) ++lt_phases;
@@ -608,19 +629,35 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         }
     }
     // The switch of Sec. 4.3: label pruning starts once a phase's trees explore
-    // many vertices per label (Psi = expansions / labels above psi_th); before
+    // many vertices per label (Psi = expansions / labels above psi_th), or once
+    // the Common Label Table pruned a large share of their expansions; before
     // that, the per-vertex table query would cost more than it saves.
     if (hybrid && !use_lt && T > T0) {
         const double psi = double(agg[0] - exp0) / double(T - T0);
-        if (psi > psi_th) use_lt = true;
+        const double cut = agg[0] > exp0 ? double(agg[6] - pr0) / double(agg[0] - exp0) : 0.0;
+        if (psi > psi_th || (P.eta && cut >= CLT_PRUNE_TH && o.psi_threshold == 0.0f)) use_lt = true;
         // far down the ranking and still cheap trees: the rest is one phase
         else if (pe >= std::max<uint64_t>(uint64_t(P.slots) * 8, 8192) && psi < psi_th / 2)
             hybrid_off = true;
     }
+    if (hybrid && !table.buf.p) {
+        // the first phase built the table's trees: the Common Label Table from
+        // their labels, for every later phase
+        CUDA_TRY(cudaEventRecord(ev[5], s));
+        st = table_from_records(rg, P, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
+                                (const uint32_t *)b_od.p, T, s, table, &launches);
+        if (st != CHL_OK) goto done;
+        CUDA_TRY(cudaEventRecord(ev[6], s));
+        with_table = true;
+    }
+    // The next phase is one more wave of trees after the first (the table's
+    // pruning share decides the switch), doubles while the label table is
+    // used, so that it stays fresh, and grows fourfold before.
     if (hybrid && pe < re) {
         const uint64_t step_min = uint64_t(P.slots) * 2;
         const uint64_t nx = hybrid_off ? re
-                                       : std::max<uint64_t>(uint64_t(pe) * (use_lt ? 2 : 4), pe + step_min);
+                            : ph == 0 ? uint64_t(pe) + P.slots
+                                      : std::max<uint64_t>(uint64_t(pe) * (use_lt ? 2 : 4), pe + step_min);
         phases.push_back({pe, uint32_t(std::min<uint64_t>(nx, re))});
     }
     double t_tree = trace ? now_ms() - t_ph : 0;
@@ -631,13 +668,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             CUDA_TRY(cudaMallocAsync(&b_ltroot.p, size_t(P.slots) * n * 4, s));
             CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, size_t(P.slots) * n * 4, s));
         }
-        int tl_long = 0;
-        CUDA_TRY(assemble_labels(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
-                                 (const uint32_t *)b_od.p, rg.vert_at, lt, &tl_long, s, &launches));
-        if (tl_long) {
-            st = set_error(CHL_EOVERFLOW, "a vertex holds more labels than the segment sorter supports");
-            goto done;
-        }
+        CUDA_TRY(assemble_table(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
+                                (const uint32_t *)b_od.p, rg.pos_of, lt, s, &launches));
     }
     if (trace) {
         CUDA_TRY(cudaStreamSynchronize(s));
@@ -672,7 +704,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     cudaEventElapsedTime(&ms_total, ev[0], ev[3]);
     cudaEventElapsedTime(&ms_tree, ev[1], ev[2]);
     cudaEventElapsedTime(&ms_sort, ev[2], ev[3]);
-    if (with_table) cudaEventElapsedTime(&ms_table, ev[1], ev[4]);
+    if (with_table && hybrid) cudaEventElapsedTime(&ms_table, ev[5], ev[6]);
+    else if (with_table) cudaEventElapsedTime(&ms_table, ev[1], ev[4]);
 
     L = new (std::nothrow) chl_labels;
     if (!L) {

@@ -62,8 +62,9 @@ struct TreeLaunch {
     uint32_t hc_hubs;
     uint32_t hc_stride;
     // label table of the earlier phases of a hybrid build, or lt_off = null:
-    // all labels of the hubs of rank position < lt_hubs, CSR by caller vertex
-    // id (offsets [n+1]) with ascending hub positions lt_hp and distances lt_d
+    // all labels of the hubs of rank position < lt_hubs, CSR by vertex rank
+    // position (offsets [n+1]) of hub positions lt_hp and distances lt_d, each
+    // vertex's entries in no particular order
     const uint64_t *lt_off;
     const uint32_t *lt_hp;
     const uint32_t *lt_d;
@@ -107,16 +108,16 @@ cudaError_t launch_split_trivial(const TreeLaunch &p, uint32_t begin, uint32_t c
                                  unsigned int *list_n, cudaStream_t s);
 // settled-filter words for n vertices that keep the CTAs per SM of fin_words = 0
 uint32_t plant_fin_words(int threads_per_tree, uint32_t n);
-// Common Label Table entries from label records of the table's trees
+// Common Label Table entries from label records (those of hub positions < hubs)
 cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
                             unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
-                            uint32_t stride, cudaStream_t s);
+                            uint32_t stride, uint32_t hubs, cudaStream_t s);
 
 // label assembly (chl_labels.cu)
 struct LabelCSR {
     uint64_t *offsets = nullptr; // [n+1] by caller vertex id
     uint32_t *hub = nullptr;     // caller vertex id
-    uint32_t *hubpos = nullptr;  // rank position of hub (sorted ascending per vertex)
+    uint32_t *hubpos = nullptr;  // rank position of hub (ascending per vertex, but see assemble_table)
     uint32_t *dist = nullptr;
 };
 // builds CSR from T label triples; returns error status via cudaError_t, sets
@@ -124,6 +125,13 @@ struct LabelCSR {
 cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const uint32_t *in_h,
                             const uint32_t *in_d, const uint32_t *vert_at, LabelCSR &out,
                             int *too_long, cudaStream_t s, int *launches);
+
+// the same records as a table for distance queries: offsets by rank position
+// (pos_of maps caller ids to positions), hubpos and dist only, each vertex's
+// entries in no particular order (hub = null)
+cudaError_t assemble_table(uint32_t n, uint64_t T, const uint32_t *in_v, const uint32_t *in_h,
+                           const uint32_t *in_d, const uint32_t *pos_of, LabelCSR &out,
+                           cudaStream_t s, int *launches);
 
 // parents of label records into the slots of the assembled CSR (parent[T])
 cudaError_t place_parents(uint64_t T, const uint32_t *in_v, const uint32_t *in_h, const uint32_t *in_p,

@@ -27,6 +27,27 @@ __global__ void count_kernel(uint64_t T, const uint32_t *v, uint64_t *cnt) {
         atomicAdd((unsigned long long *)&cnt[v[i]], 1ull);
 }
 
+// unsorted table by rank position: (hubpos, dist) straight into each
+// vertex's segment
+__global__ void count_table_kernel(uint64_t T, const uint32_t *v, const uint32_t *pos_of,
+                                   uint64_t *cnt) {
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
+         i += uint64_t(gridDim.x) * blockDim.x)
+        atomicAdd((unsigned long long *)&cnt[pos_of[v[i]]], 1ull);
+}
+
+__global__ void scatter_table_kernel(uint64_t T, const uint32_t *v, const uint32_t *h,
+                                     const uint32_t *d, const uint32_t *pos_of, const uint64_t *off,
+                                     uint64_t *fill, uint32_t *hubpos, uint32_t *dist) {
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
+         i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t x = pos_of[v[i]];
+        const uint64_t k = off[x] + atomicAdd((unsigned long long *)&fill[x], 1ull);
+        hubpos[k] = h[i];
+        dist[k] = d[i];
+    }
+}
+
 __global__ void scatter_kernel(uint64_t T, const uint32_t *v, const uint32_t *h, const uint32_t *d,
                                const uint64_t *off, uint64_t *fill, uint64_t *tmp) {
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
@@ -204,6 +225,38 @@ done:
     if (e != cudaSuccess || *too_long) {
         if (out.offsets) cudaFreeAsync(out.offsets, s);
         if (out.hub) cudaFreeAsync(out.hub, s);
+        if (out.hubpos) cudaFreeAsync(out.hubpos, s);
+        if (out.dist) cudaFreeAsync(out.dist, s);
+        out = LabelCSR{};
+    }
+    return e;
+}
+
+cudaError_t assemble_table(uint32_t n, uint64_t T, const uint32_t *in_v, const uint32_t *in_h,
+                           const uint32_t *in_d, const uint32_t *pos_of, LabelCSR &out,
+                           cudaStream_t s, int *launches) {
+    cudaError_t e = cudaSuccess;
+    uint64_t *cnt = nullptr;
+    out = LabelCSR{};
+    const size_t Tb = (T ? T : 1);
+    CKE(cudaMallocAsync(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(cudaMallocAsync(&out.hubpos, Tb * sizeof(uint32_t), s));
+    CKE(cudaMallocAsync(&out.dist, Tb * sizeof(uint32_t), s));
+    CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
+    count_table_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, pos_of, cnt);
+    *launches += 1;
+    CKE(cudaGetLastError());
+    CKE(exclusive_scan_u64(cnt, out.offsets, uint64_t(n) + 1, s, launches));
+    CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
+    scatter_table_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, in_h, in_d, pos_of, out.offsets,
+                                                          cnt, out.hubpos, out.dist);
+    *launches += 1;
+    CKE(cudaGetLastError());
+done:
+    if (cnt) cudaFreeAsync(cnt, s);
+    if (e != cudaSuccess) {
+        if (out.offsets) cudaFreeAsync(out.offsets, s);
         if (out.hubpos) cudaFreeAsync(out.hubpos, s);
         if (out.dist) cudaFreeAsync(out.dist, s);
         out = LabelCSR{};

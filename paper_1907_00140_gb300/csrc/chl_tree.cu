@@ -403,8 +403,8 @@ __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared 
 }
 
 // Label table of earlier phases (hybrid pruning): every label of every hub of
-// rank position below p.lt_hubs, as CSR by caller vertex id with hub
-// positions ascending. min over shared hubs c of d(h,c) + d(c,v) <= dv means a
+// rank position below p.lt_hubs, as CSR by vertex rank position (entries of a
+// vertex unordered). min over shared hubs c of d(h,c) + d(c,v) <= dv means a
 // vertex outranking h lies on a shortest h-v path, as for the Common Label
 // Table: the table is complete for a rank-closed set of hubs (Sec. 4.3). The
 // query must see every table label of h and of v: a vertex reached only past a
@@ -414,14 +414,13 @@ __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared 
 // holds, written into the slot's dense array p.lt_root by hub position.
 __device__ __forceinline__ uint32_t lth_slot(uint32_t hp) { return (hp * 2654435761u) >> 22; }
 
-// One warp answers the query of one vertex: each lane takes every 32nd table
-// label of v (coalesced), looks its hub up in the root's hash, and the warp
-// stops at the first step where some lane found a witness.
+// One warp answers the query of one vertex, whose table labels are [a, b):
+// each lane takes every 32nd of them (coalesced), looks its hub up in the
+// root's labels, and the warp stops at the first step where some lane found a
+// witness.
 __device__ __forceinline__ bool lt_prunes_warp(const TreeLaunch &p, const Shared &S,
-                                               const uint32_t *rootd, uint32_t v, uint32_t dv,
-                                               int lane) {
-    const uint32_t cv = __ldg(&p.vert_at[v]);
-    const uint64_t a = __ldg(&p.lt_off[cv]), b = __ldg(&p.lt_off[cv + 1]);
+                                               const uint32_t *rootd, uint64_t a, uint64_t b,
+                                               uint32_t dv, int lane) {
     for (uint64_t j0 = a; j0 < b; j0 += 32) {
         const uint64_t j = j0 + lane;
         bool hit = false;
@@ -493,21 +492,32 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
             }
         }
         if (S.lt_prune) {  // uniform over the CTA
-            // queue the table queries; then each warp answers whole queries
+            // queue the table queries with their label ranges; then each warp
+            // answers whole queries
+            uint64_t la = 0, lb = 0;
+            if (ask) {
+                la = __ldg(&p.lt_off[vid]);
+                lb = __ldg(&p.lt_off[vid + 1]);
+                ask = lb > la;  // no table label: nothing to find
+            }
             const unsigned qm = __ballot_sync(FULL, ask);
             uint32_t qs = 0;
             if (qm) {
                 const int leader = __ffs(qm) - 1;
                 if (lane == leader) qs = atomicAdd(&S.qn, uint32_t(__popc(qm)));
                 qs = __shfl_sync(FULL, qs, leader) + __popc(qm & ((1u << lane) - 1));
-                if (ask) F.base[qs] = (uint64_t(vid) << 32) | dv;
+                if (ask) {
+                    F.base[qs] = la;
+                    F.pre[qs] = ((lb - la) << 32) | dv;
+                }
             }
             __syncthreads();
             const uint32_t qn = S.qn;
             const uint32_t *rootd = S.lt_dense ? p.lt_root + size_t(blockIdx.x) * p.n : nullptr;
             for (uint32_t q = warp; q < qn; q += NW) {
-                const uint64_t e = F.base[q];
-                const bool hit = lt_prunes_warp(p, S, rootd, uint32_t(e >> 32), uint32_t(e), lane);
+                const uint64_t a = F.base[q], e = F.pre[q];
+                const bool hit = lt_prunes_warp(p, S, rootd, a, a + (e >> 32), uint32_t(e), lane);
+                __syncwarp();  // every lane has read the entry before lane 0 rewrites it
                 if (lane == 0) F.pre[q] = hit;
             }
             __syncthreads();
@@ -779,9 +789,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             bool lt_dense = false;
             uint64_t lt_a = 0, lt_b = 0;
             if (lt_prune) {
-                const uint32_t ch = __ldg(&p.vert_at[h]);
-                lt_a = __ldg(&p.lt_off[ch]);
-                lt_b = __ldg(&p.lt_off[ch + 1]);
+                lt_a = __ldg(&p.lt_off[h]);
+                lt_b = __ldg(&p.lt_off[h + 1]);
                 lt_dense = lt_b - lt_a > min(LTH_MAX, p.lt_hash_max);  // uniform over the CTA
                 lt_prune = !lt_dense || p.lt_root;
                 lt_dense = lt_dense && lt_prune;
@@ -1109,25 +1118,28 @@ uint32_t plant_fin_words(int tpt, uint32_t n) {
 namespace chl {
 namespace {
 
-// Common Label Table from the labels of the table's own trees: record i is
-// (caller vertex out_v[i], hub pos out_h[i] < hubs, distance out_d[i])
+// Common Label Table from label records: record i is (caller vertex out_v[i],
+// hub pos out_h[i], distance out_d[i]); those of hubs below `hubs` go in
 __global__ void clt_fill_kernel(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
                                 unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
-                                uint32_t stride) {
+                                uint32_t stride, uint32_t hubs) {
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < count;
-         i += (unsigned long long)gridDim.x * blockDim.x)
-        hc[size_t(pos_of[out_v[i]]) * stride + out_h[i]] = out_d[i];
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t c = out_h[i];
+        if (c < hubs) hc[size_t(pos_of[out_v[i]]) * stride + c] = out_d[i];
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
                             unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
-                            uint32_t stride, cudaStream_t s) {
+                            uint32_t stride, uint32_t hubs, cudaStream_t s) {
     if (!count) return cudaSuccess;
     unsigned long long blocks = (count + 255) / 256;
     if (blocks > 152ull * 32) blocks = 152ull * 32;
-    clt_fill_kernel<<<unsigned(blocks), 256, 0, s>>>(out_v, out_h, out_d, count, pos_of, hc, stride);
+    clt_fill_kernel<<<unsigned(blocks), 256, 0, s>>>(out_v, out_h, out_d, count, pos_of, hc, stride,
+                                                     hubs);
     return cudaGetLastError();
 }
 
