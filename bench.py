@@ -49,11 +49,13 @@ WORKLOAD_TEXT = {
 }
 
 
-# DRAM read + write bytes per relaxed arc of plant_trees_kernel, from one ncu
-# capture (dram__bytes_read.sum + dram__bytes_write.sum = 80.7 GB over
-# 5,366,689,567 arcs, rmat18 roots at rank positions [1000, 2216), the same
-# kernel source); the bench scales it by the arcs a step relaxes
-TREE_DRAM_BYTES_PER_ARC = 15.0
+# DRAM read + write bytes of plant_trees_kernel over one whole build (the sum
+# of dram__bytes_read.sum + dram__bytes_write.sum over its 11 launches, one ncu
+# capture of the current kernel source), keyed by workload and the launch
+# parameters it was taken with; other builds report no traffic
+TREE_DRAM_BYTES_PER_BUILD = {
+    ("rmat18", 1024, 1, 32): 36.066e9 + 10.178e9,
+}
 
 
 def load_peaks():
@@ -493,17 +495,18 @@ def main():
             # plus the label entries (hub, dist: 8 B) its distance queries read
             algo += 8.0 * wu.get("Q", 0.0)
         ach = algo / (float(np.mean(tree_ms)) / 1000.0) / 1e9
-        arcs_step = float(res["explored"]["arcs"])
+        key = (name, opts.get("threads_per_tree", 1024), opts.get("bucket_delta", 0),
+               opts.get("window_buckets", 32))
+        traffic = TREE_DRAM_BYTES_PER_BUILD.get(key)
         res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                            "frac": ach / peak,
-                           "traffic": (TREE_DRAM_BYTES_PER_ARC * arcs_step
-                                       if arcs_step and not hybrid else None),
-                           "traffic_note": ("null: the per-arc capture is of the build "
-                                            "without label pruning" if hybrid else
-                                            "DRAM bytes per relaxed arc from the ncu capture of the "
-                                            "tree kernel on rmat18 roots [1000, 2216) "
-                                            f"({TREE_DRAM_BYTES_PER_ARC} B), times the arcs one "
-                                            "step relaxes"),
+                           "traffic": traffic,
+                           "traffic_note": ("DRAM read + write bytes of the tree kernel over one "
+                                            "whole build (all its launches), from one ncu capture "
+                                            "of the same build and launch parameters; per build, "
+                                            "like achieved" if traffic else
+                                            "null: no capture of this workload and these launch "
+                                            "parameters with the current kernel"),
                            "peak_kind": peak_kind,
                            "kernel": "plant_trees_kernel",
                            "algorithmic_bytes": algo,
