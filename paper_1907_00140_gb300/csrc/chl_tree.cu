@@ -60,6 +60,7 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t CLT_MAX = 64;  // largest Common Label Table (hubs)
 constexpr uint32_t LTH_SLOTS = 1024;  // hash of the root's labels in the label table
 constexpr uint32_t LTH_MAX = 512;     // most root labels the hash holds
+constexpr int QSTEPS = 4;             // label-table query: loads in flight per lane
 
 // ------------------------------------------------------------------ keys
 // Vertices are numbered by rank position (pos 0 = most important), so in the
@@ -421,22 +422,35 @@ __device__ __forceinline__ uint32_t lth_slot(uint32_t hp) { return (hp * 2654435
 __device__ __forceinline__ bool lt_prunes_warp(const TreeLaunch &p, const Shared &S,
                                                const uint32_t *rootd, uint64_t a, uint64_t b,
                                                uint32_t dv, int lane) {
-    for (uint64_t j0 = a; j0 < b; j0 += 32) {
-        const uint64_t j = j0 + lane;
+    // QSTEPS steps of 32 labels are loaded before any is looked up, so a list
+    // of up to 32 * QSTEPS labels costs one round trip to memory
+    for (uint64_t j0 = a; j0 < b; j0 += 32 * QSTEPS) {
+        uint32_t dc[QSTEPS], hp[QSTEPS];
+#pragma unroll
+        for (int u = 0; u < QSTEPS; ++u) {
+            const uint64_t j = j0 + uint64_t(u) * 32 + lane;
+            dc[u] = NONE;  // above every distance (R7)
+            hp[u] = 0;
+            if (j < b) {
+                dc[u] = __ldg(&p.lt_d[j]);
+                hp[u] = __ldg(&p.lt_hp[j]);
+            }
+        }
         bool hit = false;
-        if (j < b) {
-            const uint32_t dcv = __ldg(&p.lt_d[j]);
-            if (dcv <= dv && rootd) {
+#pragma unroll
+        for (int u = 0; u < QSTEPS; ++u) {
+            if (dc[u] > dv) continue;
+            if (rootd) {
                 // written by this CTA at tree start: a plain load
-                const uint32_t dhc = rootd[__ldg(&p.lt_hp[j])];
-                hit = dhc != NONE && uint64_t(dhc) + dcv <= dv;
-            } else if (dcv <= dv) {
-                const uint32_t c = __ldg(&p.lt_hp[j]);
+                const uint32_t dhc = rootd[hp[u]];
+                hit |= dhc != NONE && uint64_t(dhc) + dc[u] <= dv;
+            } else {
+                const uint32_t c = hp[u];
                 for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
                     const uint32_t key = S.lth_key[sx];
                     if (key == 0) break;
                     if (key == c + 1) {
-                        hit = uint64_t(S.lth_val[sx]) + dcv <= dv;
+                        hit |= uint64_t(S.lth_val[sx]) + dc[u] <= dv;
                         break;
                     }
                 }
