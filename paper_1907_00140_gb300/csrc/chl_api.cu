@@ -379,6 +379,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     LabelCSR lt;  // labels of earlier phases (hybrid)
     bool use_lt = false, hybrid = false, hybrid_off = false;
     uint64_t lt_phases = 0;
+    uint64_t lt_records = 0;  // output records the label table holds
     const double psi_th = o.psi_threshold > 0.0f ? double(o.psi_threshold) : PSI_TH;
     uint32_t claimed_upto = 0;
     bool first = true;
@@ -662,14 +663,20 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     }
     double t_tree = trace ? now_ms() - t_ph : 0;
     if (use_lt && ph + 1 < phases.size()) {
-        // every label so far, as CSR, for the next phase's pruning
-        free_csr(lt, s);
+        // every label so far, as CSR, for the next phase's pruning: the first
+        // time sorted from all records, then grown by each phase's new ones
         if (!b_ltroot.p) {
             CUDA_TRY(cudaMallocAsync(&b_ltroot.p, size_t(P.slots) * n * 4, s));
             CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, size_t(P.slots) * n * 4, s));
         }
-        CUDA_TRY(assemble_table(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
-                                (const uint32_t *)b_od.p, rg.pos_of, lt, s, &launches));
+        if (!lt.offsets)
+            CUDA_TRY(assemble_table(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
+                                    (const uint32_t *)b_od.p, rg.pos_of, lt, s, &launches));
+        else
+            CUDA_TRY(grow_table(n, lt, lt_records, T, (const uint32_t *)b_ov.p,
+                                (const uint32_t *)b_oh.p, (const uint32_t *)b_od.p, rg.pos_of, s,
+                                &launches));
+        lt_records = T;
     }
     if (trace) {
         CUDA_TRY(cudaStreamSynchronize(s));

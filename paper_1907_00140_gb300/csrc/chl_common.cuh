@@ -133,6 +133,12 @@ cudaError_t assemble_table(uint32_t n, uint64_t T, const uint32_t *in_v, const u
                            const uint32_t *in_d, const uint32_t *pos_of, LabelCSR &out,
                            cudaStream_t s, int *launches);
 
+// a table from assemble_table of records [0, T0) grown by records [T0, T):
+// each vertex keeps its old entries first (lt is replaced; freed on success)
+cudaError_t grow_table(uint32_t n, LabelCSR &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
+                       const uint32_t *in_h, const uint32_t *in_d, const uint32_t *pos_of,
+                       cudaStream_t s, int *launches);
+
 // parents of label records into the slots of the assembled CSR (parent[T])
 cudaError_t place_parents(uint64_t T, const uint32_t *in_v, const uint32_t *in_h, const uint32_t *in_p,
                           const LabelCSR &csr, uint32_t *parent, cudaStream_t s, int *launches);

@@ -48,6 +48,43 @@ __global__ void scatter_table_kernel(uint64_t T, const uint32_t *v, const uint32
     }
 }
 
+// entries per vertex of the grown table: its old entries plus the new ones
+__global__ void grown_count_kernel(uint32_t n, const uint64_t *old_off, uint64_t *cnt) {
+    for (uint64_t v = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
+         v += uint64_t(gridDim.x) * blockDim.x)
+        cnt[v] += old_off[v + 1] - old_off[v];
+}
+
+// one warp per vertex: its old entries to the front of its new segment
+__global__ void copy_segments_kernel(uint32_t n, const uint64_t *old_off, const uint32_t *old_hp,
+                                     const uint32_t *old_d, const uint64_t *new_off, uint32_t *hp,
+                                     uint32_t *d) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t v = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const uint64_t a = old_off[v], len = old_off[v + 1] - a, o = new_off[v];
+        for (uint64_t i = lane; i < len; i += 32) {
+            hp[o + i] = old_hp[a + i];
+            d[o + i] = old_d[a + i];
+        }
+    }
+}
+
+// new records after each vertex's old entries
+__global__ void scatter_new_kernel(uint64_t T0, uint64_t T, const uint32_t *v, const uint32_t *h,
+                                   const uint32_t *d, const uint32_t *pos_of, const uint64_t *old_off,
+                                   const uint64_t *off, uint64_t *fill, uint32_t *hubpos,
+                                   uint32_t *dist) {
+    for (uint64_t i = T0 + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
+         i += uint64_t(gridDim.x) * blockDim.x) {
+        const uint32_t x = pos_of[v[i]];
+        const uint64_t k = off[x] + (old_off[x + 1] - old_off[x]) +
+                           atomicAdd((unsigned long long *)&fill[x], 1ull);
+        hubpos[k] = h[i];
+        dist[k] = d[i];
+    }
+}
+
 __global__ void scatter_kernel(uint64_t T, const uint32_t *v, const uint32_t *h, const uint32_t *d,
                                const uint64_t *off, uint64_t *fill, uint64_t *tmp) {
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
@@ -261,6 +298,54 @@ done:
         if (out.dist) cudaFreeAsync(out.dist, s);
         out = LabelCSR{};
     }
+    return e;
+}
+
+cudaError_t grow_table(uint32_t n, LabelCSR &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
+                       const uint32_t *in_h, const uint32_t *in_d, const uint32_t *pos_of,
+                       cudaStream_t s, int *launches) {
+    cudaError_t e = cudaSuccess;
+    uint64_t *cnt = nullptr;
+    LabelCSR out;
+    const uint64_t dT = T - T0;
+    const size_t Tb = (T ? T : 1);
+    CKE(cudaMallocAsync(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(cudaMallocAsync(&out.hubpos, Tb * sizeof(uint32_t), s));
+    CKE(cudaMallocAsync(&out.dist, Tb * sizeof(uint32_t), s));
+    CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
+    if (dT) {
+        count_table_kernel<<<grid_for(dT, 256), 256, 0, s>>>(dT, in_v + T0, pos_of, cnt);
+        *launches += 1;
+    }
+    grown_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, lt.offsets, cnt);
+    *launches += 1;
+    CKE(cudaGetLastError());
+    CKE(exclusive_scan_u64(cnt, out.offsets, uint64_t(n) + 1, s, launches));
+    copy_segments_kernel<<<152 * 16, 256, 0, s>>>(n, lt.offsets, lt.hubpos, lt.dist, out.offsets,
+                                                  out.hubpos, out.dist);
+    *launches += 1;
+    CKE(cudaGetLastError());
+    if (dT) {
+        CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
+        scatter_new_kernel<<<grid_for(dT, 256), 256, 0, s>>>(T0, T, in_v, in_h, in_d, pos_of,
+                                                             lt.offsets, out.offsets, cnt, out.hubpos,
+                                                             out.dist);
+        *launches += 1;
+        CKE(cudaGetLastError());
+    }
+done:
+    if (cnt) cudaFreeAsync(cnt, s);
+    if (e != cudaSuccess) {
+        if (out.offsets) cudaFreeAsync(out.offsets, s);
+        if (out.hubpos) cudaFreeAsync(out.hubpos, s);
+        if (out.dist) cudaFreeAsync(out.dist, s);
+        return e;
+    }
+    cudaFreeAsync(lt.offsets, s);
+    cudaFreeAsync(lt.hubpos, s);
+    cudaFreeAsync(lt.dist, s);
+    lt = out;
     return e;
 }
 
