@@ -402,8 +402,9 @@ def build_labels(g, rank, stream: int | None = None, **opts) -> Labels:
     bucket_delta, window_buckets, slots, mode)."""
     csr, rkp, keep = _csr_args(g, rank)
     o = chl_build_opts()
+    kinds = dict(chl_build_opts._fields_)
     for k, v in opts.items():
-        setattr(o, k, int(v))
+        setattr(o, k, float(v) if kinds.get(k) is C.c_float else int(v))
     h = chl_build(csr, rkp, o, _current_stream() if stream is None else stream)
     return Labels(h)
 
