@@ -296,7 +296,7 @@ def main():
     ap.add_argument("--queries", type=int, default=1_000_000)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-extras", action="store_true", help="skip plain/cpu/e2e legs")
-    ap.add_argument("--serve-sets", default="main",
+    ap.add_argument("--serve-sets", default="main,rmat21",
                     help="label sets resident in the serving run: 'main' (the bench build) "
                          "and/or workload names, comma separated (e.g. main,rmat21)")
     ap.add_argument("--serve-duration", type=float, default=0.1,
