@@ -477,7 +477,7 @@ def main():
                       "single_launch_p99_us": float(np.percentile(lat, 99)),
                       "single_launch_p999_us": float(np.percentile(lat, 99.9))}
 
-    # ---- roofline of the tree kernel (algorithmic bytes per SURVEY-style unit counts)
+    # ---- roofline of the tree kernel (algorithmic bytes from per-unit work counts)
     peak, peak_kind = load_peaks()
     # the build prunes with the Common Label Table of 16 hubs unless told otherwise
     eta = opts.get("common_hubs", 0)

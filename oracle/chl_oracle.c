@@ -315,7 +315,7 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
     uint64_t settled = 0, arcs = 0, nl = 0;
     /* pruning by the Common Label Table applies to trees of roots outside it */
     const int prune = g->hc && g->n - 1 - Rh >= g->eta;
-    /* line 1-2: delta_h = 0, a[h] = h; add h to Q; cnt = 1 */
+    /* start: delta_h = 0, a[h] = h, h queued, cnt = 1 */
     ws_touch(ws, h);
     delta[h] = 0;
     a[h] = h;
@@ -388,18 +388,18 @@ static int build_pll(const graph *g, const uint32_t *roots, uint64_t nroots, uin
         const uint32_t h = roots[ri];
         const uint32_t Rh = g->rank[h];
         uint64_t settled = 0, arcs = 0, nl = 0, qe = L[h].len;
-        /* line 1: LR = hash(L_h) */
+        /* the root's labels by hub (LR), for the distance queries */
         for (uint32_t i = 0; i < L[h].len; ++i) LR[L[h].hub[i]] = L[h].dist[i];
         uint64_t *delta = ws.dist;
         ws_touch(&ws, h);
         delta[h] = 0;
-        hpush_or_decrease(&ws.q, h);                             /* line 2 */
+        hpush_or_decrease(&ws.q, h);                             /* queue the root */
         while (ws.q.size) {
-            uint32_t v = hpop(&ws.q);                            /* line 4 */
+            uint32_t v = hpop(&ws.q);                            /* the closest queued vertex */
             ws.done[v] = 1;
             settled++;
-            if (g->rank[v] > Rh) continue;                       /* line 5: rank query */
-            /* line 6: DQ(v, h, delta_v, LR, L_v) */
+            if (g->rank[v] > Rh) continue;                       /* rank query: v outranks h */
+            /* distance query DQ(v, h, delta_v) over L_v and LR */
             int dq = 0;
             for (uint32_t i = 0; i < L[v].len && !dq; ++i) {
                 ++qe;
@@ -408,9 +408,9 @@ static int build_pll(const graph *g, const uint32_t *roots, uint64_t nroots, uin
             }
             if (dq) continue;
             if (delta[v] >= UINT32_MAX) *overflow = 1;
-            if (vpush(&L[v], h, (uint32_t)delta[v])) { rc = -1; break; }   /* line 7 */
+            if (vpush(&L[v], h, (uint32_t)delta[v])) { rc = -1; break; }   /* label (h, delta_v) */
             nl++;
-            for (uint64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {  /* lines 8-10 */
+            for (uint64_t e = g->row_ptr[v]; e < g->row_ptr[v + 1]; ++e) {  /* relax the arcs of v */
                 uint32_t u = g->col[e];
                 arcs++;
                 if (ws.done[u]) continue;

@@ -280,7 +280,7 @@ void chl_server::run_builder() {
     for (;;) {
         Req *r = nullptr;
         {
-            // free memory is read outside the lock: the driver call must not
+            // free memory is read outside the lock: cudaMemGetInfo must not
             // hold up the batcher
             size_t fr = 0, tot = 0;
             cudaMemGetInfo(&fr, &tot);

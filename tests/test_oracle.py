@@ -354,6 +354,24 @@ def test_stats_psi():
     assert st[:, 0].sum() < stc[:, 0].sum()           # early termination explores less
 
 
+def test_pll_query_entry_count():
+    """The label entries Algorithm 1's distance queries read (a work count of
+    the bench's roofline). The first tree reads none (no labels exist yet). In
+    the second tree every list holds exactly the top hub's label, so the count
+    is the root's one entry plus one per settled vertex that the rank query
+    does not drop, which is every settled vertex but the root (the top vertex
+    outranks the root and is dropped). Later trees read at least the root's
+    list."""
+    g, rank = W.load("ba2k")
+    L, st = O.build_labels(g, rank, "pll", with_stats=True)
+    assert L.total == O.build_labels(g, rank, "plant").total
+    q, settled = st[:, 3].astype(np.int64), st[:, 0].astype(np.int64)
+    assert q[0] == 0
+    assert q[1] == 1 + (settled[1] - 2) + 1  # root list + non-root, non-top vertices + the root's own query
+    assert (q[1:] >= 1).all()
+    assert (st[:, 2] <= st[:, 0]).all()
+
+
 def test_overflow_flag():
     big = 2 ** 31
     g = from_edges(4, [(0, 1, big), (1, 2, big), (2, 3, 5)])
