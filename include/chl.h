@@ -133,6 +133,10 @@ typedef struct chl_labels chl_labels;
  *                          alone (the paper's 16-node runs use 100 on
  *                          scale-free and 500 on road networks, where the
  *                          switch also costs communication). Not negative.
+ *   pruned_threads_per_tree  CUDA threads per tree in the phases that prune
+ *                          with the labels of earlier phases (a power of two
+ *                          in [32, 1024]); smaller blocks put more of those
+ *                          small trees in flight. 0 = threads_per_tree
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
@@ -172,6 +176,7 @@ typedef struct {
     int32_t common_hubs;
     int32_t pruned_bucket_delta;
     float psi_threshold;
+    int32_t pruned_threads_per_tree;
 } chl_build_opts;
 
 #define CHL_MAX_COMMON_HUBS 64

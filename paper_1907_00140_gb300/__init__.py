@@ -96,7 +96,8 @@ class chl_build_opts(C.Structure):
                 ("threads_per_tree", C.c_int32), ("bucket_delta", C.c_int32),
                 ("window_buckets", C.c_int32), ("slots", C.c_int32), ("mode", C.c_int32),
                 ("flags", C.c_int32), ("label_capacity", C.c_uint64), ("common_hubs", C.c_int32),
-                ("pruned_bucket_delta", C.c_int32), ("psi_threshold", C.c_float)]
+                ("pruned_bucket_delta", C.c_int32), ("psi_threshold", C.c_float),
+                ("pruned_threads_per_tree", C.c_int32)]
 
 
 class chl_tune_report(C.Structure):

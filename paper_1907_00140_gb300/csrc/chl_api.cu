@@ -74,6 +74,9 @@ cudaError_t grow_records(void **bufs, int nbufs, uint64_t T, uint64_t ncap, cuda
 
 struct Params {
     int tpt;
+    int tpt_lt;          // threads per tree in the label-pruned phases
+    int slots_lt;        // ... and their slots
+    uint32_t fin_words_lt;
     uint32_t delta;
     uint32_t delta_lt;  // bucket width of the phases that prune with the label table
     uint32_t nwin;
@@ -116,9 +119,14 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     }
     p.w_min = g.w_min ? g.w_min : 1;
     p.n = g.n;
+    p.tpt_lt = o.pruned_threads_per_tree ? o.pruned_threads_per_tree : p.tpt;
+    p.fin_words_lt = plant_fin_words(p.tpt_lt, g.n);
     int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words);
     if (per_sm < 1) per_sm = 1;
+    int per_sm_lt = plant_max_slots_per_sm(p.tpt_lt, p.fin_words_lt);
+    if (per_sm_lt < 1) per_sm_lt = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
+    long long slots_lt = o.slots > 0 ? o.slots : (long long)sms * per_sm_lt;
     // slot state per vertex: key + round tag 4 + (4 + nwin) lists of 4 bytes,
     // + 4 for the root's labels of a hybrid build
     const double per_slot = (p.kb + 8.0 + 4.0 * (4 + p.nwin)) * double(g.n) + 64.0;
@@ -126,7 +134,10 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     long long cap = (long long)(budget / per_slot);
     if (o.slots <= 0 && slots > cap) slots = cap;
     if (slots < 1) slots = 1;
+    if (o.slots <= 0 && slots_lt > cap) slots_lt = cap;
+    if (slots_lt < 1) slots_lt = 1;
     p.slots = int(slots);
+    p.slots_lt = int(slots_lt);
     return p;
 }
 
@@ -155,15 +166,15 @@ struct SlotState {
     DevBuf key, tags, lists, ctr;
     cudaError_t alloc(const Params &P, uint32_t n, cudaStream_t s) {
         key.s = tags.s = lists.s = ctr.s = s;
-        const size_t sn = size_t(P.slots) * n;
+        const size_t sn = size_t(std::max(P.slots, P.slots_lt)) * n;
         cudaError_t e;
         if ((e = cudaMallocAsync(&key.p, sn * P.kb, s))) return e;
         if ((e = cudaMemsetAsync(key.p, 0xFF, sn * P.kb, s))) return e;
         if ((e = cudaMallocAsync(&tags.p, sn * 4, s))) return e;
         if ((e = cudaMemsetAsync(tags.p, 0, sn * 4, s))) return e;
         if ((e = cudaMallocAsync(&lists.p, sn * 4 * (4 + P.nwin), s))) return e;
-        if ((e = cudaMallocAsync(&ctr.p, size_t(P.slots) * 16, s))) return e;
-        if ((e = cudaMemsetAsync(ctr.p, 0, size_t(P.slots) * 16, s))) return e;
+        if ((e = cudaMallocAsync(&ctr.p, size_t(std::max(P.slots, P.slots_lt)) * 16, s))) return e;
+        if ((e = cudaMemsetAsync(ctr.p, 0, size_t(std::max(P.slots, P.slots_lt)) * 16, s))) return e;
         return cudaSuccess;
     }
     void fill(const Params &P, uint32_t n, TreeLaunch &tl) const {
@@ -337,6 +348,10 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (o.threads_per_tree && (o.threads_per_tree < 32 || o.threads_per_tree > 1024 ||
                                (o.threads_per_tree & (o.threads_per_tree - 1))))
         return set_error(CHL_EINVAL, "threads_per_tree must be a power of two in [32, 1024]");
+    if (o.pruned_threads_per_tree &&
+        (o.pruned_threads_per_tree < 32 || o.pruned_threads_per_tree > 1024 ||
+         (o.pruned_threads_per_tree & (o.pruned_threads_per_tree - 1))))
+        return set_error(CHL_EINVAL, "pruned_threads_per_tree must be a power of two in [32, 1024]");
     if (o.window_buckets && (o.window_buckets < 2 || o.window_buckets > 64))
         return set_error(CHL_EINVAL, "window_buckets must be in [2,64]");
     if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
@@ -437,7 +452,12 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         chl_build_opts oq = o;
         if (o.mode == 1 && !oq.threads_per_tree) oq.threads_per_tree = 512;  // plain form: one CTA
         P = choose_params(rg, oq, sms, free_b);
-        if (o.mode == 1) P.slots = 1;
+        if (o.mode == 1) {
+            P.slots = 1;
+            P.slots_lt = 1;
+            P.tpt_lt = P.tpt;
+            P.fin_words_lt = P.fin_words;
+        }
     }
 
     CUDA_TRY(slot.alloc(P, n, s));
@@ -507,6 +527,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             tl.lt_root = (uint32_t *)b_ltroot.p;
             tl.lt_hash_max = (o.flags & CHL_FLAG_DENSE_ROOT_LABELS) ? 0 : 0xFFFFFFFFu;
             set_delta(tl, P.delta_lt);
+            tl.fin_words = P.fin_words_lt;
+            tl.fin_bits = P.fin_words_lt * 32 < n ? P.fin_words_lt * 32 : n;
         }
         // the batched form first writes the labels of the phase's trivial
         // roots and lists the others: room for one record per root
@@ -572,6 +594,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
                     CUDA_TRY(launch_plant_trees(one, P.tpt, 1, s));
                     ++launches;
                 }
+            } else if (lt.offsets) {
+                CUDA_TRY(launch_plant_trees(tl, P.tpt_lt, P.slots_lt, s));
+                ++launches;
             } else {
                 CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
                 ++launches;
@@ -666,8 +691,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         // every label so far, as CSR, for the next phase's pruning: the first
         // time sorted from all records, then grown by each phase's new ones
         if (!b_ltroot.p) {
-            CUDA_TRY(cudaMallocAsync(&b_ltroot.p, size_t(P.slots) * n * 4, s));
-            CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, size_t(P.slots) * n * 4, s));
+            CUDA_TRY(cudaMallocAsync(&b_ltroot.p, size_t(P.slots_lt) * n * 4, s));
+            CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, size_t(P.slots_lt) * n * 4, s));
         }
         if (!lt.offsets)
             CUDA_TRY(assemble_table(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,

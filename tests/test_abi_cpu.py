@@ -75,7 +75,8 @@ def test_bad_options_are_einval(lib):
     out = C.c_void_p()
     for field, val in [("common_hubs", 65), ("threads_per_tree", 48), ("threads_per_tree", 96), ("threads_per_tree", 2048), ("window_buckets", 1), ("mode", 3),
                        ("root_end", 9), ("slots", -1), ("flags", 16), ("pruned_bucket_delta", -2),
-                       ("psi_threshold", -1.0), ("psi_threshold", float("nan"))]:
+                       ("psi_threshold", -1.0), ("psi_threshold", float("nan")),
+                       ("pruned_threads_per_tree", 48), ("pruned_threads_per_tree", 2048)]:
         o = chl.chl_build_opts()
         setattr(o, field, val)
         assert lib.chl_build(C.byref(g), C.c_void_p(1), C.byref(o), None, C.byref(out)) == chl.CHL_EINVAL, field

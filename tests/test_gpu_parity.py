@@ -284,7 +284,8 @@ def test_hybrid_phases_are_exact():
     for opts in (dict(), dict(threads_per_tree=256), dict(threads_per_tree=1024, bucket_delta=2),
                  dict(flags=chl.CHL_FLAG_DENSE_ROOT_LABELS), dict(pruned_bucket_delta=1),
                  dict(pruned_bucket_delta=4096, flags=chl.CHL_FLAG_PARENTS), dict(psi_threshold=0.5),
-                 dict(psi_threshold=8.0, label_capacity=1000)):
+                 dict(psi_threshold=8.0, label_capacity=1000), dict(pruned_threads_per_tree=256),
+                 dict(threads_per_tree=512, pruned_threads_per_tree=64, slots=5)):
         L = chl.build_labels(G, R, **opts)
         st = L.stats()
         assert st["phases"] > 1, st
