@@ -195,9 +195,12 @@ typedef struct {
  *   launches       kernels launched by the build
  *   rounds         expansion rounds of the tree searches (all trees)
  *   buckets        distance buckets entered after the first (all trees)
- *   pruned         expansions cut by the Common Label Table (all trees)
- *   table_ms       device time of building the Common Label Table (its trees
- *                  and the table fill; part of tree_ms), 0 without a table
+ *   pruned         expansions cut by the Common Label Table or by the label
+ *                  table of earlier phases (all trees)
+ *   table_ms       device time of building the Common Label Table (part of
+ *                  tree_ms): its trees and the fill, or in a hybrid build,
+ *                  whose first phase holds the table's trees, the fill alone;
+ *                  0 without a table
  *   phases         tree phases run (1 unless the build is hybrid)
  *   label_table_phases  phases whose trees pruned with the label table of the
  *                  earlier ones (0: the switch threshold was never passed)
