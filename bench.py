@@ -490,7 +490,8 @@ def main():
         # its floor (batched phases see staler tables; that overhead is not credited)
         wu = work_units(f"{name}/pll")
     if wu and wu_plain:
-        algo = 28.0 * wu["S"] + 16.0 * wu["A"] + 12.0 * wu_plain["T"]
+        T_units = wu["T"] if wu.get("T_exact") else wu_plain["T"]
+        algo = 28.0 * wu["S"] + 16.0 * wu["A"] + 12.0 * T_units
         if hybrid:
             # plus the label entries (hub, dist: 8 B) its distance queries read
             algo += 8.0 * wu.get("Q", 0.0)
