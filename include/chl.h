@@ -8,20 +8,20 @@
  *   a ranking function R (a total order on V, larger R = more important;
  *   Sec. 1), the CHL holds a label (h, d(v,h)) in L_v exactly when h is the
  *   highest-ranked vertex of SP_{v,h}, the set of vertices on all shortest
- *   v-h paths (Sec. 1; Lemma 1 of Sec. 3.1). It is unique for a fixed R and
+ *   v-h paths (Sec. 1; Lemma 1 of Sec. 4.1). It is unique for a fixed R and
  *   minimal (Sec. 1).
  *
- *   chl_build computes it the PLaNT way (Sec. 4.2, Algorithm 3): one
+ *   chl_build computes it the PLaNT way (Sec. 5.2, Algorithm 3): one
  *   shortest-path tree per root h that carries, for every vertex, its
  *   distance and the highest rank seen on any shortest path to it; a vertex
  *   receives h as a hub when no higher-ranked vertex lies on any of its
  *   shortest paths from h, and a tree stops once every pending vertex is
- *   outranked (early termination, Sec. 4.2). Labels of each vertex are then
+ *   outranked (early termination, Sec. 5.2). Labels of each vertex are then
  *   sorted by hub rank (Algorithm 2, sort step).
  *
  *   chl_query answers point-to-point shortest distance (PPSD) queries,
  *   d(u,v) = min over common hubs h of d(u,h) + d(v,h) (Sec. 1), by merging
- *   the two rank-sorted label lists (Sec. 5, querying with labels on a single
+ *   the two rank-sorted label lists (Sec. 6, querying with labels on a single
  *   node).
  *
  * Conventions
@@ -95,7 +95,7 @@ typedef struct chl_labels chl_labels;
  *   root_begin, root_end   build only trees whose root has rank position p in
  *                          [root_begin, root_end), p = n-1-R(root) (p = 0 is
  *                          the most important vertex). root_end = 0 means n.
- *                          Trees are independent (Sec. 4.2), so disjoint
+ *                          Trees are independent (Sec. 5.2), so disjoint
  *                          ranges partition the labels by hub.
  *   threads_per_tree       CUDA threads cooperating on one tree (a power of
  *                          two in [32, 1024])
@@ -111,7 +111,7 @@ typedef struct chl_labels chl_labels;
  *   label_capacity         initial size of the label buffer in labels; when
  *                          a tree does not fit, the buffer doubles and the
  *                          roots that did not fit are built again
- *   common_hubs            eta of the Common Label Table (Sec. 4.3): the trees
+ *   common_hubs            eta of the Common Label Table (Sec. 5.3): the trees
  *                          of the eta most important roots are built first and
  *                          all their labels kept in a table; every other tree
  *                          skips (no label, no relaxation) a vertex whose
@@ -124,7 +124,7 @@ typedef struct chl_labels chl_labels;
  *                          the labels of earlier phases (their trees are
  *                          small, so wide buckets save rounds); 0 = the power
  *                          of two nearest twice the mean arc weight
- *   psi_threshold          Psi_th of the hybrid switch (Sec. 4.3): once a
+ *   psi_threshold          Psi_th of the hybrid switch (Sec. 5.2): once a
  *                          phase expands more than Psi_th vertices per label it
  *                          generates, the later phases prune with the labels of
  *                          the earlier ones. 0 = 16, and the switch also fires
@@ -145,7 +145,7 @@ typedef struct chl_labels chl_labels;
 /* chl_build_opts.flags: store with every label (h, d) of v the parent of v in
    the shortest-path tree of h (the next vertex from v towards h; h itself for
    the label of h), which lets chl_path return shortest paths in time linear in
-   their length (Sec. 4.3, Extensions). Keys become 8 bytes; labels take 16
+   their length (Sec. 5.4, Extensions). Keys become 8 bytes; labels take 16
    instead of 12 bytes. Among several shortest-path predecessors the one with
    the highest rank is stored, so the parents are unique for a fixed R. */
 #define CHL_FLAG_PARENTS 2
@@ -153,7 +153,7 @@ typedef struct chl_labels chl_labels;
    phase (no hybrid pruning). By default such a build runs its roots in phases
    of doubling size, and the trees of each phase also skip a vertex whose
    distance query over all labels of the earlier phases is at most its
-   distance (the PLaNT-to-label-pruning hybrid of Sec. 4.3, on one GPU: the
+   distance (the PLaNT-to-label-pruning hybrid of Sec. 5.2, on one GPU: the
    earlier phases' hubs form a rank-closed set, so the labels stay canonical
    and no cleaning pass is needed). */
 #define CHL_FLAG_NO_HYBRID 4
@@ -225,7 +225,7 @@ typedef struct {
 
 /*
  * chl_build — canonical hub labels of g under ranking `rank` (PLaNT,
- * Sec. 4.2, Algorithm 3; early termination as in Sec. 4.2; label sort as in
+ * Sec. 5.2, Algorithm 3; early termination as in Sec. 5.2; label sort as in
  * Algorithm 2).
  *   g        input graph (see chl_csr); g->mem says where its arrays are
  *   rank     [n] uint32 R(v), a permutation of [0,n); same memory kind as g
@@ -299,7 +299,7 @@ chl_status chl_labels_copy(const chl_labels *L, uint64_t *offsets, uint32_t *hub
                            chl_mem dst_mem, void *stream);
 
 /*
- * chl_query — PPSD queries (Sec. 1 cover property; Sec. 5 QLSN merge).
+ * chl_query — PPSD queries (Sec. 1 cover property; Sec. 6 QLSN merge).
  *   pairs    [q][2] uint32 vertex ids (u, v), device or host per `mem`
  *   q        number of pairs (0 is allowed and does nothing)
  *   out      [q] uint32, out[i] = d(u_i, v_i), UINT32_MAX if u_i and v_i are
@@ -344,7 +344,7 @@ chl_status chl_labels_parents(const chl_labels *L, uint32_t *parent, chl_mem mem
  * canonical hub H (the highest-ranked hub among those with the minimum
  * d(u,H) + d(H,v), i.e. the highest-ranked vertex on its shortest paths) is
  * found by the query merge; the path then follows the stored parents from u
- * to H and from v to H (Sec. 4.3, Extensions): time linear in its length.
+ * to H and from v to H (Sec. 5.4, Extensions): time linear in its length.
  *   paths  [q][max_len] vertex ids, u first and v last; entries past the
  *          path's length (or past max_len) are left untouched
  *   lens   [q] vertices on the path (1 for u = v, 0 when u and v are not
@@ -366,7 +366,7 @@ const char *chl_version(void);
 
 /* ====================================================================== serving
  * A request loop on one GPU (the paper has no counterpart: it answers queries
- * one at a time from resident labels, Sec. 5 QLSN). Label sets stay resident in
+ * one at a time from resident labels, Sec. 6 QLSN). Label sets stay resident in
  * device memory; PPSD queries that arrive while others are on the GPU are
  * gathered into the next batch (continuous batching) of one launch that may mix
  * label sets, with up to `query_slots` batches in flight on their own streams;

@@ -8,10 +8,10 @@ benchmark's CPU-baseline leg may import this package; the GPU library
 Functions follow the paper:
   * ``build_labels``: the canonical labeling (Sec. 1), three independent ways:
       ``"canonical"`` — the definition (h is a hub of v iff h is the
-      highest-ranked vertex of SP_{v,h}; Sec. 1, Lemma 1 in Sec. 3.1);
+      highest-ranked vertex of SP_{v,h}; Sec. 1, Lemma 1 in Sec. 4.1);
       ``"plant"`` — Algorithm 3 (PLaNTDijkstra) with early termination;
-      ``"pll"`` — Algorithm 1 run sequentially in rank order (Sec. 3).
-  * ``query``: PPSD by linear merge of rank-sorted lists (Sec. 1, Sec. 5 QLSN).
+      ``"pll"`` — Algorithm 1 run sequentially in rank order (Sec. 4).
+  * ``query``: PPSD by linear merge of rank-sorted lists (Sec. 1, Sec. 6 QLSN).
   * ``count_redundant``: labels that ``DQ_Clean`` (Algorithm 2) flags.
 """
 from __future__ import annotations
@@ -97,10 +97,10 @@ def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
 
     method: "canonical" (the definition), "plant" (Algorithm 3), "pll"
     (sequential Algorithm 1) or "plant_clt" (Algorithm 3 pruned by the Common
-    Label Table of the `eta` most important hubs, Sec. 4.3; eta is capped at n).
+    Label Table of the `eta` most important hubs, Sec. 5.3; eta is capped at n).
 
     roots: None = every vertex in descending rank; else only labels with hub
-    in `roots` are produced (each tree is independent, Sec. 4.2).
+    in `roots` are produced (each tree is independent, Sec. 5.2).
     tie_seed != 0 randomises the pop order of equal-distance vertices.
     Returns Labels, or (Labels, stats[k,4] = settled, arcs scanned, labels per
     root, label entries read by the distance queries (Algorithm 1 only)) when
@@ -158,7 +158,7 @@ def count_redundant(L: Labels, rank) -> int:
 
 # ------------------------------------------------------------------ shortest-path recovery
 def parents(g, rank, L: Labels) -> np.ndarray:
-    """SPT parent of every label, aligned with L.hub/L.dist (Sec. 4.3,
+    """SPT parent of every label, aligned with L.hub/L.dist (Sec. 5.4,
     Extensions: the parent of v in the tree of h stored with the label).
     For (h, d) in L_v, v != h: the highest-ranked neighbour p of v on a shortest
     h-v path, i.e. with d(h, p) + w(p, v) = d. Every vertex of those paths has h

@@ -13,9 +13,9 @@
  * included; L_v the labels (h, d(v,h)) of v.
  *
  * Three independent ways to build the labeling are provided; the paper proves
- * each yields the CHL (Sec. 1 definition; Sec. 4.2 PLaNT; Sec. 3 sequential PLL):
+ * each yields the CHL (Sec. 1 definition; Sec. 5.2 PLaNT; Sec. 4 sequential PLL):
  *
- *   ORC_CANONICAL  the definition (Sec. 1; Lemma 1, Sec. 3.1): (h, d(v,h)) is
+ *   ORC_CANONICAL  the definition (Sec. 1; Lemma 1, Sec. 4.1): (h, d(v,h)) is
  *                  in L_v iff h is the highest-ranked vertex of SP_{v,h}.
  *                  Per root h: full Dijkstra, then best[v] = max rank over
  *                  SP_{h,v} by one pass over the settle order, label iff
@@ -24,18 +24,18 @@
  *                  notation, with early termination (cnt). Reading used: a
  *                  popped vertex outranked by nA gets no label but is still
  *                  relaxed; the paper states PLaNT does not prune trees
- *                  (Sec. 1, Sec. 4.2) and its termination rule counts such
+ *                  (Sec. 1, Sec. 5.2) and its termination rule counts such
  *                  vertices as explored.
  *   ORC_PLL        Algorithm 1 (pruned Dijkstra with rank queries) run
  *                  sequentially over roots in descending rank; sequential
- *                  PLL outputs the CHL (Sec. 3, proof of Claim 1).
- *   ORC_PLANT_CLT  PLaNT with the Common Label Table of Sec. 4.3: first the
+ *                  PLL outputs the CHL (Sec. 4, proof of Claim 1).
+ *   ORC_PLANT_CLT  PLaNT with the Common Label Table of Sec. 5.3: first the
  *                  trees of the eta most important roots (Algorithm 3, no
  *                  pruning); their labels, for every vertex, form the table
  *                  HC. Every other tree is Algorithm 3 in which a popped v is
  *                  pruned (no label, no relaxation) when a distance query on
  *                  HC, min over the table's hubs c of d(h,c) + d(c,v), is at
- *                  most delta_v. Sec. 4.3 states the resulting labels are not
+ *                  most delta_v. Sec. 5.3 states the resulting labels are not
  *                  redundant because HC holds all labels of every hub ranked
  *                  above any hub it prunes with.
  *
@@ -207,7 +207,7 @@ static void ws_free(workspace *w) {
     free(w->q.heap); free(w->q.where); free(w->out.buf);
 }
 
-/* reset only the entries the previous tree modified (footnote in Sec. 3.1) */
+/* reset only the entries the previous tree modified (footnote in Sec. 4.1) */
 static void ws_reset(workspace *w) {
     for (size_t i = 0; i < w->ntouched; ++i) {
         uint32_t v = w->touched[i];
@@ -227,7 +227,7 @@ typedef struct {
     const uint32_t *col;
     const uint32_t *w;
     const uint32_t *rank;
-    /* Common Label Table (Sec. 4.3), or NULL: hc[v * eta + i] = d(v, c_i) when
+    /* Common Label Table (Sec. 5.3), or NULL: hc[v * eta + i] = d(v, c_i) when
        (c_i, d) is a label of v, UINT32_MAX otherwise, c_i the vertex of rank
        n-1-i (i = 0 most important) */
     const uint32_t *hc;
@@ -298,7 +298,7 @@ static inline uint32_t argmax_rank(const graph *g, uint32_t x, uint32_t y) {
     return g->rank[x] >= g->rank[y] ? x : y;
 }
 
-/* distance query on the Common Label Table between h and v (Sec. 4.3) */
+/* distance query on the Common Label Table between h and v (Sec. 5.3) */
 static uint64_t hc_query(const graph *g, uint32_t h, uint32_t v) {
     uint64_t best = INF64;
     const uint32_t *a = g->hc + (uint64_t)h * g->eta, *b = g->hc + (uint64_t)v * g->eta;
@@ -328,7 +328,7 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
         settled++;
         uint32_t nA = argmax_rank(g, v, a[v]);                 /* nA = argmax_{x in {v,a[v]}} R(x) */
         if (a[v] == h) cnt--;
-        if (prune && hc_query(g, h, v) <= delta[v]) continue;  /* Sec. 4.3: pruned */
+        if (prune && hc_query(g, h, v) <= delta[v]) continue;  /* Sec. 5.3: pruned */
         if (g->rank[nA] <= Rh) {                               /* R[nA] > R[h]: no label */
             if (emit(ws, v, h, delta[v])) return;              /* L_v = L_v U {(h, delta_v)} */
             nl++;
@@ -444,7 +444,7 @@ typedef struct {
     int method;
     const uint32_t *roots;
     uint64_t nroots;
-    _Atomic uint64_t next;   /* dynamic claim of the next root (Sec. 3.1) */
+    _Atomic uint64_t next;   /* dynamic claim of the next root (Sec. 4.1) */
     root_stats *stats;
     uint64_t tie_seed;
 } job;
@@ -645,7 +645,7 @@ int orc_build(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const ui
     return rc;
 }
 
-/* ------------------------------------------------------------------ queries (Sec. 5, QLSN) */
+/* ------------------------------------------------------------------ queries (Sec. 6, QLSN) */
 /*
  * d(u,v) = min over common hubs h of d(u,h) + d(v,h) (Sec. 1): linear merge
  * of the two rank-sorted lists, scanned to the end. UINT32_MAX when no hub is

@@ -2,19 +2,19 @@
 
 TEST/BENCH INFRASTRUCTURE: calls only ``oracle`` and ``workloads``.
 
-For the PLaNT build (Algorithm 3 with early termination, Sec. 4.2) the units
+For the PLaNT build (Algorithm 3 with early termination, Sec. 5.2) the units
 are, summed over all roots h:
   S = vertices settled (popped) by the tree of h,
   A = arcs scanned by those vertices,
   T = labels emitted (= total size of the canonical labeling).
 T is exact up to `pll_below` vertices: sequential Algorithm 1 (pruned
-Dijkstra with rank queries, Sec. 3) builds the same labeling quickly; above
+Dijkstra with rank queries, Sec. 4) builds the same labeling quickly; above
 that it is estimated like S and A. S and A are exact for small workloads and
 otherwise a stratified estimate: every one of the 64 most important roots,
 then rank-position strata of doubling width with `per_stratum` seeded roots
 each (mean x stratum size), with a standard error.
 
-With the Common Label Table (Sec. 4.3) the trees explore less; the entry
+With the Common Label Table (Sec. 5.3) the trees explore less; the entry
 "<workload>/clt<eta>" holds S and A of Algorithm 3 pruned by the table of the
 eta most important hubs (the table's own trees included), same sampling.
 

@@ -8,10 +8,10 @@ of that header is exposed under the same name with the same arguments
 computation happens inside libchl.so on the GPU; there is no CPU fallback, and
 calling into this module without a built library raises.
 
-Method: PLaNT (Lakhotia et al., arXiv 1907.00140, Sec. 4.2, Algorithm 3)
+Method: PLaNT (Lakhotia et al., arXiv 1907.00140, Sec. 5.2, Algorithm 3)
 builds one shortest-path tree per root in rank order and labels a vertex with
 the root exactly when no higher-ranked vertex lies on any of its shortest
-paths from the root; queries merge the two rank-sorted label lists (Sec. 5).
+paths from the root; queries merge the two rank-sorted label lists (Sec. 6).
 """
 from __future__ import annotations
 

@@ -213,7 +213,7 @@ void free_csr(LabelCSR &c, cudaStream_t s) {
     c = LabelCSR{};
 }
 
-// Common Label Table (Sec. 4.3): all labels of the `hubs` most important
+// Common Label Table (Sec. 5.3): all labels of the `hubs` most important
 // vertices, as a dense [n][stride] table of distances (all ones = no label).
 struct CommonTable {
     DevBuf buf;
@@ -484,7 +484,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (parents) CUDA_TRY(cudaMallocAsync(&b_op.p, cap * 4, s));
 
     CUDA_TRY(cudaEventRecord(ev[1], s));
-    // Hybrid phases (Sec. 4.3): a build that starts at the top root runs its
+    // Hybrid phases (Sec. 5.2): a build that starts at the top root runs its
     // roots in phases; the trees of a phase also prune with every label of all
     // earlier phases (a rank-closed hub set, so the labels stay canonical)
     // once the switch has fired. Other builds run as one phase.
@@ -654,7 +654,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             cap *= 2;
         }
     }
-    // The switch of Sec. 4.3: label pruning starts once a phase's trees explore
+    // The switch of Sec. 5.2: label pruning starts once a phase's trees explore
     // many vertices per label (Psi = expansions / labels above psi_th), or once
     // the Common Label Table pruned a large share of their expansions; before
     // that, the per-vertex table query would cost more than it saves.

@@ -55,7 +55,7 @@ struct TreeLaunch {
     uint32_t w_min;     // lightest arc weight
     uint32_t fin_words; // settled-filter bitmap words in dynamic shared memory
     uint32_t fin_bits;  // vertices (pos) the bitmap covers: min(n, 32 * fin_words)
-    // Common Label Table (Sec. 4.3), or hc = null: hc[v * hc_stride + c] =
+    // Common Label Table (Sec. 5.3), or hc = null: hc[v * hc_stride + c] =
     // d(v, c) for table hub c (pos c < hc_hubs) when (c, d) is a label of v,
     // else all ones; hc_stride = hc_hubs rounded up to a multiple of 4
     const uint32_t *hc;

@@ -8,7 +8,7 @@
 // vertex with the highest rank becomes 0. In that numbering the ancestor with
 // the highest rank is the smallest id, so "highest-ranked ancestor" in
 // Algorithm 3 becomes an unsigned min inside the packed search key, and the
-// trees of the most important roots (the largest ones, Sec. 4.1 label counts
+// trees of the most important roots (the largest ones, Sec. 5.1 label counts
 // per tree) come first in the claim order.
 #include <cstdio>
 

@@ -1,7 +1,7 @@
 // Label assembly: from the (vertex, hub, dist) records the trees emit, in
 // whatever order the trees finished, to per-vertex lists sorted by hub rank
 // (Algorithm 2, "sort labels in L_v using hub rank"; the lists are stored
-// per vertex only, as in the footnote of Sec. 6.2).
+// per vertex only, as in the footnote of Sec. 7.2).
 //
 //   1. count labels per vertex (atomic histogram)
 //   2. exclusive scan -> offsets

@@ -2,7 +2,7 @@
 //
 // d(u,v) = min over hubs h in L_u and L_v of d(u,h) + d(v,h) (Sec. 1, cover
 // property); the paper's single-node mode merges the two hub-rank-sorted lists
-// (Sec. 5 QLSN, footnote of Sec. 6.2 on linear-merge querying).
+// (Sec. 6 QLSN, footnote of Sec. 7.2 on linear-merge querying).
 //
 // One warp per query. Both lists are read in 32-entry chunks with coalesced
 // loads (hub rank position, ascending). Each lane takes one entry of the L_u
@@ -142,7 +142,7 @@ __device__ __forceinline__ uint64_t find_hub(const uint64_t *__restrict__ off,
     return __ldg(&hp[lo]) == hpos ? lo : ~0ull;
 }
 
-// Shortest paths by following the SPT parents stored with the labels (Sec. 4.3
+// Shortest paths by following the SPT parents stored with the labels (Sec. 5.4,
 // Extensions): from u and from v towards their canonical hub H, each step the
 // parent stored with w's label of H. One warp per pair (merge), lane 0 walks.
 __global__ void paths_kernel(uint32_t n, const uint64_t *__restrict__ off,

@@ -1,16 +1,16 @@
-// PLaNT shortest-path trees on the GPU (Sec. 4.2, Algorithm 3).
+// PLaNT shortest-path trees on the GPU (Sec. 5.2, Algorithm 3).
 //
 // One persistent launch builds every tree of a root range. Each CTA owns a
 // tree "slot" (dense per-vertex state in global memory) and repeatedly claims
 // the next root in rank order with a global atomic counter, the dynamic
-// root claiming of Sec. 3.1 (threads pop the most important remaining root).
+// root claiming of Sec. 4.1 (threads pop the most important remaining root).
 //
 // Per tree the search is a bucketed label-correcting Dijkstra (delta-stepping,
 // bucket width delta) over packed keys (see "Keys" below): an atomicMin keeps
 // the shortest distance and, at equal distance, prefers a path through a
 // vertex that outranks the root (Algorithm 3, equal-distance branch). Every
 // vertex that is expanded relaxes all its arcs, labelled or not: PLaNT does
-// not prune trees (Sec. 1, Sec. 4.2); a vertex outranked by its ancestor only
+// not prune trees (Sec. 1, Sec. 5.2); a vertex outranked by its ancestor only
 // gets no label.
 //
 // Pending vertices (keys in later buckets) are held per bucket:
@@ -21,14 +21,14 @@
 //            used up it restarts at the nearest far bucket
 //   nxt      vertices improved inside the current bucket during a round
 // plus `touched`, every vertex that got a finite key (for emission and for
-// resetting only what the tree modified, footnote of Sec. 3.1).
+// resetting only what the tree modified, footnote of Sec. 4.1).
 // The value an atomicMin replaces says which lists already hold the vertex,
 // since buckets only move down: a window bucket is joined iff the old key was
 // in another bucket, far iff the old key was unreached (a key beyond the
 // window was far-listed when it was set, and keys never rise back past the
 // window). Only the per-round nxt list needs a tag (rtag, the round id).
 //
-// Early termination (Sec. 4.2). The paper stops when every vertex in
+// Early termination (Sec. 5.2). The paper stops when every vertex in
 // Dijkstra's queue is outranked; Algorithm 3 keeps the count `cnt` of queued
 // vertices whose ancestor is the root. Here `cnt` counts the live vertices
 // whose key lies beyond the current bucket: every successful atomicMin on a
@@ -72,7 +72,7 @@ constexpr int QSTEPS = 4;             // label-table query: loads in flight per 
 // clean = 1 iff no vertex before v on the best known paths outranks h. Under
 // unsigned min a shorter distance wins and, at equal distance, clean = 0
 // wins: a vertex is outranked as soon as one of its shortest paths is (the
-// equal-distance branch of Algorithm 3; Sec. 4.2's example, a[v5] = v1).
+// equal-distance branch of Algorithm 3; Sec. 5.2's example, a[v5] = v1).
 // v is live (would get the label (h, d)) iff clean and v >= h, and the bit
 // it passes on to its out-neighbours is exactly its own liveness.
 // Three layouts (K below is one of these traits; K::T is the stored word):
@@ -81,7 +81,7 @@ constexpr int QSTEPS = 4;             // label-table query: loads in flight per 
 //                                              checks w_max * n)
 //   KeyW  uint64  dist << 1 | clean            otherwise
 //   KeyP  uint64  dist << 32 | clean << 31 | parent, for path recovery (the
-//                 SPT parent stored with each label, Sec. 4.3 Extensions):
+//                 SPT parent stored with each label, Sec. 5.4 (Extensions)):
 //                 among equal (dist, clean) the smallest parent id wins, so
 //                 the parent is the lowest-numbered tight predecessor, a
 //                 deterministic choice. A candidate carries its source
@@ -385,7 +385,7 @@ __device__ __forceinline__ uint32_t owner(const Frontier<TPB, K> &F, uint64_t j,
 // row that covers i0 (the last row of the previous step). Lanes first load
 // UNROLL arcs, then UNROLL keys, then commit, so each lane has UNROLL
 // independent loads in flight at each stage.
-// Common Label Table pruning (Sec. 4.3): the distance query between the root
+// Common Label Table pruning (Sec. 5.3): the distance query between the root
 // and v over the table hubs, min_c d(h, c) + d(c, v); the table row of v is
 // read as 16-byte vectors (rows are padded to a multiple of 4 hubs)
 __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared &S, uint32_t v) {
@@ -407,7 +407,7 @@ __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared 
 // rank position below p.lt_hubs, as CSR by vertex rank position (entries of a
 // vertex unordered). min over shared hubs c of d(h,c) + d(c,v) <= dv means a
 // vertex outranking h lies on a shortest h-v path, as for the Common Label
-// Table: the table is complete for a rank-closed set of hubs (Sec. 4.3). The
+// Table: the table is complete for a rank-closed set of hubs (Sec. 5.3). The
 // query must see every table label of h and of v: a vertex reached only past a
 // pruned one is left with a wrong distance and ancestor unless it is pruned
 // too, which the complete query guarantees (a partial one would not). The
@@ -540,7 +540,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
         }
         if (cut) {
             // a table hub, which outranks h, lies on a shortest h-v path:
-            // v gets no label and is not expanded (Sec. 4.3)
+            // v gets no label and is not expanded (Sec. 5.3)
             ++pruned;
             deg = 0;
             if (clean) atomic_min_key(&sl.key[vid], make_key<K>(dv, false, 0));

@@ -1,6 +1,6 @@
 """Full-size parity on sampled outputs.
 
-Trees are independent (Sec. 4.2), so the labels whose hub is a sampled root
+Trees are independent (Sec. 5.2), so the labels whose hub is a sampled root
 can be checked one tree at a time against the oracle; the whole labeling is
 checked through the cover property (query = Dijkstra distance, Sec. 1) on
 sampled pairs and through invariants that hold at any size. The GPU build

@@ -1,7 +1,7 @@
 """GPU parity: labels and query answers of libchl.so against the CPU oracle.
 
 All arithmetic is integer and the canonical labeling is unique for a fixed
-rank (Sec. 1; PLaNT, DGLL and Hybrid produce the same labels, Sec. 6.3), so
+rank (Sec. 1; PLaNT, DGLL and Hybrid produce the same labels, Sec. 7.3), so
 every comparison is bit-exact: offsets, hub ids, distances and query answers.
 Calls go through the C ABI (ctypes binding) with device tensors, except where
 the host-memory path itself is under test.
@@ -170,7 +170,7 @@ def test_tuned_parameters_are_exact(ba2k):
 
 
 def test_common_label_table_prunes(ba2k):
-    """The table (Sec. 4.3) cuts expansions and arcs but not one label."""
+    """The table (Sec. 5.3) cuts expansions and arcs but not one label."""
     g, rank, ref = ba2k
     G, R = DG(g), dev(rank)
     off_ = chl.build_labels(G, R, common_hubs=-1)
@@ -275,7 +275,7 @@ def test_query_rejects_bad_vertex(ba2k):
 
 def test_hybrid_phases_are_exact():
     """A scale-free build deep enough to pass the Psi switch prunes its later
-    phases with the label table of the earlier ones (Sec. 4.3) and still equals
+    phases with the label table of the earlier ones (Sec. 5.2) and still equals
     the oracle; the single-phase build gives the same labels with more work."""
     g = W.rmat(14, 16, seed=14, wlo=1, whi=255)
     rank = W.degree_rank(g)

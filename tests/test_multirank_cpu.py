@@ -1,5 +1,5 @@
 """Host logic of the multi-rank form on CPU (gloo, world size 2): trees are
-independent (Sec. 4.2), so ranks that build disjoint root ranges (the ABI's
+independent (Sec. 5.2), so ranks that build disjoint root ranges (the ABI's
 root_begin/root_end) hold disjoint, hub-partitioned label sets whose union is
 the full labeling; the benchmark's step time is the maximum over ranks. The
 per-rank labels here come from the oracle (no GPU); the GPU build of a root

@@ -7,7 +7,7 @@ fails at least one of them:
     scipy, hub of v = highest-ranked vertex of SP_{v,h}; Sec. 1, Lemma 1),
   * closed forms (tree, star, path) and two hand-derived fixtures
     (tests/golden: the "always relax" reading of Algorithm 3 and the
-    equal-distance tie rule of the Sec. 4.2 example),
+    equal-distance tie rule of the Sec. 5.2 example),
   * the cover property against scipy's Dijkstra (Sec. 1),
   * minimality by DQ_Clean (Algorithm 2, Lemma 2),
   * uniqueness under shuffled root order and randomised tie-breaking,
@@ -333,7 +333,7 @@ def test_invariants():
 
 
 def test_subset_of_roots_is_hub_partition():
-    """Trees are independent (Sec. 4.2): labels of a root subset are exactly the
+    """Trees are independent (Sec. 5.2): labels of a root subset are exactly the
     full labels whose hub lies in that subset."""
     g, rank = W.load("ba2k")
     full = O.build_labels(g, rank, "plant")
@@ -380,7 +380,7 @@ def test_overflow_flag():
     assert not O.build_labels(from_edges(3, [(0, 1, 5), (1, 2, 5)]), rank[:3] - 1, "plant").overflow
 
 
-# ------------------------------------------------------------------ Common Label Table (Sec. 4.3)
+# ------------------------------------------------------------------ Common Label Table (Sec. 5.3)
 @pytest.mark.parametrize("name,g,rank", tiny_cases(), ids=[c[0] for c in tiny_cases()])
 @pytest.mark.parametrize("eta", [1, 2, 5])
 def test_common_label_table_brute_force(name, g, rank, eta):
@@ -436,7 +436,7 @@ def test_common_label_table_root_subset():
         assert np.array_equal(part.dist, full.dist[keep])
 
 
-# ------------------------------------------------------------------ shortest-path recovery (Sec. 4.3, Extensions)
+# ------------------------------------------------------------------ shortest-path recovery (Sec. 5.4, Extensions)
 def brute_parent(g, rank, D, v, h, d):
     """Highest-ranked neighbour p of v with D[h, p] + w(p, v) = d, from the
     all-pairs distances (no labels involved)."""

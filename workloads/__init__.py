@@ -4,10 +4,10 @@ Input synthesis only: graphs, ranking functions and query pairs. Nothing here
 computes any part of the labeling method; the CPU oracle (``oracle``) and the
 GPU library (``paper_1907_00140_gb300``) both consume these arrays.
 
-The graph families stand in for the paper's datasets (Sec. 6.1, Table 2):
+The graph families stand in for the paper's datasets (Sec. 7.1, Table 2):
 R-MAT and Barabasi-Albert graphs with degree ranking for the scale-free
 networks, a 2-D grid with a sampled shortest-path-tree ranking for the road
-networks (betweenness approximated by sampling trees, Sec. 6.1).
+networks (betweenness approximated by sampling trees, Sec. 7.1).
 
 The generators are plain C (``chl_gen.c``), built with gcc on first use.
 """

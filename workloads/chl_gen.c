@@ -17,9 +17,9 @@
  * by neighbour id), w[2m] (uint32, >= 1, equal on both arcs of an edge).
  *
  * Ranks follow the paper's convention (Sec. 1): R is a permutation of [0,n),
- * a larger R is a more important vertex. Degree ranking (Sec. 6.1, scale-free
+ * a larger R is a more important vertex. Degree ranking (Sec. 7.1, scale-free
  * graphs) sorts by degree descending, then id ascending; the road-like ranking
- * (Sec. 6.1 approximates betweenness by sampling shortest-path trees) counts,
+ * (Sec. 7.1 approximates betweenness by sampling shortest-path trees) counts,
  * for each vertex, the tree paths through it over seeded sample roots.
  */
 #include <stdint.h>
