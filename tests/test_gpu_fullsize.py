@@ -1,11 +1,18 @@
-"""Full-size parity on sampled outputs.
+"""Full-size parity on sampled outputs and on whole-labeling digests.
 
 Trees are independent (Sec. 5.2), so the labels whose hub is a sampled root
 can be checked one tree at a time against the oracle; the whole labeling is
 checked through the cover property (query = Dijkstra distance, Sec. 1) on
-sampled pairs and through invariants that hold at any size. The GPU build
-runs in the default launch configuration, the one the benchmark times.
+sampled pairs and through invariants that hold at any size, and bit for bit
+against the SHA-256 of the oracle's whole labeling that
+tests/golden/make_digests.py stored (the oracle is too slow to rerun here).
+The GPU build runs in the default launch configuration, the one the benchmark
+times.
 """
+import importlib.util
+import json
+import os
+
 import numpy as np
 import pytest
 from scipy.sparse import csr_matrix
@@ -24,6 +31,23 @@ import paper_1907_00140_gb300 as chl  # noqa: E402
 from test_gpu_parity import DG, dev  # noqa: E402
 
 
+_GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+_spec = importlib.util.spec_from_file_location("make_digests", os.path.join(_GOLD, "make_digests.py"))
+_md = importlib.util.module_from_spec(_spec)
+_spec.loader.exec_module(_md)
+
+
+def check_digest(name, off, hub, dist):
+    """the whole labeling against the oracle's stored digest (when stored)"""
+    path = os.path.join(_GOLD, "label_digests.json")
+    gold = json.load(open(path)).get(name) if os.path.exists(path) else None
+    if gold is None:
+        return False
+    assert len(hub) == gold["labels"]
+    assert _md.digest(off, hub, dist) == gold["sha256"]
+    return True
+
+
 def sample_roots(n, seed):
     """rank positions: the 64 most important, 256 uniform, the 256 least important"""
     rng = np.random.default_rng(seed)
@@ -36,6 +60,7 @@ def check_workload(name, seed):
     n = g.n
     L = chl.build_labels(DG(g), dev(rank))
     off, hub, dist = L.to_numpy()
+    check_digest(name, off, hub, dist)
     order = np.empty(n, np.uint32)
     order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
     # 1) sampled trees, bit-exact
@@ -108,3 +133,15 @@ def test_rmat21_sampled_root_ranges():
         sel = hub == h
         vert = np.repeat(np.arange(n), np.diff(off.astype(np.int64)))[sel]
         assert np.array_equal(dist[sel], D[vert].astype(np.uint32))
+
+
+@pytest.mark.slow
+def test_rmat21_whole_labeling_digest():
+    """The whole default (hybrid) build of R-MAT scale 21, 224M labels, equals
+    the oracle's sequential Algorithm 1 labeling bit for bit (stored digest)."""
+    g, rank = W.load("rmat21")
+    L = chl.build_labels(DG(g), dev(rank))
+    off, hub, dist = L.to_numpy()
+    L.free()
+    if not check_digest("rmat21", off, hub, dist):
+        pytest.skip("no stored digest for rmat21")
