@@ -383,14 +383,23 @@ def _csr_args(g, rank):
     return csr, rkp, (k1, k2, k3, k4)
 
 
+def _build_opts(**kw) -> chl_build_opts:
+    """chl_build_opts with the given fields (floats for float fields, else ints)."""
+    o = chl_build_opts()
+    kinds = dict(chl_build_opts._fields_)
+    for k, v in kw.items():
+        if k not in kinds:
+            raise TypeError(f"unknown build option {k!r}")
+        setattr(o, k, float(v) if kinds[k] is C.c_float else int(v))
+    return o
+
+
 def tune(g, rank, stream: int | None = None, **fixed):
     """Measured choice of threads_per_tree, bucket_delta and window_buckets
     for this graph (chl_tune). Returns (build options for build_labels,
     tuning report)."""
     csr, rkp, keep = _csr_args(g, rank)
-    base = chl_build_opts()
-    for k, v in fixed.items():
-        setattr(base, k, int(v))
+    base = _build_opts(**fixed)
     best, rep = chl_tune(csr, rkp, base, _current_stream() if stream is None else stream)
     out = {k: getattr(best, k) for k in ("threads_per_tree", "bucket_delta", "window_buckets")}
     return out, rep.as_dict()
@@ -402,10 +411,7 @@ def build_labels(g, rank, stream: int | None = None, **opts) -> Labels:
     opts: fields of chl_build_opts (root_begin, root_end, threads_per_tree,
     bucket_delta, window_buckets, slots, mode)."""
     csr, rkp, keep = _csr_args(g, rank)
-    o = chl_build_opts()
-    kinds = dict(chl_build_opts._fields_)
-    for k, v in opts.items():
-        setattr(o, k, float(v) if kinds.get(k) is C.c_float else int(v))
+    o = _build_opts(**opts)
     h = chl_build(csr, rkp, o, _current_stream() if stream is None else stream)
     return Labels(h)
 

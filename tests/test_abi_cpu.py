@@ -87,3 +87,30 @@ def test_no_fallback_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(chl, "_lib", None)
     with pytest.raises(RuntimeError):
         chl.lib()
+
+
+def test_build_options_are_marshalled_by_field_type(monkeypatch):
+    """build_labels passes float options as floats and integer options as
+    integers, and rejects unknown names (no GPU: chl_build is intercepted)."""
+    import numpy as np
+    seen = {}
+
+    def fake_build(csr, rank_ptr, opts, stream):
+        seen["opts"] = opts
+        raise RuntimeError("intercepted")
+
+    monkeypatch.setattr(chl, "chl_build", fake_build)
+
+    class G:
+        n = 2
+        row_ptr = np.array([0, 1, 2], np.uint64)
+        col = np.array([1, 0], np.uint32)
+        w = np.array([3, 3], np.uint32)
+
+    rank = np.array([1, 0], np.uint32)
+    with pytest.raises(RuntimeError, match="intercepted"):
+        chl.build_labels(G, rank, psi_threshold=0.5, bucket_delta=7, slots=3)
+    o = seen["opts"]
+    assert abs(o.psi_threshold - 0.5) < 1e-7 and o.bucket_delta == 7 and o.slots == 3
+    with pytest.raises(TypeError):
+        chl.build_labels(G, rank, no_such_option=1)
