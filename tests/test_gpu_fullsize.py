@@ -37,12 +37,15 @@ _md = importlib.util.module_from_spec(_spec)
 _spec.loader.exec_module(_md)
 
 
-def check_digest(name, off, hub, dist):
-    """the whole labeling against the oracle's stored digest (when stored)"""
+def check_digest(name, g, rank, off, hub, dist):
+    """the whole labeling against the oracle's stored digest (when stored);
+    the inputs are checked first, so that a generator that differs on this
+    machine is told apart from a labeling that differs"""
     path = os.path.join(_GOLD, "label_digests.json")
     gold = json.load(open(path)).get(name) if os.path.exists(path) else None
     if gold is None:
         return False
+    assert _md.input_digest(g, rank) == gold["input_sha256"], f"{name}: inputs differ on this machine"
     assert len(hub) == gold["labels"]
     assert _md.digest(off, hub, dist) == gold["sha256"]
     return True
@@ -60,7 +63,7 @@ def check_workload(name, seed):
     n = g.n
     L = chl.build_labels(DG(g), dev(rank))
     off, hub, dist = L.to_numpy()
-    check_digest(name, off, hub, dist)
+    check_digest(name, g, rank, off, hub, dist)
     order = np.empty(n, np.uint32)
     order[n - 1 - rank.astype(np.int64)] = np.arange(n, dtype=np.uint32)
     # 1) sampled trees, bit-exact
@@ -143,5 +146,5 @@ def test_rmat21_whole_labeling_digest():
     L = chl.build_labels(DG(g), dev(rank))
     off, hub, dist = L.to_numpy()
     L.free()
-    if not check_digest("rmat21", off, hub, dist):
+    if not check_digest("rmat21", g, rank, off, hub, dist):
         pytest.skip("no stored digest for rmat21")
