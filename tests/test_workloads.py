@@ -71,3 +71,20 @@ def test_pairs_ranges():
     q = W.degree_pairs(g, 10000, 2)
     deg = g.degree()
     assert deg[q[:, 0]].mean() > 1.5 * deg.mean()  # degree-weighted endpoints
+
+
+@pytest.mark.parametrize("name", ["rmat18", "grid512"])
+def test_inputs_match_stored_digests(name):
+    """The generators still produce the inputs whose canonical labelings
+    tests/golden/label_digests.json holds (the full-size GPU tests compare
+    against those digests)."""
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_digests", os.path.join(here, "make_digests.py"))
+    md = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(md)
+    gold = json.load(open(os.path.join(here, "label_digests.json")))[name]
+    g, rank = W.load(name)
+    assert md.input_digest(g, rank) == gold["input_sha256"]
