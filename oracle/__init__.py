@@ -56,6 +56,8 @@ def _load():
             vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
             lib.orc_build.argtypes = [u32, vp, vp, vp, vp, i32, vp, u64, i32, u64, u32,
                                       C.POINTER(_Labels), vp]
+            lib.orc_build_phased.argtypes = [u32, vp, vp, vp, vp, vp, u32, i32,
+                                             C.POINTER(_Labels), vp]
             lib.orc_labels_free.argtypes = [C.POINTER(_Labels)]
             lib.orc_query.argtypes = [u32, vp, vp, vp, vp, vp, u64, vp, i32]
             lib.orc_count_redundant.argtypes = [u32, vp, vp, vp, vp]
@@ -123,6 +125,37 @@ def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
                        stats.ctypes.data if stats is not None else None)
     if rc != 0:
         raise RuntimeError(f"orc_build failed: {rc}")
+    try:
+        T = int(out.total)
+        off = np.ctypeslib.as_array(out.offsets, shape=(n + 1,)).copy()
+        hub = np.ctypeslib.as_array(out.hub, shape=(T,)).copy() if T else np.zeros(0, np.uint32)
+        dist = np.ctypeslib.as_array(out.dist, shape=(T,)).copy() if T else np.zeros(0, np.uint32)
+        L = Labels(off, hub, dist, bool(out.overflow))
+    finally:
+        lib.orc_labels_free(C.byref(out))
+    return (L, stats) if with_stats else L
+
+
+def build_labels_phased(g, rank, ends, threads: int = 1, with_stats: bool = False):
+    """Labels built in phases, the Hybrid of Sec. 5.2 as label-pruned phases:
+    phase k holds the roots of rank positions [ends[k-1], ends[k]) (ends
+    increasing, last = n); its trees run Algorithm 3 and also skip a popped
+    vertex whose distance query over every label of the earlier phases' roots
+    is at most its distance (hubs ranked above all of the phase's roots, the
+    condition of Sec. 5.3). The result must be the canonical labeling.
+    Returns Labels, or (Labels, stats[n,4] by rank position) when with_stats."""
+    lib = _load()
+    n = int(g.n)
+    row, col, w = _u(g.row_ptr, np.uint64), _u(g.col, np.uint32), _u(g.w, np.uint32)
+    rank = _u(rank, np.uint32)
+    ends = _u(np.asarray(ends), np.uint32)
+    stats = np.zeros((n, 4), np.uint64) if with_stats else None
+    out = _Labels()
+    rc = lib.orc_build_phased(n, row.ctypes.data, col.ctypes.data, w.ctypes.data, rank.ctypes.data,
+                              ends.ctypes.data, len(ends), int(threads), C.byref(out),
+                              stats.ctypes.data if stats is not None else None)
+    if rc != 0:
+        raise RuntimeError(f"orc_build_phased failed: {rc}")
     try:
         T = int(out.total)
         off = np.ctypeslib.as_array(out.offsets, shape=(n + 1,)).copy()

@@ -177,6 +177,7 @@ typedef struct {
     uint32_t *anc;      /* a[v] (Algorithm 3) / best rank holder (definition) */
     uint32_t *order;    /* settle order */
     uint32_t *touched;  /* vertices whose entries were modified */
+    uint64_t *lr;       /* the root's table labels by hub vertex, INF64 = none (phased method) */
     uint8_t *done;
     size_t ntouched;
     iheap q;
@@ -191,19 +192,21 @@ static int ws_init(workspace *w, uint32_t n, uint64_t tie_seed) {
     w->anc = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
     w->order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
     w->touched = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    w->lr = (uint64_t *)malloc((size_t)n * sizeof(uint64_t));
     w->done = (uint8_t *)calloc(n, 1);
     w->q.heap = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
     w->q.where = (uint32_t *)calloc(n, sizeof(uint32_t));
-    if (!w->dist || !w->anc || !w->order || !w->touched || !w->done || !w->q.heap || !w->q.where)
+    if (!w->dist || !w->anc || !w->order || !w->touched || !w->lr || !w->done || !w->q.heap ||
+        !w->q.where)
         return -1;
-    for (uint32_t v = 0; v < n; ++v) { w->dist[v] = INF64; w->anc[v] = v; }
+    for (uint32_t v = 0; v < n; ++v) { w->dist[v] = INF64; w->anc[v] = v; w->lr[v] = INF64; }
     w->q.key = w->dist;
     w->q.tie_seed = tie_seed;
     return 0;
 }
 
 static void ws_free(workspace *w) {
-    free(w->dist); free(w->anc); free(w->order); free(w->touched); free(w->done);
+    free(w->dist); free(w->anc); free(w->order); free(w->touched); free(w->lr); free(w->done);
     free(w->q.heap); free(w->q.where); free(w->out.buf);
 }
 
@@ -232,6 +235,13 @@ typedef struct {
        n-1-i (i = 0 most important) */
     const uint32_t *hc;
     uint32_t eta;
+    /* label table of earlier phases (orc_build_phased), or lt_off = NULL:
+       every label (hub, dist) of the roots of rank position below lt_hubs,
+       CSR by vertex */
+    const uint64_t *lt_off;
+    const uint32_t *lt_hub;
+    const uint32_t *lt_dist;
+    uint32_t lt_hubs;
 } graph;
 
 /* per root: vertices settled, arcs scanned, labels, and (Algorithm 1 only) label
@@ -308,6 +318,16 @@ static uint64_t hc_query(const graph *g, uint32_t h, uint32_t v) {
     return best;
 }
 
+/* distance query between the root (its table labels in ws->lr) and v over the
+   label table of earlier phases: some hub c with d(h,c) + d(c,v) <= dv */
+static int lt_query_prunes(const graph *g, const workspace *ws, uint32_t v, uint64_t dv) {
+    for (uint64_t i = g->lt_off[v]; i < g->lt_off[v + 1]; ++i) {
+        const uint64_t dh = ws->lr[g->lt_hub[i]];
+        if (dh != INF64 && dh + g->lt_dist[i] <= dv) return 1;
+    }
+    return 0;
+}
+
 static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st) {
     uint64_t *delta = ws->dist;
     uint32_t *a = ws->anc;          /* a[v] = v for untouched v (ws_reset invariant) */
@@ -315,6 +335,11 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
     uint64_t settled = 0, arcs = 0, nl = 0;
     /* pruning by the Common Label Table applies to trees of roots outside it */
     const int prune = g->hc && g->n - 1 - Rh >= g->eta;
+    /* pruning by the labels of earlier phases (phased method): the root's own
+       table labels go into lr for the queries */
+    const int lt = g->lt_off && g->n - 1 - Rh >= g->lt_hubs;
+    if (lt)
+        for (uint64_t i = g->lt_off[h]; i < g->lt_off[h + 1]; ++i) ws->lr[g->lt_hub[i]] = g->lt_dist[i];
     /* start: delta_h = 0, a[h] = h, h queued, cnt = 1 */
     ws_touch(ws, h);
     delta[h] = 0;
@@ -329,6 +354,7 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
         uint32_t nA = argmax_rank(g, v, a[v]);                 /* nA = argmax_{x in {v,a[v]}} R(x) */
         if (a[v] == h) cnt--;
         if (prune && hc_query(g, h, v) <= delta[v]) continue;  /* Sec. 5.3: pruned */
+        if (lt && lt_query_prunes(g, ws, v, delta[v])) continue;  /* pruned by earlier phases */
         if (g->rank[nA] <= Rh) {                               /* R[nA] > R[h]: no label */
             if (emit(ws, v, h, delta[v])) return;              /* L_v = L_v U {(h, delta_v)} */
             nl++;
@@ -354,6 +380,8 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
             }
         }
     }
+    if (lt)
+        for (uint64_t i = g->lt_off[h]; i < g->lt_off[h + 1]; ++i) ws->lr[g->lt_hub[i]] = INF64;
     if (st) { st->settled = settled; st->arcs = arcs; st->labels = nl; }
 }
 
@@ -641,6 +669,71 @@ int orc_build(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const ui
     }
     out->overflow = ovf;
     free(own_roots);
+    if (rc) orc_labels_free(out);
+    return rc;
+}
+
+/*
+ * Labels built in phases: the Hybrid of Sec. 5.2 in the form the library runs
+ * it (reading R15 of the design notes: label-pruned phases instead of GLL
+ * supersteps and cleaning). Phase k holds the roots of rank positions
+ * [ends[k-1], ends[k]) (ends[-1] = 0, ends[nphases-1] = n). Its trees run
+ * Algorithm 3 and also skip a popped vertex (no label, no relaxation) whose
+ * distance query over every label of the earlier phases' roots is at most
+ * its distance. Those roots are all hubs ranked above the phase's roots, the
+ * condition Sec. 5.3 states for pruning without redundant labels, so the
+ * result is the canonical labeling whatever the phases.
+ * stats (optional, [n] by rank position). Returns as orc_build.
+ */
+int orc_build_phased(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const uint32_t *w,
+                     const uint32_t *rank, const uint32_t *ends, uint32_t nphases, int threads,
+                     orc_labels *out, root_stats *stats) {
+    memset(out, 0, sizeof(*out));
+    if (n == 0 || nphases == 0 || ends[nphases - 1] != n) return -3;
+    for (uint32_t k = 0; k < nphases; ++k)
+        if (ends[k] == 0 || (k && ends[k] <= ends[k - 1])) return -3;
+    if (threads < 1) threads = 1;
+    graph g = { n, row_ptr, col, w, rank, NULL, 0 };
+    uint32_t *order = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+    uint64_t *off = (uint64_t *)calloc((size_t)n + 1, sizeof(uint64_t));
+    uint64_t *fill = (uint64_t *)calloc((size_t)n, sizeof(uint64_t));
+    tbuf *parts = (tbuf *)calloc((size_t)threads, sizeof(tbuf));
+    tbuf all = { 0 };
+    uint32_t *thub = NULL, *tdist = NULL;
+    int rc = 0, ovf = 0;
+    if (!order || !off || !fill || !parts) rc = -1;
+    if (!rc)
+        for (uint32_t v = 0; v < n; ++v) order[n - 1 - rank[v]] = v;
+    for (uint32_t k = 0; k < nphases && !rc; ++k) {
+        const uint32_t pb = k ? ends[k - 1] : 0, pe = ends[k];
+        if (k) {
+            /* every label so far, as CSR by vertex */
+            free(thub); free(tdist);
+            thub = (uint32_t *)malloc(all.len * sizeof(uint32_t) + 4);
+            tdist = (uint32_t *)malloc(all.len * sizeof(uint32_t) + 4);
+            if (!thub || !tdist) { rc = -1; break; }
+            memset(off, 0, ((size_t)n + 1) * sizeof(uint64_t));
+            for (size_t i = 0; i < all.len; ++i) off[all.buf[i].v + 1]++;
+            for (uint32_t v = 0; v < n; ++v) { off[v + 1] += off[v]; fill[v] = off[v]; }
+            for (size_t i = 0; i < all.len; ++i) {
+                const uint64_t at = fill[all.buf[i].v]++;
+                thub[at] = all.buf[i].hub;
+                tdist[at] = all.buf[i].dist;
+            }
+            g.lt_off = off; g.lt_hub = thub; g.lt_dist = tdist; g.lt_hubs = pb;
+        }
+        rc = run_trees(&g, ORC_PLANT, order + pb, pe - pb, threads, 0, stats ? stats + pb : NULL,
+                       parts, &ovf);
+        for (int t = 0; t < threads; ++t) {
+            for (size_t i = 0; i < parts[t].len && !rc; ++i)
+                if (tpush(&all, parts[t].buf[i].v, parts[t].buf[i].hub, parts[t].buf[i].dist)) rc = -1;
+            free(parts[t].buf);
+            memset(&parts[t], 0, sizeof(tbuf));
+        }
+    }
+    if (!rc) rc = assemble(&g, &all, 1, out);
+    out->overflow = ovf;
+    free(parts); free(all.buf); free(order); free(off); free(fill); free(thub); free(tdist);
     if (rc) orc_labels_free(out);
     return rc;
 }

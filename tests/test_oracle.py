@@ -380,6 +380,54 @@ def test_overflow_flag():
     assert not O.build_labels(from_edges(3, [(0, 1, 5), (1, 2, 5)]), rank[:3] - 1, "plant").overflow
 
 
+# ------------------------------------------------------------------ phased labeling (Hybrid, Sec. 5.2/5.3)
+def phase_schedules(n):
+    """phase ends by rank position: one phase (Algorithm 3), the top root
+    alone first, every root its own phase, and irregular splits"""
+    out = [[n], [1, n], list(range(1, n + 1))]
+    out.append(sorted({min(n, x) for x in (2, 3, 5, 8, 13, n)}))
+    out.append(sorted({max(1, n // 3), max(1, 2 * n // 3), n}))
+    return [list(e) for e in {tuple(e) for e in out}]
+
+
+@pytest.mark.parametrize("name,g,rank", tiny_cases(), ids=[c[0] for c in tiny_cases()])
+def test_phased_brute_force(name, g, rank):
+    """Pruning each phase's trees by every label of the earlier phases (a
+    rank-closed hub set) gives the canonical labeling for every schedule."""
+    want = brute_chl(g, rank)
+    for ends in phase_schedules(g.n):
+        assert as_dict(O.build_labels_phased(g, rank, ends)) == want, ends
+
+
+@pytest.mark.parametrize("which", ["ba2k", "grid24", "rmat10"])
+def test_phased_agrees_and_prunes(which):
+    """Equal to Algorithm 3 on larger graphs under seeded random schedules;
+    with every root its own phase the trees relax exactly the arcs sequential
+    Algorithm 1 relaxes (the same pruning, query for query), and any split
+    relaxes fewer arcs than the single phase."""
+    if which == "ba2k":
+        g, rank = W.load("ba2k")
+    elif which == "grid24":
+        g = W.grid(24, 60, seed=24)
+        rank = W.spt_count_rank(g, 16, seed=24)
+    else:
+        g = W.rmat(10, 8, seed=10, wlo=1, whi=50)
+        rank = W.degree_rank(g)
+    ref = O.build_labels(g, rank, "plant")
+    _, st1 = O.build_labels_phased(g, rank, [g.n], with_stats=True)
+    rng = np.random.default_rng(5)
+    for _ in range(3):
+        k = int(rng.integers(2, 12))
+        ends = sorted(set(rng.integers(1, g.n, size=k).tolist()) | {g.n})
+        L, st = O.build_labels_phased(g, rank, ends, threads=4, with_stats=True)
+        assert np.array_equal(L.offsets, ref.offsets) and np.array_equal(L.hub, ref.hub)
+        assert np.array_equal(L.dist, ref.dist)
+        assert st[:, 1].sum() < st1[:, 1].sum()
+    _, st_each = O.build_labels_phased(g, rank, np.arange(1, g.n + 1), with_stats=True)
+    _, st_pll = O.build_labels(g, rank, "pll", with_stats=True)
+    assert st_each[:, 1].sum() == st_pll[:, 1].sum()
+
+
 # ------------------------------------------------------------------ Common Label Table (Sec. 5.3)
 @pytest.mark.parametrize("name,g,rank", tiny_cases(), ids=[c[0] for c in tiny_cases()])
 @pytest.mark.parametrize("eta", [1, 2, 5])
