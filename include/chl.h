@@ -129,9 +129,7 @@ typedef struct chl_labels chl_labels;
  *                          generates, the later phases prune with the labels of
  *                          the earlier ones. 0 = 16, and the switch also fires
  *                          once the Common Label Table pruned at least 10% of
- *                          a phase's expansions, or right after the first
- *                          phase when it left fewer than 4 labels per vertex
- *                          for each arc per vertex; a value set here uses Psi
+ *                          a phase's expansions; a value set here uses Psi
  *                          alone (the paper's 16-node runs use 100 on
  *                          scale-free and 500 on road networks, where the
  *                          switch also costs communication). Not negative.

@@ -204,11 +204,6 @@ constexpr double PSI_TH = 16.0;
 // above which they do: where the top 16 hubs already cut that much, the labels
 // of every earlier hub cut far more and the per-vertex query pays
 constexpr double CLT_PRUNE_TH = 0.10;
-// ... or, after the first phase (which has no table to measure pruning by),
-// labels per vertex below this many arcs per vertex: a table query reads at
-// most a vertex's labels (8 B each), while each expansion it saves relaxes
-// the vertex's arcs (16 B each) and the subtree behind them
-constexpr double LABELS_PER_ARC_TH = 4.0;
 
 void free_csr(LabelCSR &c, cudaStream_t s) {
     if (c.offsets) cudaFreeAsync(c.offsets, s);
@@ -660,17 +655,13 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         }
     }
     // The switch of Sec. 5.2: label pruning starts once a phase's trees explore
-    // many vertices per label (Psi = expansions / labels above psi_th), once
-    // the Common Label Table pruned a large share of their expansions, or right
-    // after the first phase when its labels per vertex are few against the arcs
-    // per vertex; before that, the per-vertex table query would cost more than
-    // it saves.
+    // many vertices per label (Psi = expansions / labels above psi_th), or once
+    // the Common Label Table pruned a large share of their expansions; before
+    // that, the per-vertex table query would cost more than it saves.
     if (hybrid && !use_lt && T > T0) {
         const double psi = double(agg[0] - exp0) / double(T - T0);
         const double cut = agg[0] > exp0 ? double(agg[6] - pr0) / double(agg[0] - exp0) : 0.0;
-        const bool cheap_queries = ph == 0 && double(T) < LABELS_PER_ARC_TH * double(rg.m2);
-        if (psi > psi_th || (o.psi_threshold == 0.0f && P.eta && (cut >= CLT_PRUNE_TH || cheap_queries)))
-            use_lt = true;
+        if (psi > psi_th || (P.eta && cut >= CLT_PRUNE_TH && o.psi_threshold == 0.0f)) use_lt = true;
         // far down the ranking and still cheap trees: the rest is one phase
         else if (pe >= std::max<uint64_t>(uint64_t(P.slots) * 8, 8192) && psi < psi_th / 2)
             hybrid_off = true;
