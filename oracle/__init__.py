@@ -105,8 +105,8 @@ def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
     in `roots` are produced (each tree is independent, Sec. 5.2).
     tie_seed != 0 randomises the pop order of equal-distance vertices.
     Returns Labels, or (Labels, stats[k,4] = settled, arcs scanned, labels per
-    root, label entries read by the distance queries (Algorithm 1 only)) when
-    with_stats.
+    root, label entries read by the distance queries (Algorithm 1 only; the
+    phased method also counts them)) when with_stats.
     """
     lib = _load()
     n = int(g.n)

@@ -244,8 +244,8 @@ typedef struct {
     uint32_t lt_hubs;
 } graph;
 
-/* per root: vertices settled, arcs scanned, labels, and (Algorithm 1 only) label
-   entries read by its distance queries */
+/* per root: vertices settled, arcs scanned, labels, and label entries read by
+   its distance queries (Algorithm 1 and the phased method) */
 typedef struct { uint64_t settled, arcs, labels, qentries; } root_stats;
 
 static int emit(workspace *ws, uint32_t v, uint32_t h, uint64_t d) {
@@ -319,9 +319,12 @@ static uint64_t hc_query(const graph *g, uint32_t h, uint32_t v) {
 }
 
 /* distance query between the root (its table labels in ws->lr) and v over the
-   label table of earlier phases: some hub c with d(h,c) + d(c,v) <= dv */
-static int lt_query_prunes(const graph *g, const workspace *ws, uint32_t v, uint64_t dv) {
+   label table of earlier phases: some hub c with d(h,c) + d(c,v) <= dv; *qe
+   counts the entries read */
+static int lt_query_prunes(const graph *g, const workspace *ws, uint32_t v, uint64_t dv,
+                           uint64_t *qe) {
     for (uint64_t i = g->lt_off[v]; i < g->lt_off[v + 1]; ++i) {
+        ++*qe;
         const uint64_t dh = ws->lr[g->lt_hub[i]];
         if (dh != INF64 && dh + g->lt_dist[i] <= dv) return 1;
     }
@@ -332,7 +335,7 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
     uint64_t *delta = ws->dist;
     uint32_t *a = ws->anc;          /* a[v] = v for untouched v (ws_reset invariant) */
     const uint32_t Rh = g->rank[h];
-    uint64_t settled = 0, arcs = 0, nl = 0;
+    uint64_t settled = 0, arcs = 0, nl = 0, qe = 0;
     /* pruning by the Common Label Table applies to trees of roots outside it */
     const int prune = g->hc && g->n - 1 - Rh >= g->eta;
     /* pruning by the labels of earlier phases (phased method): the root's own
@@ -354,7 +357,7 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
         uint32_t nA = argmax_rank(g, v, a[v]);                 /* nA = argmax_{x in {v,a[v]}} R(x) */
         if (a[v] == h) cnt--;
         if (prune && hc_query(g, h, v) <= delta[v]) continue;  /* Sec. 5.3: pruned */
-        if (lt && lt_query_prunes(g, ws, v, delta[v])) continue;  /* pruned by earlier phases */
+        if (lt && lt_query_prunes(g, ws, v, delta[v], &qe)) continue;  /* pruned by earlier phases */
         if (g->rank[nA] <= Rh) {                               /* R[nA] > R[h]: no label */
             if (emit(ws, v, h, delta[v])) return;              /* L_v = L_v U {(h, delta_v)} */
             nl++;
@@ -380,9 +383,11 @@ static void tree_plant(const graph *g, workspace *ws, uint32_t h, root_stats *st
             }
         }
     }
-    if (lt)
+    if (lt) {
+        qe += g->lt_off[h + 1] - g->lt_off[h];  /* the root's own list, read once */
         for (uint64_t i = g->lt_off[h]; i < g->lt_off[h + 1]; ++i) ws->lr[g->lt_hub[i]] = INF64;
-    if (st) { st->settled = settled; st->arcs = arcs; st->labels = nl; }
+    }
+    if (st) { st->settled = settled; st->arcs = arcs; st->labels = nl; st->qentries = qe; }
 }
 
 /* ------------------------------------------------------------------ Algorithm 1 (sequential PLL) */
