@@ -355,7 +355,8 @@ def main():
 
     # search parameters measured once for this graph (chl_tune), outside the timed region
     if args.opts:
-        opts = {k: int(v) for k, v in (kv.split("=") for kv in args.opts.split(","))}
+        opts = {k: (float(v) if any(c in v for c in ".eE") else int(v))
+                for k, v in (kv.split("=") for kv in args.opts.split(","))}
         tune_rep = {"trials": 0, "sample_roots": 0}
     else:
         opts, tune_rep = chl.tune(DG, R)

@@ -77,6 +77,7 @@ struct Params {
     int tpt_lt;          // threads per tree in the label-pruned phases
     int slots_lt;        // ... and their slots
     uint32_t fin_words_lt;
+    uint32_t stage_lt;   // staging bytes of the queried lists in those phases
     uint32_t delta;
     uint32_t delta_lt;  // bucket width of the phases that prune with the label table
     uint32_t nwin;
@@ -112,7 +113,10 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     const bool narrow_fits = double(g.w_max) * double(g.n) <= double(0x7FFFFFFE);
     // parents ride in the low 31 bits of an 8-byte key
     p.kb = (narrow_fits && !(o.flags & (CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS))) ? 4 : 8;
-    p.fin_words = plant_fin_words(p.tpt, g.n);
+    {
+        uint32_t st0 = 0;
+        plant_smem_split(p.tpt, g.n, false, &p.fin_words, &st0);
+    }
     {
         const int want = o.common_hubs == 0 ? 16 : o.common_hubs;  // the paper's eta = 16
         p.eta = want < 0 ? 0u : (uint32_t(want) < g.n ? uint32_t(want) : g.n);
@@ -120,10 +124,10 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     p.w_min = g.w_min ? g.w_min : 1;
     p.n = g.n;
     p.tpt_lt = o.pruned_threads_per_tree ? o.pruned_threads_per_tree : p.tpt;
-    p.fin_words_lt = plant_fin_words(p.tpt_lt, g.n);
-    int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words);
+    plant_smem_split(p.tpt_lt, g.n, true, &p.fin_words_lt, &p.stage_lt);
+    int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words, 0);
     if (per_sm < 1) per_sm = 1;
-    int per_sm_lt = plant_max_slots_per_sm(p.tpt_lt, p.fin_words_lt);
+    int per_sm_lt = plant_max_slots_per_sm(p.tpt_lt, p.fin_words_lt, p.stage_lt);
     if (per_sm_lt < 1) per_sm_lt = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
     long long slots_lt = o.slots > 0 ? o.slots : (long long)sms * per_sm_lt;
@@ -204,14 +208,6 @@ constexpr double PSI_TH = 16.0;
 // above which they do: where the top 16 hubs already cut that much, the labels
 // of every earlier hub cut far more and the per-vertex query pays
 constexpr double CLT_PRUNE_TH = 0.10;
-
-void free_csr(LabelCSR &c, cudaStream_t s) {
-    if (c.offsets) cudaFreeAsync(c.offsets, s);
-    if (c.hub) cudaFreeAsync(c.hub, s);
-    if (c.hubpos) cudaFreeAsync(c.hubpos, s);
-    if (c.dist) cudaFreeAsync(c.dist, s);
-    c = LabelCSR{};
-}
 
 // Common Label Table (Sec. 5.3): all labels of the `hubs` most important
 // vertices, as a dense [n][stride] table of distances (all ones = no label).
@@ -391,7 +387,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     unsigned long long agg[7] = {0, 0, 0, 0, 0, 0, 0};
     std::vector<uint32_t> pending;  // roots still to build (after a full buffer)
     std::vector<std::pair<uint32_t, uint32_t>> phases;
-    LabelCSR lt;  // labels of earlier phases (hybrid)
+    LabelTable lt;  // labels of earlier phases (hybrid)
     bool use_lt = false, hybrid = false, hybrid_off = false;
     uint64_t lt_phases = 0;
     uint64_t lt_records = 0;  // output records the label table holds
@@ -456,7 +452,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             P.slots = 1;
             P.slots_lt = 1;
             P.tpt_lt = P.tpt;
-            P.fin_words_lt = P.fin_words;
+            plant_smem_split(P.tpt_lt, rg.n, true, &P.fin_words_lt, &P.stage_lt);
         }
     }
 
@@ -505,7 +501,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
                             : std::make_pair(rb, re));
     for (size_t ph = 0; ph < phases.size(); ++ph) {
     const uint32_t pb = phases[ph].first, pe = phases[ph].second;
-    const uint64_t exp0 = agg[0], T0 = T, arc0 = agg[1], pr0 = agg[6];
+    const uint64_t exp0 = agg[0], T0 = T, arc0 = agg[1], pr0 = agg[6], rd0 = agg[4], bk0 = agg[5];
     const int ph_lt = lt.offsets ? 1 : 0;
     if (trace) t_ph = now_ms();
     if (lt.offsets) ++lt_phases;
@@ -521,14 +517,14 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         table.fill(tl);
         if (lt.offsets) {
             tl.lt_off = lt.offsets;
-            tl.lt_hp = lt.hubpos;
-            tl.lt_d = lt.dist;
+            tl.lt_e = lt.e;
             tl.lt_hubs = pb;
             tl.lt_root = (uint32_t *)b_ltroot.p;
             tl.lt_hash_max = (o.flags & CHL_FLAG_DENSE_ROOT_LABELS) ? 0 : 0xFFFFFFFFu;
             set_delta(tl, P.delta_lt);
             tl.fin_words = P.fin_words_lt;
             tl.fin_bits = P.fin_words_lt * 32 < n ? P.fin_words_lt * 32 : n;
+            tl.stage_bytes = P.stage_lt;
         }
         // the batched form first writes the labels of the phase's trivial
         // roots and lists the others: room for one record per root
@@ -613,6 +609,10 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             st = set_error(CHL_ETIMEOUT, "a tree exceeded its round limit");
             goto done;
         }
+        if (hc.flags[0] == ERR_WAIT_LIMIT) {
+            st = set_error(CHL_ETIMEOUT, "a tree's staging copies did not complete in time");
+            goto done;
+        }
         T = records_kept(hc);
         if (!hc.flags[1]) break;  // every root of this attempt fit
         // collect roots that failed or were never claimed, grow the buffer, go again
@@ -694,26 +694,30 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             CUDA_TRY(cudaMallocAsync(&b_ltroot.p, size_t(P.slots_lt) * n * 4, s));
             CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, size_t(P.slots_lt) * n * 4, s));
         }
+        // hubs of the Common Label Table are left out: every tree of a label-
+        // pruned phase also queries that table, which holds all their labels
+        const uint32_t min_hub = table.buf.p ? table.hubs : 0;
         if (!lt.offsets)
             CUDA_TRY(assemble_table(n, T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
-                                    (const uint32_t *)b_od.p, rg.pos_of, lt, s, &launches));
+                                    (const uint32_t *)b_od.p, rg.pos_of, min_hub, lt, s, &launches));
         else
             CUDA_TRY(grow_table(n, lt, lt_records, T, (const uint32_t *)b_ov.p,
-                                (const uint32_t *)b_oh.p, (const uint32_t *)b_od.p, rg.pos_of, s,
-                                &launches));
+                                (const uint32_t *)b_oh.p, (const uint32_t *)b_od.p, rg.pos_of, min_hub,
+                                s, &launches));
         lt_records = T;
     }
     if (trace) {
         CUDA_TRY(cudaStreamSynchronize(s));
         std::fprintf(stderr,
                      "chl phase %zu roots [%u, %u) table %d trees %.3f ms assemble %.3f ms "
-                     "expanded %llu arcs %llu labels %llu\n",
+                     "expanded %llu arcs %llu labels %llu rounds %llu buckets %llu pruned %llu\n",
                      ph, pb, pe, ph_lt, t_tree, now_ms() - t_ph - t_tree,
                      (unsigned long long)(agg[0] - exp0), (unsigned long long)(agg[1] - arc0),
-                     (unsigned long long)(T - T0));
+                     (unsigned long long)(T - T0), (unsigned long long)(agg[4] - rd0),
+                     (unsigned long long)(agg[5] - bk0), (unsigned long long)(agg[6] - pr0));
     }
     }  // phases
-    free_csr(lt, s);
+    free_table(lt, s);
     CUDA_TRY(cudaEventRecord(ev[2], s));
     // slot state and table are no longer needed: release them before assembly
     slot.release();
@@ -772,7 +776,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     csr = LabelCSR{};
     *out = L;
 done:
-    free_csr(lt, s);
+    free_table(lt, s);
     if (csr_parent) cudaFreeAsync(csr_parent, s);
     if (csr.offsets) cudaFreeAsync(csr.offsets, s);
     if (csr.hub) cudaFreeAsync(csr.hub, s);
@@ -1219,7 +1223,7 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     if (!o.threads_per_tree && !o.root_begin && !o.root_end && !(o.flags & CHL_FLAG_NO_HYBRID)) {
         double best_build = -1.0;
         int best_tpt = bestP.tpt;
-        for (int t : {512, 1024}) {
+        for (int t : {256, 512, 1024}) {
             chl_build_opts q = *best;
             q.threads_per_tree = t;
             chl_labels *Lt = nullptr;

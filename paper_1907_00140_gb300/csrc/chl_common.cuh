@@ -62,13 +62,14 @@ struct TreeLaunch {
     uint32_t hc_hubs;
     uint32_t hc_stride;
     // label table of the earlier phases of a hybrid build, or lt_off = null:
-    // all labels of the hubs of rank position < lt_hubs, CSR by vertex rank
-    // position (offsets [n+1]) of hub positions lt_hp and distances lt_d, each
-    // vertex's entries in no particular order
+    // all labels of the hubs of rank position in [hc_hubs, lt_hubs) (the
+    // Common Label Table answers for the hubs below hc_hubs), CSR by vertex
+    // rank position (offsets [n+1]) of {hub position, distance} entries, each
+    // vertex's entries in no particular order (see LabelTable)
     const uint64_t *lt_off;
-    const uint32_t *lt_hp;
-    const uint32_t *lt_d;
+    const uint2 *lt_e;     // {hub position, distance}
     uint32_t lt_hubs;
+    uint32_t stage_bytes;  // shared-memory staging of the queried lists (multiple of 16)
     // per slot [n], all ones when idle, or null: the root's table labels by
     // hub position, for roots with more of them than the shared-memory hash holds
     uint32_t *lt_root;
@@ -95,19 +96,26 @@ struct TreeLaunch {
     unsigned long long *stats; // [0] expanded [1] arcs [2] trivial [3] trees [4] rounds [5] buckets [6] pruned
 };
 
-enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2 };
+enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2, ERR_WAIT_LIMIT = 3 };
 
 // launches (defined in chl_tree.cu)
 cudaError_t launch_plant_trees(const TreeLaunch &p, int threads_per_tree, int slots,
                                cudaStream_t s);
-int plant_max_slots_per_sm(int threads_per_tree, uint32_t fin_words);
+// CTAs per SM of a launch with that bitmap and staging area
+int plant_max_slots_per_sm(int threads_per_tree, uint32_t fin_words, uint32_t stage_bytes);
 // roots [begin, begin + count): the label of every trivial root is written to
 // the output (p.out_*, p.out_count; the caller guarantees room for count
 // records), the other roots are appended to list (*list_n of them)
 cudaError_t launch_split_trivial(const TreeLaunch &p, uint32_t begin, uint32_t count, uint32_t *list,
                                  unsigned int *list_n, cudaStream_t s);
-// settled-filter words for n vertices that keep the CTAs per SM of fin_words = 0
-uint32_t plant_fin_words(int threads_per_tree, uint32_t n);
+// dynamic shared memory per CTA (bytes) that keeps the CTAs per SM of a launch
+// without any
+uint32_t plant_dyn_budget(int threads_per_tree);
+// that budget split between the settled-filter bitmap (at most one bit per
+// vertex) and, for phases that prune with the label table (staged), the
+// staging area of the queried lists
+void plant_smem_split(int threads_per_tree, uint32_t n, bool staged, uint32_t *fin_words,
+                      uint32_t *stage_bytes);
 // Common Label Table entries from label records (those of hub positions < hubs)
 cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
                             unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
@@ -126,18 +134,26 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
                             const uint32_t *in_d, const uint32_t *vert_at, LabelCSR &out,
                             int *too_long, cudaStream_t s, int *launches);
 
-// the same records as a table for distance queries: offsets by rank position
-// (pos_of maps caller ids to positions), hubpos and dist only, each vertex's
-// entries in no particular order (hub = null)
+// The same records as a table for the distance queries of label pruning:
+// offsets [n+1] by rank position (pos_of maps caller ids to positions), entries
+// {hub position, distance} interleaved, each vertex's entries in no particular
+// order. Records of hubs below min_hub are left out. The entry array has two
+// spare entries past the last (all ones), so a read widened to 16-byte
+// boundaries stays inside it.
+struct LabelTable {
+    uint64_t *offsets = nullptr;
+    uint2 *e = nullptr;
+};
 cudaError_t assemble_table(uint32_t n, uint64_t T, const uint32_t *in_v, const uint32_t *in_h,
-                           const uint32_t *in_d, const uint32_t *pos_of, LabelCSR &out,
-                           cudaStream_t s, int *launches);
+                           const uint32_t *in_d, const uint32_t *pos_of, uint32_t min_hub,
+                           LabelTable &out, cudaStream_t s, int *launches);
 
 // a table from assemble_table of records [0, T0) grown by records [T0, T):
 // each vertex keeps its old entries first (lt is replaced; freed on success)
-cudaError_t grow_table(uint32_t n, LabelCSR &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
+cudaError_t grow_table(uint32_t n, LabelTable &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
                        const uint32_t *in_h, const uint32_t *in_d, const uint32_t *pos_of,
-                       cudaStream_t s, int *launches);
+                       uint32_t min_hub, cudaStream_t s, int *launches);
+void free_table(LabelTable &t, cudaStream_t s);
 
 // parents of label records into the slots of the assembled CSR (parent[T])
 cudaError_t place_parents(uint64_t T, const uint32_t *in_v, const uint32_t *in_h, const uint32_t *in_p,

@@ -28,23 +28,24 @@ __global__ void count_kernel(uint64_t T, const uint32_t *v, uint64_t *cnt) {
 }
 
 // unsorted table by rank position: (hubpos, dist) straight into each
-// vertex's segment
-__global__ void count_table_kernel(uint64_t T, const uint32_t *v, const uint32_t *pos_of,
-                                   uint64_t *cnt) {
+// vertex's segment; records of hubs below min_hub are left out (the dense
+// Common Label Table answers for those hubs)
+__global__ void count_table_kernel(uint64_t T, const uint32_t *v, const uint32_t *h,
+                                   const uint32_t *pos_of, uint32_t min_hub, uint64_t *cnt) {
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
          i += uint64_t(gridDim.x) * blockDim.x)
-        atomicAdd((unsigned long long *)&cnt[pos_of[v[i]]], 1ull);
+        if (h[i] >= min_hub) atomicAdd((unsigned long long *)&cnt[pos_of[v[i]]], 1ull);
 }
 
 __global__ void scatter_table_kernel(uint64_t T, const uint32_t *v, const uint32_t *h,
-                                     const uint32_t *d, const uint32_t *pos_of, const uint64_t *off,
-                                     uint64_t *fill, uint32_t *hubpos, uint32_t *dist) {
+                                     const uint32_t *d, const uint32_t *pos_of, uint32_t min_hub,
+                                     const uint64_t *off, uint64_t *fill, uint2 *e) {
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
          i += uint64_t(gridDim.x) * blockDim.x) {
+        if (h[i] < min_hub) continue;
         const uint32_t x = pos_of[v[i]];
         const uint64_t k = off[x] + atomicAdd((unsigned long long *)&fill[x], 1ull);
-        hubpos[k] = h[i];
-        dist[k] = d[i];
+        e[k] = make_uint2(h[i], d[i]);
     }
 }
 
@@ -56,32 +57,28 @@ __global__ void grown_count_kernel(uint32_t n, const uint64_t *old_off, uint64_t
 }
 
 // one warp per vertex: its old entries to the front of its new segment
-__global__ void copy_segments_kernel(uint32_t n, const uint64_t *old_off, const uint32_t *old_hp,
-                                     const uint32_t *old_d, const uint64_t *new_off, uint32_t *hp,
-                                     uint32_t *d) {
+__global__ void copy_segments_kernel(uint32_t n, const uint64_t *old_off, const uint2 *old_e,
+                                     const uint64_t *new_off, uint2 *e) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
     for (uint64_t v = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
         const uint64_t a = old_off[v], len = old_off[v + 1] - a, o = new_off[v];
-        for (uint64_t i = lane; i < len; i += 32) {
-            hp[o + i] = old_hp[a + i];
-            d[o + i] = old_d[a + i];
-        }
+        for (uint64_t i = lane; i < len; i += 32) e[o + i] = old_e[a + i];
     }
 }
 
 // new records after each vertex's old entries
 __global__ void scatter_new_kernel(uint64_t T0, uint64_t T, const uint32_t *v, const uint32_t *h,
-                                   const uint32_t *d, const uint32_t *pos_of, const uint64_t *old_off,
-                                   const uint64_t *off, uint64_t *fill, uint32_t *hubpos,
-                                   uint32_t *dist) {
+                                   const uint32_t *d, const uint32_t *pos_of, uint32_t min_hub,
+                                   const uint64_t *old_off, const uint64_t *off, uint64_t *fill,
+                                   uint2 *e) {
     for (uint64_t i = T0 + uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
          i += uint64_t(gridDim.x) * blockDim.x) {
+        if (h[i] < min_hub) continue;
         const uint32_t x = pos_of[v[i]];
         const uint64_t k = off[x] + (old_off[x + 1] - old_off[x]) +
                            atomicAdd((unsigned long long *)&fill[x], 1ull);
-        hubpos[k] = h[i];
-        dist[k] = d[i];
+        e[k] = make_uint2(h[i], d[i]);
     }
 }
 
@@ -269,68 +266,67 @@ done:
     return e;
 }
 
+// Entries are allocated with two spare ones past the last, so that a read
+// widened to 16-byte boundaries (two entries) stays inside the array.
 cudaError_t assemble_table(uint32_t n, uint64_t T, const uint32_t *in_v, const uint32_t *in_h,
-                           const uint32_t *in_d, const uint32_t *pos_of, LabelCSR &out,
-                           cudaStream_t s, int *launches) {
+                           const uint32_t *in_d, const uint32_t *pos_of, uint32_t min_hub,
+                           LabelTable &out, cudaStream_t s, int *launches) {
     cudaError_t e = cudaSuccess;
     uint64_t *cnt = nullptr;
-    out = LabelCSR{};
-    const size_t Tb = (T ? T : 1);
+    out = LabelTable{};
     CKE(cudaMallocAsync(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&out.hubpos, Tb * sizeof(uint32_t), s));
-    CKE(cudaMallocAsync(&out.dist, Tb * sizeof(uint32_t), s));
+    CKE(cudaMallocAsync(&out.e, (size_t(T) + 2) * sizeof(uint2), s));
+    CKE(cudaMemsetAsync(out.e, 0xFF, (size_t(T) + 2) * sizeof(uint2), s));
     CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
-    count_table_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, pos_of, cnt);
+    count_table_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, in_h, pos_of, min_hub, cnt);
     *launches += 1;
     CKE(cudaGetLastError());
     CKE(exclusive_scan_u64(cnt, out.offsets, uint64_t(n) + 1, s, launches));
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
-    scatter_table_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, in_h, in_d, pos_of, out.offsets,
-                                                          cnt, out.hubpos, out.dist);
+    scatter_table_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, in_h, in_d, pos_of, min_hub,
+                                                          out.offsets, cnt, out.e);
     *launches += 1;
     CKE(cudaGetLastError());
 done:
     if (cnt) cudaFreeAsync(cnt, s);
     if (e != cudaSuccess) {
         if (out.offsets) cudaFreeAsync(out.offsets, s);
-        if (out.hubpos) cudaFreeAsync(out.hubpos, s);
-        if (out.dist) cudaFreeAsync(out.dist, s);
-        out = LabelCSR{};
+        if (out.e) cudaFreeAsync(out.e, s);
+        out = LabelTable{};
     }
     return e;
 }
 
-cudaError_t grow_table(uint32_t n, LabelCSR &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
+cudaError_t grow_table(uint32_t n, LabelTable &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
                        const uint32_t *in_h, const uint32_t *in_d, const uint32_t *pos_of,
-                       cudaStream_t s, int *launches) {
+                       uint32_t min_hub, cudaStream_t s, int *launches) {
     cudaError_t e = cudaSuccess;
     uint64_t *cnt = nullptr;
-    LabelCSR out;
+    LabelTable out;
     const uint64_t dT = T - T0;
-    const size_t Tb = (T ? T : 1);
     CKE(cudaMallocAsync(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&out.hubpos, Tb * sizeof(uint32_t), s));
-    CKE(cudaMallocAsync(&out.dist, Tb * sizeof(uint32_t), s));
+    CKE(cudaMallocAsync(&out.e, (size_t(T) + 2) * sizeof(uint2), s));
+    CKE(cudaMemsetAsync(out.e, 0xFF, (size_t(T) + 2) * sizeof(uint2), s));
     CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
     if (dT) {
-        count_table_kernel<<<grid_for(dT, 256), 256, 0, s>>>(dT, in_v + T0, pos_of, cnt);
+        count_table_kernel<<<grid_for(dT, 256), 256, 0, s>>>(dT, in_v + T0, in_h + T0, pos_of, min_hub,
+                                                             cnt);
         *launches += 1;
     }
     grown_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, lt.offsets, cnt);
     *launches += 1;
     CKE(cudaGetLastError());
     CKE(exclusive_scan_u64(cnt, out.offsets, uint64_t(n) + 1, s, launches));
-    copy_segments_kernel<<<152 * 16, 256, 0, s>>>(n, lt.offsets, lt.hubpos, lt.dist, out.offsets,
-                                                  out.hubpos, out.dist);
+    copy_segments_kernel<<<grid_for(uint64_t(n) * 32, 256), 256, 0, s>>>(n, lt.offsets, lt.e,
+                                                                         out.offsets, out.e);
     *launches += 1;
     CKE(cudaGetLastError());
     if (dT) {
         CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
-        scatter_new_kernel<<<grid_for(dT, 256), 256, 0, s>>>(T0, T, in_v, in_h, in_d, pos_of,
-                                                             lt.offsets, out.offsets, cnt, out.hubpos,
-                                                             out.dist);
+        scatter_new_kernel<<<grid_for(dT, 256), 256, 0, s>>>(T0, T, in_v, in_h, in_d, pos_of, min_hub,
+                                                             lt.offsets, out.offsets, cnt, out.e);
         *launches += 1;
         CKE(cudaGetLastError());
     }
@@ -338,15 +334,19 @@ done:
     if (cnt) cudaFreeAsync(cnt, s);
     if (e != cudaSuccess) {
         if (out.offsets) cudaFreeAsync(out.offsets, s);
-        if (out.hubpos) cudaFreeAsync(out.hubpos, s);
-        if (out.dist) cudaFreeAsync(out.dist, s);
+        if (out.e) cudaFreeAsync(out.e, s);
         return e;
     }
     cudaFreeAsync(lt.offsets, s);
-    cudaFreeAsync(lt.hubpos, s);
-    cudaFreeAsync(lt.dist, s);
+    cudaFreeAsync(lt.e, s);
     lt = out;
     return e;
+}
+
+void free_table(LabelTable &t, cudaStream_t s) {
+    if (t.offsets) cudaFreeAsync(t.offsets, s);
+    if (t.e) cudaFreeAsync(t.e, s);
+    t = LabelTable{};
 }
 
 namespace {

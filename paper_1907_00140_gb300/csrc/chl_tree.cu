@@ -45,7 +45,9 @@
 // that prefix ends, and it and every later tree give up their labels whole
 // (no partial tree is kept); the host rebuilds those roots after growing the
 // buffer.
+#include <algorithm>
 #include <cstdio>
+#include <cstdlib>
 
 #include "chl_common.cuh"
 
@@ -60,7 +62,8 @@ constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t CLT_MAX = 64;  // largest Common Label Table (hubs)
 constexpr uint32_t LTH_SLOTS = 1024;  // hash of the root's labels in the label table
 constexpr uint32_t LTH_MAX = 512;     // most root labels the hash holds
-constexpr int QSTEPS = 4;             // label-table query: loads in flight per lane
+constexpr int QSTEPS = 4;             // label-table query from global memory: loads in flight per lane
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // polls of a staging barrier before it counts as hung
 
 // ------------------------------------------------------------------ keys
 // Vertices are numbered by rank position (pos 0 = most important), so in the
@@ -133,6 +136,9 @@ struct Shared {
     int lt_prune;          // ... and by the label table of earlier phases
     int lt_dense;          // the root's table labels are in p.lt_root, not the hash
     uint32_t qn;           // table queries queued by the current chunk
+    uint32_t stage_used;   // bytes of the staging area reserved by the current batch
+    uint32_t bn;           // queries staged in the current batch
+    unsigned long long mbar;  // barrier that counts the staging copies of a batch
     uint32_t hch[CLT_MAX]; // table row of the root: d(h, c) per table hub c
     // the root's labels in the label table, hashed by hub position (key + 1)
     uint32_t lth_key[LTH_SLOTS];
@@ -212,7 +218,54 @@ __device__ __forceinline__ void atomic_set_key(uint64_t *a, uint64_t v) {
 // key, and a probe of a marked target skips its key load. Bits are set when a
 // vertex is expanded and cleared per tree; a probe that misses a fresh bit
 // only does a load it could have saved.
-extern __shared__ uint32_t fin_bitmap[];
+extern __shared__ __align__(128) uint32_t fin_bitmap[];
+
+// The staging area of the label-table queries follows the bitmap in dynamic
+// shared memory, at the next multiple of 128 bytes.
+__device__ __forceinline__ uint32_t stage_offset(uint32_t fin_words) { return (fin_words * 4u + 127u) & ~127u; }
+
+// ---- shared-memory barrier and bulk copy (PTX mbarrier, cp.async.bulk)
+__device__ __forceinline__ uint32_t smem_addr(const void *ptr) {
+    return uint32_t(__cvta_generic_to_shared(ptr));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *m, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(m)), "r"(count) : "memory");
+    // make the initialised barrier visible to the copy engine's proxy
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long *m) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n\t}" ::"r"(
+                     smem_addr(m))
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *m, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.release.cta.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+            smem_addr(m)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *m, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(m)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// global -> shared copy by the copy engine; both addresses 16-byte aligned,
+// bytes a multiple of 16; completion counted on barrier m
+__device__ __forceinline__ void bulk_to_shared(void *dst, const void *src, uint32_t bytes,
+                                               unsigned long long *m) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(m))
+        : "memory");
+}
 
 // kv = make_key(dv, lv) of the expanded vertex: the candidate through arc
 // (u, w) is kv + 2w (the clean bit rides along in bit 0). With 4-byte keys
@@ -235,117 +288,6 @@ __device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot
     q.live = true;
 }
 
-// Commit of one warp step, called by all 32 lanes: the atomicMins of all
-// UNROLL probes are issued together (independent, so their round trips
-// overlap), then each lane classifies its improvements, and the appends to
-// the touched list, nxt and far take one shared atomic per warp and list, the
-// window buckets one per bucket, the live-pending count one per warp.
-template <typename K>
-__device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
-                                            uint32_t h, const Probe<K> (&q)[UNROLL]) {
-    using KS = typename K::T;
-    const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1;
-    KS old[UNROLL];
-    bool imp[UNROLL];
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        imp[k] = false;
-        old[k] = 0;
-        if (q[k].live && q[k].cand < q[k].seen) old[k] = atomic_min_key(&sl.key[q[k].u], q[k].cand);
-    }
-    bool any = false;
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        imp[k] = q[k].live && q[k].cand < q[k].seen && q[k].cand < old[k];
-        any |= imp[k];
-    }
-    if (!__any_sync(FULL, any)) return;
-    int dcnt = 0;
-    uint32_t cls[UNROLL];  // 0 none, 1 nxt (current bucket), 2 window bucket, 3 far, | 4 unreached
-    uint32_t sx[UNROLL];
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        cls[k] = 0;
-        sx[k] = NONE;
-        if (imp[k]) {
-            const uint32_t u = q[k].u;
-            const bool unreached = old[k] == key_inf<K>();
-            const uint32_t nb = bucket_of(p, key_dist<K>(q[k].cand));
-            const uint32_t ob = unreached ? NONE : bucket_of(p, key_dist<K>(old[k]));
-            const bool f_new = nb > S.bcur && is_live<K>(q[k].cand, u, h);
-            const bool f_old = !unreached && ob > S.bcur && is_live<K>(old[k], u, h);
-            dcnt += int(f_new) - int(f_old);
-            if (nb == S.bcur) {
-                if (atomicExch(&sl.rtag[u], S.rid) != S.rid) cls[k] = 1;
-            } else if (key_dist<K>(q[k].cand) < S.w_hi) {
-                if (ob != nb) {
-                    cls[k] = 2;
-                    sx[k] = nb - S.win_base;
-                }
-            } else if (unreached) {
-                cls[k] = 3;
-            }
-            if (unreached) cls[k] |= 4;
-        }
-    }
-    // which (list, k) pairs occur anywhere in the warp: the rest is skipped
-    uint32_t bits = dcnt ? 0x10000u : 0u;
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        if (cls[k] & 4) bits |= 1u << k;
-        if ((cls[k] & 3) == 1) bits |= 1u << (4 + k);
-        if ((cls[k] & 3) == 3) bits |= 1u << (8 + k);
-        if ((cls[k] & 3) == 2) bits |= 1u << (12 + k);
-    }
-    const uint32_t seen = __reduce_or_sync(FULL, bits);
-    if (seen & 0x10000u) {
-        const int dsum = __reduce_add_sync(FULL, dcnt);
-        if (lane == 0 && dsum) atomicAdd(&S.cnt, dsum);
-    }
-    // touched (first finite key), nxt and far: one reservation per list
-    unsigned mt[UNROLL], mn[UNROLL], mf[UNROLL];
-    uint32_t ct = 0, cn = 0, cf = 0;
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        mt[k] = (seen >> k) & 1 ? __ballot_sync(FULL, (cls[k] & 4) != 0) : 0u;
-        mn[k] = (seen >> (4 + k)) & 1 ? __ballot_sync(FULL, (cls[k] & 3) == 1) : 0u;
-        mf[k] = (seen >> (8 + k)) & 1 ? __ballot_sync(FULL, (cls[k] & 3) == 3) : 0u;
-        ct += __popc(mt[k]);
-        cn += __popc(mn[k]);
-        cf += __popc(mf[k]);
-    }
-    uint32_t bt = 0, bn = 0, bf = 0;
-    if (lane == 0) {
-        if (ct) bt = atomicAdd(&S.touch_n, ct);
-        if (cn) bn = atomicAdd(&S.nxt_n, cn);
-        if (cf) bf = atomicAdd(&S.far_n, cf);
-    }
-    bt = __shfl_sync(FULL, bt, 0);
-    bn = __shfl_sync(FULL, bn, 0);
-    bf = __shfl_sync(FULL, bf, 0);
-    uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
-#pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
-        const uint32_t u = q[k].u;
-        if (cls[k] & 4) sl.touch[bt + __popc(mt[k] & lt)] = u;
-        if ((cls[k] & 3) == 1) nxt[bn + __popc(mn[k] & lt)] = u;
-        if ((cls[k] & 3) == 3) sl.far[bf + __popc(mf[k] & lt)] = u;
-        bt += __popc(mt[k]);
-        bn += __popc(mn[k]);
-        bf += __popc(mf[k]);
-        if ((seen >> (12 + k)) & 1) {
-            // lanes joining the same window bucket share one counter update
-            const unsigned g = __match_any_sync(FULL, sx[k]);
-            const int ld = __ffs(g) - 1;
-            uint32_t base = 0;
-            if ((cls[k] & 3) == 2 && lane == ld) base = atomicAdd(&S.sub_n[sx[k]], (uint32_t)__popc(g));
-            base = __shfl_sync(FULL, base, ld);
-            if ((cls[k] & 3) == 2) sl.sub[size_t(sx[k]) * p.n + base + __popc(g & lt)] = u;
-        }
-    }
-}
-
 // Frontier staging of one chunk of up to TPB list entries, compacted to the
 // entries that are expanded (stale ones dropped): each row's start (with the
 // vertex's liveness in bit 63), its distance, and the exclusive prefix of the
@@ -361,7 +303,135 @@ struct Frontier {
     typename K::T kv[TPB];  // make_key(distance, liveness, vertex) of the row's vertex
     uint32_t wrows[TPB / 32];
     uint64_t wdeg[TPB / 32];
+    // per warp: the improvements of one step, compacted (vertex, new key, old key)
+    uint32_t iu[TPB / 32][32];
+    typename K::T ic[TPB / 32][32];
+    typename K::T io[TPB / 32][32];
 };
+
+// Commit of one warp step, called by all 32 lanes. The atomicMins of all
+// UNROLL probes are issued together (independent, so their round trips
+// overlap). The improvements (typically a few per step of 128 arcs) are then
+// compacted through the warp's shared buffer, so that each is classified by
+// one lane, and the appends to the touched list, nxt, far and the window
+// buckets take one shared atomic per warp and list (per bucket for the
+// window), the live-pending count one per warp; more than 32 improvements
+// take several passes.
+template <typename K>
+__device__ __forceinline__ void commit_one(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
+                                           uint32_t h, bool has, uint32_t u, typename K::T cand,
+                                           typename K::T old) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1;
+    uint32_t cls = 0;  // 0 none, 1 nxt (current bucket), 2 window bucket, 3 far
+    uint32_t sx = NONE;
+    bool touch = false;
+    int dcnt = 0;
+    if (has) {
+        const bool unreached = old == key_inf<K>();
+        const uint32_t nb = bucket_of(p, key_dist<K>(cand));
+        const uint32_t ob = unreached ? NONE : bucket_of(p, key_dist<K>(old));
+        const bool f_new = nb > S.bcur && is_live<K>(cand, u, h);
+        const bool f_old = !unreached && ob > S.bcur && is_live<K>(old, u, h);
+        dcnt = int(f_new) - int(f_old);
+        if (nb == S.bcur) {
+            if (atomicExch(&sl.rtag[u], S.rid) != S.rid) cls = 1;
+        } else if (key_dist<K>(cand) < S.w_hi) {
+            if (ob != nb) {
+                cls = 2;
+                sx = nb - S.win_base;
+            }
+        } else if (unreached) {
+            cls = 3;
+        }
+        touch = unreached;
+    }
+    const int dsum = __reduce_add_sync(FULL, dcnt);
+    const unsigned mt = __ballot_sync(FULL, touch);
+    const unsigned mn = __ballot_sync(FULL, cls == 1);
+    const unsigned mf = __ballot_sync(FULL, cls == 3);
+    const unsigned mw = __ballot_sync(FULL, cls == 2);
+    uint32_t bt = 0, bn = 0, bf = 0;
+    if (lane == 0) {
+        if (dsum) atomicAdd(&S.cnt, dsum);
+        if (mt) bt = atomicAdd(&S.touch_n, uint32_t(__popc(mt)));
+        if (mn) bn = atomicAdd(&S.nxt_n, uint32_t(__popc(mn)));
+        if (mf) bf = atomicAdd(&S.far_n, uint32_t(__popc(mf)));
+    }
+    if (mt) {
+        bt = __shfl_sync(FULL, bt, 0);
+        if (touch) sl.touch[bt + __popc(mt & lt)] = u;
+    }
+    if (mn) {
+        bn = __shfl_sync(FULL, bn, 0);
+        uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
+        if (cls == 1) nxt[bn + __popc(mn & lt)] = u;
+    }
+    if (mf) {
+        bf = __shfl_sync(FULL, bf, 0);
+        if (cls == 3) sl.far[bf + __popc(mf & lt)] = u;
+    }
+    if (mw) {
+        // lanes joining the same window bucket share one counter update
+        const unsigned g = __match_any_sync(FULL, sx);
+        const int ld = __ffs(g) - 1;
+        uint32_t base = 0;
+        if (cls == 2 && lane == ld) base = atomicAdd(&S.sub_n[sx], uint32_t(__popc(g)));
+        base = __shfl_sync(FULL, base, ld);
+        if (cls == 2) sl.sub[size_t(sx) * p.n + base + __popc(g & lt)] = u;
+    }
+}
+
+template <int TPB, typename K>
+__device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F,
+                                            const Slot<K> &sl, uint32_t h,
+                                            const Probe<K> (&q)[UNROLL]) {
+    using KS = typename K::T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    KS old[UNROLL];
+    unsigned im = 0;
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k) {
+        old[k] = 0;
+        if (q[k].live && q[k].cand < q[k].seen) old[k] = atomic_min_key(&sl.key[q[k].u], q[k].cand);
+    }
+#pragma unroll
+    for (int k = 0; k < UNROLL; ++k)
+        if (q[k].live && q[k].cand < q[k].seen && q[k].cand < old[k]) im |= 1u << k;
+    const uint32_t c = __popc(im);
+    uint32_t x = c;  // inclusive prefix of the per-lane counts
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += y;
+    }
+    const uint32_t total = __shfl_sync(FULL, x, 31);
+    for (uint32_t b0 = 0; b0 < total; b0 += 32) {
+        uint32_t j = x - c;
+#pragma unroll
+        for (int k = 0; k < UNROLL; ++k) {
+            if ((im >> k) & 1u) {
+                if (j >= b0 && j < b0 + 32) {
+                    F.iu[warp][j - b0] = q[k].u;
+                    F.ic[warp][j - b0] = q[k].cand;
+                    F.io[warp][j - b0] = old[k];
+                }
+                ++j;
+            }
+        }
+        __syncwarp();
+        const bool has = lane < total - b0;
+        uint32_t u = 0;
+        KS cand = 0, o = 0;
+        if (has) {
+            u = F.iu[warp][lane];
+            cand = F.ic[warp][lane];
+            o = F.io[warp][lane];
+        }
+        __syncwarp();  // the buffer is free for the next pass
+        commit_one<K>(p, S, sl, h, has, u, cand, o);
+    }
+}
 
 // largest o in [lo, hi) with pre[o] <= j, given pre[lo] <= j
 template <int TPB, typename K>
@@ -415,56 +485,150 @@ __device__ __forceinline__ uint64_t clt_query(const TreeLaunch &p, const Shared 
 // holds, written into the slot's dense array p.lt_root by hub position.
 __device__ __forceinline__ uint32_t lth_slot(uint32_t hp) { return (hp * 2654435761u) >> 22; }
 
-// One warp answers the query of one vertex, whose table labels are [a, b):
-// each lane takes every 32nd of them (coalesced), looks its hub up in the
-// root's labels, and the warp stops at the first step where some lane found a
-// witness.
+// does table entry (c, dc) of v witness dv: d(h, c) + dc <= dv for a hub c of
+// the root (its distance from the hash, or from the slot's dense array rootd)
+__device__ __forceinline__ bool lt_hit(const Shared &S, const uint32_t *rootd, uint32_t c, uint32_t dc,
+                                       uint32_t dv) {
+    if (dc > dv) return false;  // also every filler entry (all ones)
+    if (rootd) {
+        // written by this CTA at tree start: a plain load
+        const uint32_t dhc = rootd[c];
+        return dhc != NONE && uint64_t(dhc) + dc <= dv;
+    }
+    for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
+        const uint32_t key = S.lth_key[sx];
+        if (key == 0) return false;  // the hash holds at most half its slots
+        if (key == c + 1) return uint64_t(S.lth_val[sx]) + dc <= dv;
+    }
+}
+
+// One warp answers the query of one vertex whose table labels are entries
+// [a, b) in global memory: each lane takes every 32nd of them (coalesced),
+// QSTEPS steps of 32 are loaded before any is looked up, and the warp stops
+// at the first step where some lane found a witness.
 __device__ __forceinline__ bool lt_prunes_warp(const TreeLaunch &p, const Shared &S,
                                                const uint32_t *rootd, uint64_t a, uint64_t b,
                                                uint32_t dv, int lane) {
-    // QSTEPS steps of 32 labels are loaded before any is looked up, so a list
-    // of up to 32 * QSTEPS labels costs one round trip to memory
     for (uint64_t j0 = a; j0 < b; j0 += 32 * QSTEPS) {
-        uint32_t dc[QSTEPS], hp[QSTEPS];
+        uint2 x[QSTEPS];
 #pragma unroll
         for (int u = 0; u < QSTEPS; ++u) {
             const uint64_t j = j0 + uint64_t(u) * 32 + lane;
-            dc[u] = NONE;  // above every distance (R7)
-            hp[u] = 0;
-            if (j < b) {
-                dc[u] = __ldg(&p.lt_d[j]);
-                hp[u] = __ldg(&p.lt_hp[j]);
-            }
+            x[u] = j < b ? __ldg(&p.lt_e[j]) : make_uint2(0, NONE);
         }
         bool hit = false;
 #pragma unroll
-        for (int u = 0; u < QSTEPS; ++u) {
-            if (dc[u] > dv) continue;
-            if (rootd) {
-                // written by this CTA at tree start: a plain load
-                const uint32_t dhc = rootd[hp[u]];
-                hit |= dhc != NONE && uint64_t(dhc) + dc[u] <= dv;
-            } else {
-                const uint32_t c = hp[u];
-                for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
-                    const uint32_t key = S.lth_key[sx];
-                    if (key == 0) break;
-                    if (key == c + 1) {
-                        hit |= uint64_t(S.lth_val[sx]) + dc[u] <= dv;
-                        break;
-                    }
-                }
-            }
+        for (int u = 0; u < QSTEPS; ++u) hit |= lt_hit(S, rootd, x[u].x, x[u].y, dv);
+        if (__any_sync(0xffffffffu, hit)) return true;
+    }
+    return false;
+}
+
+// The same query over len entries already staged in shared memory.
+__device__ __forceinline__ bool lt_prunes_staged(const Shared &S, const uint32_t *rootd, const uint2 *e,
+                                                 uint32_t len, uint32_t dv, int lane) {
+    for (uint32_t j0 = 0; j0 < len; j0 += 32) {
+        const uint32_t j = j0 + lane;
+        bool hit = false;
+        if (j < len) {
+            const uint2 x = e[j];
+            hit = lt_hit(S, rootd, x.x, x.y, dv);
         }
         if (__any_sync(0xffffffffu, hit)) return true;
     }
     return false;
 }
 
+// Wait for the current phase of the staging barrier, bounded: past WAIT_LIMIT
+// polls the error flag is set and the tree aborts; the wait goes on for as
+// long again, so that copies still in flight land before the area is reused.
+__device__ __forceinline__ void stage_wait(const TreeLaunch &p, Shared &S, uint32_t parity) {
+    for (uint32_t it = 0; !mbar_try_wait(&S.mbar, parity); ++it) {
+        if (it == WAIT_LIMIT) {
+            atomicExch(&p.flags[0], ERR_WAIT_LIMIT);
+            S.abort = 1;
+        }
+        if (it >= 2 * WAIT_LIMIT) break;
+    }
+}
+
+// Answers the chunk's qn queued label-table queries (query q: its list starts
+// at F.base[q], F.pre[q] = length << 32 | distance); the answer (1 = pruned)
+// replaces F.pre[q]. The lists are copied into the shared staging area by the
+// copy engine, as many per batch as fit, each widened to 16-byte boundaries
+// (entries are 8 bytes, so one spare entry at either end): thread q issues the
+// copy of query q, the batch's barrier counts the bytes, and then each warp
+// answers whole queries from shared memory. No registers hold loads in flight,
+// so a batch keeps hundreds of lists in flight per CTA. A list longer than
+// the staging area is answered from global memory afterwards.
+template <int TPB, typename K>
+__device__ void lt_answer(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, uint32_t qn,
+                          uint8_t *stage, uint32_t &parity) {
+    constexpr int NW = TPB / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t t = threadIdx.x;
+    const uint32_t *rootd = S.lt_dense ? p.lt_root + size_t(blockIdx.x) * p.n : nullptr;
+    // the batch's staged queries; the staging keys are free during stage A
+    uint32_t *blist = reinterpret_cast<uint32_t *>(F.kv);
+    uint64_t la = 0;
+    uint32_t bytes = 0;
+    bool todo = false;
+    if (t < qn) {
+        la = F.base[t];
+        const uint64_t len = F.pre[t] >> 32;
+        bytes = uint32_t((((la + len + 1) & ~1ull) - (la & ~1ull)) * 8u);
+        todo = bytes <= p.stage_bytes;
+        if (!todo) F.pre[t] |= 1ull << 63;  // answered from global memory
+    }
+    while (__syncthreads_or(todo)) {
+        if (t == 0) {
+            S.stage_used = 0;
+            S.bn = 0;
+        }
+        __syncthreads();
+        bool issued = false;
+        if (todo) {
+            // the first reservation of a batch always fits
+            const uint32_t off = atomicAdd(&S.stage_used, bytes);
+            if (off + bytes <= p.stage_bytes) {
+                issued = true;
+                todo = false;
+                blist[atomicAdd(&S.bn, 1u)] = t;
+                F.base[t] = (uint64_t(off) << 1) | (la & 1);
+                mbar_arrive_expect_tx(&S.mbar, bytes);
+                bulk_to_shared(stage + off, p.lt_e + (la & ~1ull), bytes, &S.mbar);
+            }
+        }
+        if (!issued) mbar_arrive(&S.mbar);  // every thread arrives once per batch
+        stage_wait(p, S, parity);
+        parity ^= 1u;
+        __syncthreads();  // blist and S.bn
+        const uint32_t bn = S.bn;
+        for (uint32_t i = warp; i < bn; i += NW) {
+            const uint32_t q = blist[i];
+            const uint64_t b = F.base[q], e = F.pre[q];
+            const uint2 *ent = reinterpret_cast<const uint2 *>(stage + (b >> 1)) + (b & 1);
+            const bool hit = lt_prunes_staged(S, rootd, ent, uint32_t(e >> 32), uint32_t(e), lane);
+            __syncwarp();  // every lane has read the entry before lane 0 rewrites it
+            if (lane == 0) F.pre[q] = hit;
+        }
+        __syncthreads();  // the next batch reuses the staging area
+    }
+    for (uint32_t q = warp; q < qn; q += NW) {
+        const uint64_t e = F.pre[q];
+        if (!(e >> 63)) continue;
+        const uint64_t a = F.base[q];
+        const bool hit =
+            lt_prunes_warp(p, S, rootd, a, a + ((e >> 32) & 0x7FFFFFFFu), uint32_t(e), lane);
+        __syncwarp();
+        if (lane == 0) F.pre[q] = hit;
+    }
+}
+
 template <int TPB, typename K>
 __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, const Slot<K> &sl,
                              uint32_t h, unsigned long long &expanded, unsigned long long &arcs,
-                             unsigned long long &pruned) {
+                             unsigned long long &pruned, uint8_t *stage, uint32_t &parity) {
     using KS = typename K::T;
     constexpr int NW = TPB / 32;
     constexpr uint32_t STEP = 32 * UNROLL;
@@ -527,13 +691,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
             }
             __syncthreads();
             const uint32_t qn = S.qn;
-            const uint32_t *rootd = S.lt_dense ? p.lt_root + size_t(blockIdx.x) * p.n : nullptr;
-            for (uint32_t q = warp; q < qn; q += NW) {
-                const uint64_t a = F.base[q], e = F.pre[q];
-                const bool hit = lt_prunes_warp(p, S, rootd, a, a + (e >> 32), uint32_t(e), lane);
-                __syncwarp();  // every lane has read the entry before lane 0 rewrites it
-                if (lane == 0) F.pre[q] = hit;
-            }
+            if (qn) lt_answer<TPB, K>(p, S, F, qn, stage, parity);
             __syncthreads();
             if (threadIdx.x == 0) S.qn = 0;  // read again only after the chunk's next barrier
             if (ask) cut = F.pre[qs] != 0;
@@ -650,7 +808,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                     if (uint32_t(k * 32 + lane) < span) probe(p, S, sl, kv[k], a[k], pr[k]);
                 }
                 if (lane == 0) arcs += span;
-                commit_step(p, S, sl, h, pr);
+                commit_step<TPB, K>(p, S, F, sl, h, pr);
                 oa = ob;
             }
         }
@@ -748,8 +906,11 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
 
     unsigned long long expanded = 0, arcs = 0, trivial = 0, trees = 0, rounds_all = 0, buckets = 0;
     unsigned long long pruned = 0;
+    uint8_t *stage = reinterpret_cast<uint8_t *>(fin_bitmap) + stage_offset(p.fin_words);
+    uint32_t parity = 0;  // phase of S.mbar the next staging batch completes
     if (threadIdx.x == 0) {
         S.rid = p.slot_ctr[blockIdx.x * 4 + 0];
+        mbar_init(&S.mbar, TPB);
     }
 
     for (;;) {
@@ -811,17 +972,20 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             }
             if (lt_dense) {
                 uint32_t *rootd = p.lt_root + so;
-                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) rootd[__ldg(&p.lt_hp[j])] = __ldg(&p.lt_d[j]);
+                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) {
+                    const uint2 e = __ldg(&p.lt_e[j]);
+                    rootd[e.x] = e.y;
+                }
             } else if (lt_prune) {
                 for (uint32_t i = threadIdx.x; i < LTH_SLOTS; i += TPB) S.lth_key[i] = 0;
                 __syncthreads();
                 const uint64_t a = lt_a;
                 const uint32_t cnt = uint32_t(lt_b - lt_a);
                 for (uint32_t i = threadIdx.x; i < cnt; i += TPB) {
-                    const uint32_t c = __ldg(&p.lt_hp[a + i]);
-                    for (uint32_t sx = lth_slot(c);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
-                        if (atomicCAS(&S.lth_key[sx], 0u, c + 1) == 0u) {
-                            S.lth_val[sx] = __ldg(&p.lt_d[a + i]);
+                    const uint2 e = __ldg(&p.lt_e[a + i]);
+                    for (uint32_t sx = lth_slot(e.x);; sx = (sx + 1) & (LTH_SLOTS - 1)) {
+                        if (atomicCAS(&S.lth_key[sx], 0u, e.x + 1) == 0u) {
+                            S.lth_val[sx] = e.y;
                             break;
                         }
                     }
@@ -855,7 +1019,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             __syncthreads();
             uint32_t rounds = 0;
             for (;;) {
-                expand_round<TPB, K>(p, S, F, sl, h, expanded, arcs, pruned);  // ends with a barrier
+                expand_round<TPB, K>(p, S, F, sl, h, expanded, arcs, pruned, stage,
+                                     parity);  // ends with a barrier
                 if (S.abort) break;
                 ++rounds_all;
                 if (++rounds > MAX_ROUNDS_PER_TREE) {
@@ -930,7 +1095,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 // reset and give up on this tree; the host reports the error
                 for (uint32_t i = threadIdx.x; i < S.touch_n; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
                 if (lt_dense)
-                    for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_hp[j])] = NONE;
+                    for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_e[j]).x] = NONE;
                 __threadfence();
                 __syncthreads();
                 break;
@@ -971,7 +1136,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             // reset exactly what this tree modified
             for (uint32_t i = threadIdx.x; i < nt; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
             if (lt_dense)
-                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_hp[j])] = NONE;
+                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_e[j]).x] = NONE;
             // the next tree reads keys with L2 loads and L2 atomics: the plain
             // reset stores must be visible there first, not only inside the CTA
             __threadfence();
@@ -1043,11 +1208,18 @@ cudaError_t allow_smem() {
     return e;
 }
 
+// dynamic shared memory of a launch: the settled bitmap, then (label-pruned
+// phases) the staging area at the next multiple of 128 bytes
+size_t dyn_bytes(uint32_t fin_words, uint32_t stage_bytes) {
+    return stage_bytes ? ((size_t(fin_words) * 4 + 127) & ~size_t(127)) + stage_bytes
+                       : size_t(fin_words) * 4;
+}
+
 template <int TPB>
 cudaError_t launch_t(const TreeLaunch &p, int slots, cudaStream_t s) {
     cudaError_t e = allow_smem<TPB>();
     if (e) return e;
-    const size_t smem = size_t(p.fin_words) * 4;
+    const size_t smem = dyn_bytes(p.fin_words, p.stage_bytes);
     if (p.out_p)
         plant_trees_kernel<TPB, KeyP><<<slots, TPB, smem, s>>>(p);
     else if (p.key_bytes == 4)
@@ -1059,38 +1231,45 @@ cudaError_t launch_t(const TreeLaunch &p, int slots, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// CTAs per SM with `words` bitmap words; all key layouts are built under the
-// same register cap, the smaller of the two is returned
+// CTAs per SM with `bytes` of dynamic shared memory; all key layouts are built
+// under the same register cap, the smallest of the three is returned
 template <int TPB>
-int occ(uint32_t words) {
+int occ(size_t bytes) {
     if (allow_smem<TPB>()) return 0;
     int b = 0, b4 = 0, bp = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB, KeyW>, TPB, size_t(words) * 4);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, plant_trees_kernel<TPB, KeyN>, TPB, size_t(words) * 4);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, plant_trees_kernel<TPB, KeyP>, TPB, size_t(words) * 4);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, plant_trees_kernel<TPB, KeyW>, TPB, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b4, plant_trees_kernel<TPB, KeyN>, TPB, bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bp, plant_trees_kernel<TPB, KeyP>, TPB, bytes);
     b = b < b4 ? b : b4;
     return b < bp ? b : bp;
 }
 
-// the largest bitmap (<= want words) that keeps the register-limited number
-// of CTAs per SM
+// the most dynamic shared memory (a multiple of 128 bytes) that keeps the
+// register-limited number of CTAs per SM
 template <int TPB>
-uint32_t fin_words_t(uint32_t want) {
+uint32_t dyn_budget_t() {
     const int full = occ<TPB>(0);
     if (full <= 0) return 0;
-    uint32_t lo = 0, hi = want;  // occ(lo) == full holds for lo = 0
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))
+        return 0;
+    uint32_t lo = 0, hi = uint32_t(optin) & ~127u;  // occ(lo) == full holds for lo = 0
     if (occ<TPB>(hi) >= full) return hi;
-    while (hi - lo > 32) {
-        const uint32_t mid = lo + (hi - lo) / 2;
+    while (hi - lo > 128) {
+        const uint32_t mid = (lo + (hi - lo) / 2) & ~127u;
+        if (mid <= lo) break;
         if (occ<TPB>(mid) >= full) lo = mid; else hi = mid;
     }
-    return lo & ~31u;
+    return lo;
 }
 
 }  // namespace
 
 cudaError_t launch_plant_trees(const TreeLaunch &p, int tpt, int slots, cudaStream_t s) {
     if (p.nwin < 2 || p.nwin > NWIN_MAX) return cudaErrorInvalidValue;
+    // the staging copies read the label table in 16-byte units
+    if (p.lt_off && ((reinterpret_cast<uintptr_t>(p.lt_e) & 15) || (p.stage_bytes & 15)))
+        return cudaErrorMisalignedAddress;
     switch (tpt) {
         case 32: return launch_t<32>(p, slots, s);
         case 64: return launch_t<64>(p, slots, s);
@@ -1102,29 +1281,43 @@ cudaError_t launch_plant_trees(const TreeLaunch &p, int tpt, int slots, cudaStre
     }
 }
 
-int plant_max_slots_per_sm(int tpt, uint32_t fin_words) {
+int plant_max_slots_per_sm(int tpt, uint32_t fin_words, uint32_t stage_bytes) {
+    const size_t bytes = dyn_bytes(fin_words, stage_bytes);
     switch (tpt) {
-        case 32: return occ<32>(fin_words);
-        case 64: return occ<64>(fin_words);
-        case 128: return occ<128>(fin_words);
-        case 256: return occ<256>(fin_words);
-        case 512: return occ<512>(fin_words);
-        case 1024: return occ<1024>(fin_words);
+        case 32: return occ<32>(bytes);
+        case 64: return occ<64>(bytes);
+        case 128: return occ<128>(bytes);
+        case 256: return occ<256>(bytes);
+        case 512: return occ<512>(bytes);
+        case 1024: return occ<1024>(bytes);
         default: return 0;
     }
 }
 
-uint32_t plant_fin_words(int tpt, uint32_t n) {
-    const uint32_t want = (n + 31) / 32;
+uint32_t plant_dyn_budget(int tpt) {
     switch (tpt) {
-        case 32: return fin_words_t<32>(want);
-        case 64: return fin_words_t<64>(want);
-        case 128: return fin_words_t<128>(want);
-        case 256: return fin_words_t<256>(want);
-        case 512: return fin_words_t<512>(want);
-        case 1024: return fin_words_t<1024>(want);
+        case 32: return dyn_budget_t<32>();
+        case 64: return dyn_budget_t<64>();
+        case 128: return dyn_budget_t<128>();
+        case 256: return dyn_budget_t<256>();
+        case 512: return dyn_budget_t<512>();
+        case 1024: return dyn_budget_t<1024>();
         default: return 0;
     }
+}
+
+void plant_smem_split(int tpt, uint32_t n, bool staged, uint32_t *fin_words, uint32_t *stage_bytes) {
+    const uint32_t budget = plant_dyn_budget(tpt);
+    const uint32_t want = (n + 31) / 32;
+    uint32_t stage = 0;
+    if (staged) {
+        if (const char *x = std::getenv("CHL_STAGE_KB")) stage = std::min<uint32_t>(budget / 2, uint32_t(atoi(x)) << 10) & ~127u;
+    }
+    const uint32_t room = budget > stage + 128 ? budget - stage - 128 : 0;
+    uint32_t fw = std::min<uint32_t>(want, room / 4);
+    if (fw < want) fw &= ~31u;
+    *fin_words = fw;
+    *stage_bytes = stage;
 }
 
 }  // namespace chl
