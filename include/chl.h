@@ -38,6 +38,10 @@
  *     are taken in 64-bit and saturate at UINT32_MAX.
  *   - The library runs every step on the GPU (sm_103a); it has no CPU
  *     fallback.
+ *   - A call that launches work clears the calling thread's CUDA last-error
+ *     state (cudaGetLastError) on entry, and again after a CUDA call of its
+ *     own failed, so that an error of earlier work is not reported as its
+ *     own and a failed allocation does not fail the next call.
  */
 #ifndef CHL_H
 #define CHL_H
@@ -137,6 +141,24 @@ typedef struct chl_labels chl_labels;
  *                          with the labels of earlier phases (a power of two
  *                          in [32, 1024]); smaller blocks put more of those
  *                          small trees in flight. 0 = threads_per_tree
+ *   switch_ratio           first-phase switch of the hybrid: when the labels
+ *                          of the first phase (one tree per slot), per arc of
+ *                          the graph, stay below this ratio, the label-pruned
+ *                          phases start right after it. Scale-free graphs give
+ *                          about 1.4 (R-MAT) to 3 (Barabasi-Albert), grids
+ *                          above 10, where label pruning costs more than it
+ *                          saves. 0 = 6 (and only when psi_threshold is 0);
+ *                          negative = never (the Psi rule alone decides)
+ *   round_limit            expansion rounds one tree may take before the
+ *                          build stops with CHL_ETIMEOUT (0 = 2^26, far above
+ *                          any tree of a graph below 2^31 vertices; a small
+ *                          value makes the bounded-wait path testable)
+ *   query_stage_kb         KiB of shared memory per tree slot in which the
+ *                          label-pruned phases stage the label lists their
+ *                          distance queries read, copied by the copy engine
+ *                          (cp.async.bulk) instead of register loads; 0 = off
+ *                          (measured slower on the R-MAT and grid workloads,
+ *                          kept for other graphs and hardware)
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
@@ -177,6 +199,9 @@ typedef struct {
     int32_t pruned_bucket_delta;
     float psi_threshold;
     int32_t pruned_threads_per_tree;
+    float switch_ratio;
+    uint32_t round_limit;
+    int32_t query_stage_kb;
 } chl_build_opts;
 
 #define CHL_MAX_COMMON_HUBS 64
@@ -271,29 +296,39 @@ typedef struct {
 chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl_build_opts *base,
                     void *stream, chl_build_opts *best, chl_tune_report *report);
 
-/* n, total number of labels, and device bytes held by the object. */
+/* n, total number of labels (the labeling's size, sum of |L_v|: the paper's
+   ALS times n, Sec. 7.1 and Table 3), and device bytes held by the object.
+   Any output pointer may be NULL. Errors: CHL_EINVAL (L is NULL). */
 chl_status chl_labels_info(const chl_labels *L, uint32_t *n, uint64_t *total, uint64_t *bytes);
 
 /* Counters of the build that produced L (see chl_build_stats). */
 chl_status chl_labels_stats(const chl_labels *L, chl_build_stats *stats);
 
 /*
- * Device views, valid until chl_labels_free(L):
+ * Device views, valid until chl_labels_free(L). The labels are stored once,
+ * per vertex (as the paper stores them for its shared-memory runs, Sec. 7.2
+ * footnote), each list in the order the sort step of Algorithm 2 gives it
+ * (by hub rank):
  *   offsets  [n+1] uint64; the labels of vertex v are entries
  *            [offsets[v], offsets[v+1])
  *   hub      [total] uint32 hub vertex id; within each vertex sorted by
  *            R(hub) descending (most important first); the last entry of
  *            L_v is v itself with distance 0
  *   dist     [total] uint32 d(v, hub)
- * Any output pointer may be NULL.
+ * Any output pointer may be NULL. The pointers are device memory of the
+ * device L was built on; the library keeps ownership. Errors: CHL_EINVAL (L is
+ * NULL).
  */
 chl_status chl_labels_view(const chl_labels *L, const uint64_t **offsets, const uint32_t **hub,
                            const uint32_t **dist);
 
 /*
- * Copy the labels into caller buffers (offsets [n+1], hub [total],
- * dist [total]; any may be NULL) in memory of kind dst_mem, ordered on
- * stream; returns after the copy completed.
+ * Copy the labels (the per-vertex, hub-rank-sorted lists of chl_labels_view:
+ * Algorithm 2's sort step, Sec. 7.2 footnote) into caller buffers (offsets
+ * [n+1], hub [total], dist [total]; any may be NULL) in memory of kind
+ * dst_mem, ordered on stream; returns after the copy completed.
+ * Errors: CHL_EINVAL (L is NULL, unknown memory kind, or the current device is
+ * not the one L was built on), CHL_ECUDA.
  */
 chl_status chl_labels_copy(const chl_labels *L, uint64_t *offsets, uint32_t *hub, uint32_t *dist,
                            chl_mem dst_mem, void *stream);
@@ -304,8 +339,8 @@ chl_status chl_labels_copy(const chl_labels *L, uint64_t *offsets, uint32_t *hub
  *   q        number of pairs (0 is allowed and does nothing)
  *   out      [q] uint32, out[i] = d(u_i, v_i), UINT32_MAX if u_i and v_i are
  *            disconnected; same memory kind as pairs
- * Errors: CHL_EINVAL (NULL pointers, a vertex id >= n), CHL_ENOMEM,
- * CHL_ECUDA.
+ * Errors: CHL_EINVAL (NULL pointers, a vertex id >= n, or the current device
+ * is not the one L was built on), CHL_ENOMEM, CHL_ECUDA.
  */
 chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t *out,
                      chl_mem mem, void *stream);
@@ -324,6 +359,8 @@ chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint64_t q, uin
  *   - q <= 1048576 (2^20) pairs per call; larger q returns CHL_EINVAL.
  *   - The first call on a device resolves the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Each call synchronises `stream` before it returns (it reads the
+ *     bad-vertex flag back to the host).
  *   - Every call uses the same array: calls whose work overlaps on the GPU
  *     (other streams, other host threads) race and must be serialised by the
  *     caller.
@@ -350,12 +387,16 @@ chl_status chl_labels_parents(const chl_labels *L, uint32_t *parent, chl_mem mem
  *   lens   [q] vertices on the path (1 for u = v, 0 when u and v are not
  *          connected); a value above max_len means the path was cut there
  *   mem    where pairs, paths and lens live
- * Errors: CHL_EINVAL (NULL, id >= n, labels without parents).
+ * Errors: CHL_EINVAL (NULL, id >= n, labels without parents, or the current
+ * device is not the one L was built on).
  */
 chl_status chl_path(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t max_len,
                     uint32_t *paths, uint32_t *lens, chl_mem mem, void *stream);
 
-/* Release the labels object (NULL is allowed). Synchronises its stream. */
+/* Release the labels object and its device arrays (NULL is allowed); the
+   counterpart of chl_build, which hands ownership to the caller. The arrays
+   are freed on the device L was built on, whatever device is current; the
+   call synchronises that device. */
 void chl_labels_free(chl_labels *L);
 
 /* Message describing the last failure on the calling thread ("" if none). */

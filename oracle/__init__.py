@@ -139,10 +139,12 @@ def build_labels(g, rank, method: str = "plant", roots=None, threads: int = 1,
 def build_labels_phased(g, rank, ends, threads: int = 1, with_stats: bool = False):
     """Labels built in phases, the Hybrid of Sec. 5.2 as label-pruned phases:
     phase k holds the roots of rank positions [ends[k-1], ends[k]) (ends
-    increasing, last = n); its trees run Algorithm 3 and also skip a popped
+    increasing, last <= n); its trees run Algorithm 3 and also skip a popped
     vertex whose distance query over every label of the earlier phases' roots
     is at most its distance (hubs ranked above all of the phase's roots, the
-    condition of Sec. 5.3). The result must be the canonical labeling.
+    condition of Sec. 5.3). The result must be the canonical labeling, or with
+    a last end below n its labels whose hub is among the top ends[-1] (trees
+    are independent, Sec. 5.2).
     Returns Labels, or (Labels, stats[n,4] by rank position) when with_stats."""
     lib = _load()
     n = int(g.n)

@@ -682,7 +682,10 @@ int orc_build(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const ui
  * Labels built in phases: the Hybrid of Sec. 5.2 in the form the library runs
  * it (reading R15 of the design notes: label-pruned phases instead of GLL
  * supersteps and cleaning). Phase k holds the roots of rank positions
- * [ends[k-1], ends[k]) (ends[-1] = 0, ends[nphases-1] = n). Its trees run
+ * [ends[k-1], ends[k]) (ends[-1] = 0, ends[nphases-1] <= n). With a last end
+ * below n only the roots of rank positions below it are built: trees are
+ * independent (Sec. 5.2), so those are the canonical labels whose hub ranks
+ * among the top ends[nphases-1]. Its trees run
  * Algorithm 3 and also skip a popped vertex (no label, no relaxation) whose
  * distance query over every label of the earlier phases' roots is at most
  * its distance. Those roots are all hubs ranked above the phase's roots, the
@@ -694,7 +697,7 @@ int orc_build_phased(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, c
                      const uint32_t *rank, const uint32_t *ends, uint32_t nphases, int threads,
                      orc_labels *out, root_stats *stats) {
     memset(out, 0, sizeof(*out));
-    if (n == 0 || nphases == 0 || ends[nphases - 1] != n) return -3;
+    if (n == 0 || nphases == 0 || ends[nphases - 1] > n) return -3;
     for (uint32_t k = 0; k < nphases; ++k)
         if (ends[k] == 0 || (k && ends[k] <= ends[k - 1])) return -3;
     if (threads < 1) threads = 1;

@@ -97,7 +97,8 @@ class chl_build_opts(C.Structure):
                 ("window_buckets", C.c_int32), ("slots", C.c_int32), ("mode", C.c_int32),
                 ("flags", C.c_int32), ("label_capacity", C.c_uint64), ("common_hubs", C.c_int32),
                 ("pruned_bucket_delta", C.c_int32), ("psi_threshold", C.c_float),
-                ("pruned_threads_per_tree", C.c_int32)]
+                ("pruned_threads_per_tree", C.c_int32), ("switch_ratio", C.c_float),
+                ("round_limit", C.c_uint32), ("query_stage_kb", C.c_int32)]
 
 
 class chl_tune_report(C.Structure):

@@ -2,6 +2,7 @@
 // memory, the build driver (graph preparation, persistent tree launch with
 // retry on a full label buffer, label assembly) and the query entry point.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cstdarg>
 #include <cstdio>
@@ -26,8 +27,28 @@ chl_status set_error(chl_status st, const char *fmt, ...) {
     return st;
 }
 
+chl_status cuda_status(cudaError_t e, const char *what) {
+    // the failed call also left e in the thread's last-error state (an
+    // allocation failure is not sticky): consume it, or the next launch check
+    // of a later call would report it again
+    (void)cudaGetLastError();
+    return set_error(e == cudaErrorMemoryAllocation ? CHL_ENOMEM : CHL_ECUDA, "%s: %s", what,
+                     cudaGetErrorString(e));
+}
+
 cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
                                int *launches);
+
+int device_sms() {
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> cached[MAXDEV];
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < MAXDEV && (v = cached[dev].load(std::memory_order_relaxed)) > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v < 1) return 1;
+    if (dev >= 0 && dev < MAXDEV) cached[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 namespace {
 
@@ -72,12 +93,17 @@ cudaError_t grow_records(void **bufs, int nbufs, uint64_t T, uint64_t ncap, cuda
     return cudaSuccess;
 }
 
+// expansion rounds one tree may take (far above any real tree)
+constexpr uint32_t DEFAULT_ROUND_LIMIT = 1u << 26;
+
 struct Params {
     int tpt;
     int tpt_lt;          // threads per tree in the label-pruned phases
     int slots_lt;        // ... and their slots
     uint32_t fin_words_lt;
     uint32_t stage_lt;   // staging bytes of the queried lists in those phases
+    uint32_t stage_want; // ... as requested
+    uint32_t round_limit;
     uint32_t delta;
     uint32_t delta_lt;  // bucket width of the phases that prune with the label table
     uint32_t nwin;
@@ -115,7 +141,7 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     p.kb = (narrow_fits && !(o.flags & (CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS))) ? 4 : 8;
     {
         uint32_t st0 = 0;
-        plant_smem_split(p.tpt, g.n, false, &p.fin_words, &st0);
+        plant_smem_split(p.tpt, g.n, 0, &p.fin_words, &st0);
     }
     {
         const int want = o.common_hubs == 0 ? 16 : o.common_hubs;  // the paper's eta = 16
@@ -124,7 +150,9 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     p.w_min = g.w_min ? g.w_min : 1;
     p.n = g.n;
     p.tpt_lt = o.pruned_threads_per_tree ? o.pruned_threads_per_tree : p.tpt;
-    plant_smem_split(p.tpt_lt, g.n, true, &p.fin_words_lt, &p.stage_lt);
+    p.stage_want = o.query_stage_kb > 0 ? uint32_t(o.query_stage_kb) << 10 : 0u;
+    plant_smem_split(p.tpt_lt, g.n, p.stage_want, &p.fin_words_lt, &p.stage_lt);
+    p.round_limit = o.round_limit ? o.round_limit : DEFAULT_ROUND_LIMIT;
     int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words, 0);
     if (per_sm < 1) per_sm = 1;
     int per_sm_lt = plant_max_slots_per_sm(p.tpt_lt, p.fin_words_lt, p.stage_lt);
@@ -184,6 +212,7 @@ struct SlotState {
     void fill(const Params &P, uint32_t n, TreeLaunch &tl) const {
         set_delta(tl, P.delta);
         tl.nwin = P.nwin;
+        tl.round_limit = P.round_limit;
         tl.key = key.p;
         tl.key_bytes = P.kb;
         tl.w_min = P.w_min;
@@ -208,6 +237,11 @@ constexpr double PSI_TH = 16.0;
 // above which they do: where the top 16 hubs already cut that much, the labels
 // of every earlier hub cut far more and the per-vertex query pays
 constexpr double CLT_PRUNE_TH = 0.10;
+// ... or, right after the first phase (one tree per slot), the labels it
+// produced per arc of the graph stay below this: scale-free graphs, whose top
+// hubs cover most shortest paths, give 1.4 to 3 and gain from pruning with
+// those labels at once; grids give above 10 and lose by it
+constexpr double SWITCH_RATIO = 6.0;
 
 // Common Label Table (Sec. 5.3): all labels of the `hubs` most important
 // vertices, as a dense [n][stride] table of distances (all ones = no label).
@@ -230,11 +264,18 @@ using namespace chl;
     do {                                                                         \
         cudaError_t e__ = (x);                                                   \
         if (e__ != cudaSuccess) {                                                \
-            st = (e__ == cudaErrorMemoryAllocation)                              \
-                     ? set_error(CHL_ENOMEM, "%s: %s", #x, cudaGetErrorString(e__)) \
-                     : set_error(CHL_ECUDA, "%s: %s", #x, cudaGetErrorString(e__)); \
+            st = cuda_status(e__, #x);                                           \
             goto done;                                                           \
         }                                                                        \
+    } while (0)
+
+// entry of a call that launches work: the calling thread's CUDA last-error
+// state is cleared, so that an error left by earlier, unrelated work is not
+// reported as a failed launch of this call
+#define ENTER()                 \
+    do {                        \
+        g_err[0] = 0;           \
+        (void)cudaGetLastError(); \
     } while (0)
 
 namespace {
@@ -320,13 +361,30 @@ done:
 
 }  // namespace
 
+// the labels live on the current device; another device's pointers would be
+// read by the kernels of this call
+static chl_status check_device(const chl_labels *L) {
+    int dev = -1;
+    const cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetDevice");
+    if (dev != L->device)
+        return set_error(CHL_EINVAL, "labels live on device %d, the current device is %d", L->device, dev);
+    return CHL_OK;
+}
+
+#define CHECK_DEVICE(L)                          \
+    do {                                         \
+        const chl_status d__ = check_device(L);  \
+        if (d__ != CHL_OK) return d__;           \
+    } while (0)
+
 extern "C" const char *chl_last_error(void) { return g_err; }
 
 extern "C" const char *chl_version(void) { return "chl-gb300 0.2 (sm_103a)"; }
 
 extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opts *opts,
                                 void *stream, chl_labels **out) {
-    g_err[0] = 0;
+    ENTER();
     if (!out) return set_error(CHL_EINVAL, "out is NULL");
     *out = nullptr;
     if (!g || !rank) return set_error(CHL_EINVAL, "graph or rank is NULL");
@@ -353,8 +411,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (o.mode != 0 && o.mode != 1) return set_error(CHL_EINVAL, "mode must be 0 or 1");
     if (o.common_hubs > int32_t(CHL_MAX_COMMON_HUBS))
         return set_error(CHL_EINVAL, "common_hubs must be at most %d", CHL_MAX_COMMON_HUBS);
-    if (o.bucket_delta < 0 || o.slots < 0 || o.pruned_bucket_delta < 0 || !(o.psi_threshold >= 0.0f))
-        return set_error(CHL_EINVAL, "negative option");
+    if (o.bucket_delta < 0 || o.slots < 0 || o.pruned_bucket_delta < 0 || !(o.psi_threshold >= 0.0f) ||
+        o.switch_ratio != o.switch_ratio || o.query_stage_kb < 0 || o.query_stage_kb > 4096)
+        return set_error(CHL_EINVAL, "negative or out-of-range option");
     if (o.flags & ~int32_t(CHL_FLAG_WIDE_KEYS | CHL_FLAG_PARENTS | CHL_FLAG_NO_HYBRID |
                            CHL_FLAG_DENSE_ROOT_LABELS))
         return set_error(CHL_EINVAL, "unknown bit in flags");
@@ -452,7 +511,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             P.slots = 1;
             P.slots_lt = 1;
             P.tpt_lt = P.tpt;
-            plant_smem_split(P.tpt_lt, rg.n, true, &P.fin_words_lt, &P.stage_lt);
+            plant_smem_split(P.tpt_lt, rg.n, P.stage_want, &P.fin_words_lt, &P.stage_lt);
         }
     }
 
@@ -661,7 +720,11 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (hybrid && !use_lt && T > T0) {
         const double psi = double(agg[0] - exp0) / double(T - T0);
         const double cut = agg[0] > exp0 ? double(agg[6] - pr0) / double(agg[0] - exp0) : 0.0;
+        const double ratio = m2 ? double(T) / double(m2) : 0.0;
+        const double ratio_th = o.switch_ratio > 0.0f ? double(o.switch_ratio) : SWITCH_RATIO;
         if (psi > psi_th || (P.eta && cut >= CLT_PRUNE_TH && o.psi_threshold == 0.0f)) use_lt = true;
+        else if (ph == 0 && o.psi_threshold == 0.0f && o.switch_ratio >= 0.0f && ratio < ratio_th)
+            use_lt = true;
         // far down the ranking and still cheap trees: the rest is one phase
         else if (pe >= std::max<uint64_t>(uint64_t(P.slots) * 8, 8192) && psi < psi_th / 2)
             hybrid_off = true;
@@ -818,6 +881,7 @@ extern "C" chl_status chl_labels_copy(const chl_labels *L, uint64_t *offsets, ui
     if (!L) return set_error(CHL_EINVAL, "labels is NULL");
     if (dst_mem != CHL_MEM_DEVICE && dst_mem != CHL_MEM_HOST)
         return set_error(CHL_EINVAL, "unknown memory kind");
+    CHECK_DEVICE(L);
     cudaStream_t s = (cudaStream_t)stream;
     const cudaMemcpyKind k = dst_mem == CHL_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
     chl_status st = CHL_OK;
@@ -831,8 +895,9 @@ done:
 
 extern "C" chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint64_t q,
                                 uint32_t *out, chl_mem mem, void *stream) {
-    g_err[0] = 0;
+    ENTER();
     if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    CHECK_DEVICE(L);
     if (q == 0) return CHL_OK;
     if (!pairs || !out) return set_error(CHL_EINVAL, "pairs or out is NULL");
     if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
@@ -863,19 +928,25 @@ done:
 
 extern "C" void chl_labels_free(chl_labels *L) {
     if (!L) return;
+    // free on the device that holds the arrays, then restore the caller's
+    int cur = -1;
+    const bool other = cudaGetDevice(&cur) == cudaSuccess && cur != L->device;
+    if (other) cudaSetDevice(L->device);
     cudaFree(L->offsets);
     cudaFree(L->hub);
     cudaFree(L->hubpos);
     cudaFree(L->dist);
     if (L->parent) cudaFree(L->parent);
+    if (other) cudaSetDevice(cur);
     delete L;
 }
 
 extern "C" chl_status chl_labels_parents(const chl_labels *L, uint32_t *parent, chl_mem mem,
                                          void *stream) {
-    g_err[0] = 0;
+    ENTER();
     if (!L || !parent) return set_error(CHL_EINVAL, "labels or parent is NULL");
     if (!L->parent) return set_error(CHL_EINVAL, "labels were built without CHL_FLAG_PARENTS");
+    CHECK_DEVICE(L);
     if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
     cudaStream_t s = (cudaStream_t)stream;
     chl_status st = CHL_OK;
@@ -890,9 +961,10 @@ done:
 
 extern "C" chl_status chl_path(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t max_len,
                                uint32_t *paths, uint32_t *lens, chl_mem mem, void *stream) {
-    g_err[0] = 0;
+    ENTER();
     if (!L) return set_error(CHL_EINVAL, "labels is NULL");
     if (!L->parent) return set_error(CHL_EINVAL, "labels were built without CHL_FLAG_PARENTS");
+    CHECK_DEVICE(L);
     if (q == 0) return CHL_OK;
     if (!pairs || !lens || (max_len && !paths)) return set_error(CHL_EINVAL, "NULL argument");
     if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
@@ -959,8 +1031,9 @@ NoAllocScratch *g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
 
 extern "C" chl_status chl_query_noalloc(const chl_labels *L, const uint32_t *pairs, uint64_t q,
                                         uint32_t *out, chl_mem mem, void *stream) {
-    g_err[0] = 0;
+    ENTER();
     if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    CHECK_DEVICE(L);
     if (q == 0) return CHL_OK;
     if (!pairs || !out) return set_error(CHL_EINVAL, "pairs or out is NULL");
     if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
@@ -1069,7 +1142,7 @@ done:
 
 extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl_build_opts *base,
                                void *stream, chl_build_opts *best, chl_tune_report *report) {
-    g_err[0] = 0;
+    ENTER();
     if (!g || !rank || !best) return set_error(CHL_EINVAL, "graph, rank or best is NULL");
     if (g->n == 0) return set_error(CHL_EINVAL, "graph has no vertices");
     if (g->n >= 0x7FFFFFFFu) return set_error(CHL_EINVAL, "n must be < 2^31");

@@ -53,6 +53,7 @@ struct TreeLaunch {
     int delta_shift;    // log2(delta) when delta is a power of two, else -1
     uint32_t nwin;
     uint32_t w_min;     // lightest arc weight
+    uint32_t round_limit;  // expansion rounds per tree before ERR_ROUND_LIMIT
     uint32_t fin_words; // settled-filter bitmap words in dynamic shared memory
     uint32_t fin_bits;  // vertices (pos) the bitmap covers: min(n, 32 * fin_words)
     // Common Label Table (Sec. 5.3), or hc = null: hc[v * hc_stride + c] =
@@ -111,10 +112,10 @@ cudaError_t launch_split_trivial(const TreeLaunch &p, uint32_t begin, uint32_t c
 // dynamic shared memory per CTA (bytes) that keeps the CTAs per SM of a launch
 // without any
 uint32_t plant_dyn_budget(int threads_per_tree);
-// that budget split between the settled-filter bitmap (at most one bit per
-// vertex) and, for phases that prune with the label table (staged), the
-// staging area of the queried lists
-void plant_smem_split(int threads_per_tree, uint32_t n, bool staged, uint32_t *fin_words,
+// that budget split between the staging area of the queried lists (phases
+// that prune with the label table; at most stage_want bytes, at most half the
+// budget) and the settled-filter bitmap (at most one bit per vertex)
+void plant_smem_split(int threads_per_tree, uint32_t n, uint32_t stage_want, uint32_t *fin_words,
                       uint32_t *stage_bytes);
 // Common Label Table entries from label records (those of hub positions < hubs)
 cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
@@ -197,5 +198,12 @@ void free_graph(RankGraph &g, cudaStream_t s);
 
 // errors (chl_api.cu)
 chl_status set_error(chl_status st, const char *fmt, ...);
+// a failed CUDA call as a status (CHL_ENOMEM for an allocation failure, else
+// CHL_ECUDA) with its message; clears the thread's CUDA last-error state
+chl_status cuda_status(cudaError_t e, const char *what);
+
+// SMs of the current device (queried once per device; 1 if the query fails),
+// for sizing grid-stride launches
+int device_sms();
 
 }  // namespace chl

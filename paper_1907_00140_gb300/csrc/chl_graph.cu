@@ -211,7 +211,7 @@ __global__ void rank_arcs_kernel(uint32_t n, const uint64_t *row, const uint32_t
 
 int grid_for(uint64_t work, int tpb) {
     uint64_t b = (work + tpb - 1) / tpb;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > uint64_t(device_sms()) * 32) b = uint64_t(device_sms()) * 32;
     if (b < 1) b = 1;
     return int(b);
 }
@@ -222,7 +222,7 @@ int grid_for(uint64_t work, int tpb) {
     do {                                                                        \
         cudaError_t e__ = (x);                                                  \
         if (e__ != cudaSuccess) {                                               \
-            st = set_error(CHL_ECUDA, "%s: %s", #x, cudaGetErrorString(e__));   \
+            st = cuda_status(e__, #x);                                          \
             goto done;                                                          \
         }                                                                       \
     } while (0)

@@ -6,9 +6,11 @@
 //   1. count labels per vertex (atomic histogram)
 //   2. exclusive scan -> offsets
 //   3. scatter (hubpos << 32 | dist) into each vertex's segment
-//   4. sort every segment by hubpos (= descending R of the hub) in shared
-//      memory: one warp per segment up to 32 labels, one CTA per segment up
-//      to MAX_SEGMENT labels (bitonic networks)
+//   4. sort every segment by hubpos (= descending R of the hub): one warp per
+//      segment up to 32 labels, one CTA per segment up to MAX_SEGMENT labels
+//      (bitonic networks in shared memory); a longer segment (one CTA each) is
+//      sorted in chunks in shared memory, then the sorted runs are merged
+//      pairwise in global memory
 //   5. split into hub (caller id), hubpos and dist arrays
 #include "chl_common.cuh"
 
@@ -19,7 +21,8 @@ cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cu
 
 namespace {
 
-constexpr uint32_t MAX_SEGMENT = 16384;
+constexpr uint32_t MAX_SEGMENT = 16384;  // longest segment sorted in shared memory at once
+constexpr uint32_t LONG_CHUNK = 4096;    // chunk of a longer segment sorted in shared memory
 
 __global__ void count_kernel(uint64_t T, const uint32_t *v, uint64_t *cnt) {
     for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < T;
@@ -92,10 +95,10 @@ __global__ void scatter_kernel(uint64_t T, const uint32_t *v, const uint32_t *h,
     }
 }
 
-// classify segments by length into three work lists; record the longest
+// classify segments by length into four work lists; record the longest
 __global__ void classify_kernel(uint32_t n, const uint64_t *off, uint32_t *small_list,
-                                uint32_t *mid_list, uint32_t *big_list, uint32_t *counts,
-                                unsigned long long *max_len) {
+                                uint32_t *mid_list, uint32_t *big_list, uint32_t *long_list,
+                                uint32_t *counts, unsigned long long *max_len) {
     for (uint64_t v = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; v < n;
          v += uint64_t(gridDim.x) * blockDim.x) {
         const uint64_t len = off[v + 1] - off[v];
@@ -104,6 +107,75 @@ __global__ void classify_kernel(uint32_t n, const uint64_t *off, uint32_t *small
         if (len <= 32) small_list[atomicAdd(&counts[0], 1u)] = uint32_t(v);
         else if (len <= 1024) mid_list[atomicAdd(&counts[1], 1u)] = uint32_t(v);
         else if (len <= MAX_SEGMENT) big_list[atomicAdd(&counts[2], 1u)] = uint32_t(v);
+        else long_list[atomicAdd(&counts[3], 1u)] = uint32_t(v);
+    }
+}
+
+// One CTA per segment longer than MAX_SEGMENT: its chunks of LONG_CHUNK keys
+// are sorted in shared memory (bitonic), then runs of width w, 2w, 4w, ...
+// are merged pairwise between tmp and tmp2 (each thread writes an equal share
+// of a merged pair, starting where the merge path of its first output crosses
+// the two runs); the sorted segment ends in tmp. Keys (hubpos << 32 | dist)
+// are distinct within a segment (one label per hub), so the order is unique.
+__global__ void __launch_bounds__(1024) sort_long_kernel(const uint32_t *list, const uint32_t *count,
+                                                         const uint64_t *off, uint64_t *tmp,
+                                                         uint64_t *tmp2) {
+    __shared__ uint64_t sm[LONG_CHUNK];
+    const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    for (uint32_t sidx = blockIdx.x; sidx < *count; sidx += gridDim.x) {
+        const uint32_t v = list[sidx];
+        const uint64_t a = off[v], len = off[v + 1] - a;
+        for (uint64_t c0 = 0; c0 < len; c0 += LONG_CHUNK) {
+            const uint32_t cl = uint32_t(len - c0 < LONG_CHUNK ? len - c0 : LONG_CHUNK);
+            for (uint32_t i = tid; i < LONG_CHUNK; i += nt) sm[i] = i < cl ? tmp[a + c0 + i] : ~0ull;
+            __syncthreads();
+            for (uint32_t k = 2; k <= LONG_CHUNK; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t i = tid; i < LONG_CHUNK; i += nt) {
+                        const uint32_t ix = i ^ j;
+                        if (ix > i) {
+                            const uint64_t x = sm[i], y = sm[ix];
+                            if ((x > y) == ((i & k) == 0)) {
+                                sm[i] = y;
+                                sm[ix] = x;
+                            }
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            for (uint32_t i = tid; i < cl; i += nt) tmp[a + c0 + i] = sm[i];
+            __syncthreads();
+        }
+        uint64_t *src = tmp + a, *dst = tmp2 + a;
+        for (uint64_t w = LONG_CHUNK; w < len; w *= 2) {
+            for (uint64_t p0 = 0; p0 < len; p0 += 2 * w) {
+                const uint64_t na = len - p0 < w ? len - p0 : w;
+                const uint64_t nb = len - p0 > w ? (len - p0 - w < w ? len - p0 - w : w) : 0;
+                const uint64_t m = na + nb;
+                const uint64_t *A = src + p0, *B = A + na;
+                const uint64_t k0 = m * tid / nt, k1 = m * (tid + 1) / nt;
+                if (k0 >= k1) continue;
+                // i = keys of A among the first k0 outputs (smallest i with A[i] > B[k0 - i - 1])
+                uint64_t lo = k0 > nb ? k0 - nb : 0, hi = k0 < na ? k0 : na;
+                while (lo < hi) {
+                    const uint64_t mid = (lo + hi) >> 1;
+                    if (A[mid] <= B[k0 - mid - 1]) lo = mid + 1; else hi = mid;
+                }
+                uint64_t i = lo, j = k0 - lo;
+                for (uint64_t k = k0; k < k1; ++k) {
+                    const bool take_a = j >= nb || (i < na && A[i] <= B[j]);
+                    dst[p0 + k] = take_a ? A[i++] : B[j++];
+                }
+            }
+            __syncthreads();
+            uint64_t *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != tmp + a)
+            for (uint64_t i = tid; i < len; i += nt) tmp[a + i] = src[i];
+        __syncthreads();
     }
 }
 
@@ -179,7 +251,8 @@ __global__ void split_kernel(uint64_t T, const uint64_t *tmp, const uint32_t *ve
 
 int grid_for(uint64_t work, int tpb) {
     uint64_t b = (work + tpb - 1) / tpb;
-    if (b > 152 * 32) b = 152 * 32;
+    const uint64_t cap = uint64_t(device_sms()) * 32;
+    if (b > cap) b = cap;
     if (b < 1) b = 1;
     return int(b);
 }
@@ -196,10 +269,11 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
                             const uint32_t *in_d, const uint32_t *vert_at, LabelCSR &out,
                             int *too_long, cudaStream_t s, int *launches) {
     cudaError_t e = cudaSuccess;
-    uint64_t *cnt = nullptr, *tmp = nullptr;
+    uint64_t *cnt = nullptr, *tmp = nullptr, *tmp2 = nullptr;
     uint32_t *lists = nullptr, *counts = nullptr;
     unsigned long long *maxlen = nullptr;
     unsigned long long hmax = 0;
+    const int sms = device_sms();
     *too_long = 0;
     out = LabelCSR{};
     const size_t Tb = (T ? T : 1);
@@ -209,7 +283,7 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
     CKE(cudaMallocAsync(&out.dist, Tb * sizeof(uint32_t), s));
     CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
     CKE(cudaMallocAsync(&tmp, Tb * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&lists, 3 * size_t(n) * sizeof(uint32_t), s));
+    CKE(cudaMallocAsync(&lists, 4 * size_t(n) * sizeof(uint32_t), s));
     CKE(cudaMallocAsync(&counts, 4 * sizeof(uint32_t), s));
     CKE(cudaMallocAsync(&maxlen, sizeof(unsigned long long), s));
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
@@ -222,30 +296,29 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
     scatter_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, in_h, in_d, out.offsets, cnt, tmp);
     classify_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, out.offsets, lists, lists + n,
-                                                     lists + 2 * size_t(n), counts, maxlen);
+                                                     lists + 2 * size_t(n), lists + 3 * size_t(n),
+                                                     counts, maxlen);
     *launches += 2;
     CKE(cudaGetLastError());
     CKE(cudaMemcpyAsync(&hmax, maxlen, sizeof(hmax), cudaMemcpyDeviceToHost, s));
     CKE(cudaStreamSynchronize(s));
-    if (hmax > MAX_SEGMENT) {
-        *too_long = 1;
-        goto done;
-    }
-    sort_small_kernel<<<152 * 8, 256, 0, s>>>(lists, counts, out.offsets, tmp);
-    sort_block_kernel<256><<<152 * 8, 256, 1024 * sizeof(uint64_t), s>>>(lists + n, counts + 1,
+    sort_small_kernel<<<sms * 8, 256, 0, s>>>(lists, counts, out.offsets, tmp);
+    sort_block_kernel<256><<<sms * 8, 256, 1024 * sizeof(uint64_t), s>>>(lists + n, counts + 1,
                                                                          out.offsets, tmp);
     *launches += 2;
     if (hmax > 1024) {
-        static bool attr_set = false;
-        if (!attr_set) {
-            CKE(cudaFuncSetAttribute(sort_block_kernel<1024>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     int(MAX_SEGMENT * sizeof(uint64_t))));
-            attr_set = true;
-        }
-        sort_block_kernel<1024><<<152, 1024, MAX_SEGMENT * sizeof(uint64_t), s>>>(
+        // the attribute belongs to the current device: set on every call
+        CKE(cudaFuncSetAttribute(sort_block_kernel<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(MAX_SEGMENT * sizeof(uint64_t))));
+        sort_block_kernel<1024><<<sms, 1024, MAX_SEGMENT * sizeof(uint64_t), s>>>(
             lists + 2 * size_t(n), counts + 2, out.offsets, tmp);
         *launches += 1;
+    }
+    if (hmax > MAX_SEGMENT) {
+        CKE(cudaMallocAsync(&tmp2, Tb * sizeof(uint64_t), s));
+        sort_long_kernel<<<sms, 1024, 0, s>>>(lists + 3 * size_t(n), counts + 3, out.offsets, tmp, tmp2);
+        *launches += 1;
+        CKE(cudaGetLastError());
     }
     split_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, tmp, vert_at, out.hub, out.hubpos, out.dist);
     *launches += 1;
@@ -253,6 +326,7 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
 done:
     if (cnt) cudaFreeAsync(cnt, s);
     if (tmp) cudaFreeAsync(tmp, s);
+    if (tmp2) cudaFreeAsync(tmp2, s);
     if (lists) cudaFreeAsync(lists, s);
     if (counts) cudaFreeAsync(counts, s);
     if (maxlen) cudaFreeAsync(maxlen, s);

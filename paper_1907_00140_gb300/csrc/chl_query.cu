@@ -250,7 +250,7 @@ cudaError_t launch_paths(uint32_t n, const uint64_t *offsets, const uint32_t *hu
                          uint32_t *lens, int *bad, cudaStream_t s) {
     if (q == 0) return cudaSuccess;
     uint64_t blocks = (q * 32 + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > uint64_t(device_sms()) * 64) blocks = uint64_t(device_sms()) * 64;
     paths_kernel<<<unsigned(blocks), 256, 0, s>>>(n, offsets, hubpos, dist, hub, parent, pairs, q,
                                                    max_len, paths, lens, bad);
     return cudaGetLastError();
@@ -261,7 +261,7 @@ cudaError_t launch_query(uint32_t n, const uint64_t *offsets, const uint32_t *hu
                          int *bad, cudaStream_t s) {
     if (q == 0) return cudaSuccess;
     uint64_t blocks = (q * 32 + 255) / 256;
-    if (blocks > 152 * 64) blocks = 152 * 64;
+    if (blocks > uint64_t(device_sms()) * 64) blocks = uint64_t(device_sms()) * 64;
     query_kernel<<<unsigned(blocks), 256, 0, s>>>(n, offsets, hubpos, dist, pairs, q, out, bad);
     return cudaGetLastError();
 }

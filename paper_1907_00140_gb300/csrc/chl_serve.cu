@@ -84,12 +84,14 @@ struct Slot {
     std::vector<Part> parts;
     uint64_t count = 0, cap = 0;             // pairs in the batch, its bucket size
     bool busy = false;
+    cudaError_t err = cudaSuccess;           // the batch's launch failed with this
 };
 
 struct Replay {
     bool active = false;
     uint64_t n = 0, next = 0;
     std::atomic<uint64_t> finished{0};
+    std::atomic<int> failed{0};  // some batch of the replay failed on the device
     Clock::time_point start;
     const double *arrival = nullptr;
     const uint32_t *set_of = nullptr;
@@ -124,6 +126,10 @@ struct chl_server {
     std::mutex replay_mu;  // one replay at a time
     uint64_t running_est = 0;
     chl_server_stats st{};
+    // fault injection on the host (tests): the batch launched as number
+    // fail_batch (1-based; CHL_FAULT_QUERY_BATCH in the environment at
+    // creation) is not launched and reports a launch failure instead
+    uint64_t fail_batch = 0;
     std::thread batcher;
     std::vector<std::thread> builders;
 
@@ -133,22 +139,27 @@ struct chl_server {
     bool launch(Slot &sl);
 };
 
-// scatter a finished slot's answers; returns true if it was busy and is now free
+// scatter a finished slot's answers; returns true if it was busy and is now
+// free. A batch whose launch or event reports an error (anything but "not
+// ready") is finished as failed: its requests get CHL_ECUDA, its replayed
+// answers UINT32_MAX, and the slot is free again.
 bool chl_server::retire(Slot &sl, bool block) {
     if (!sl.busy) return false;
-    if (block) {
-        if (cudaEventSynchronize(sl.ev) != cudaSuccess) return false;
-    } else if (cudaEventQuery(sl.ev) != cudaSuccess) {
-        return false;
+    cudaError_t e = sl.err;
+    if (e == cudaSuccess) {
+        e = block ? cudaEventSynchronize(sl.ev) : cudaEventQuery(sl.ev);
+        if (e == cudaErrorNotReady) return false;
     }
+    const bool failed = e != cudaSuccess;
     const Clock::time_point now = Clock::now();
     int bad = 0;
     // the flag was copied out with the answers (4 bytes after the bucket)
-    std::memcpy(&bad, sl.h_out + sl.cap, sizeof(int));
+    if (!failed) std::memcpy(&bad, sl.h_out + sl.cap, sizeof(int));
     std::vector<Req *> finished;
     uint64_t replayed = 0;
     for (const Part &pt : sl.parts) {
-        std::memcpy(pt.out, sl.h_out + pt.off, pt.count * 4);
+        if (failed) std::memset(pt.out, 0xFF, pt.count * 4);
+        else std::memcpy(pt.out, sl.h_out + pt.off, pt.count * 4);
         if (pt.req) {
             finished.push_back(pt.req);
         } else {
@@ -156,13 +167,17 @@ bool chl_server::retire(Slot &sl, bool block) {
             ++replayed;
         }
     }
+    if (failed && replayed) rp.failed.store(1, std::memory_order_relaxed);
     {
         std::lock_guard<std::mutex> lk(mu);
         if (replayed) rp.last_done = now;
         for (Req *r : finished) {
             r->t_done = now;
             r->done = true;
-            if (bad) {
+            if (failed) {
+                r->st = CHL_ECUDA;
+                r->err = std::string("query batch failed: ") + cudaGetErrorString(e);
+            } else if (bad) {
                 r->st = CHL_EINVAL;
                 r->err = "a query vertex id is out of range";
             }
@@ -174,6 +189,7 @@ bool chl_server::retire(Slot &sl, bool block) {
     sl.parts.clear();
     sl.count = 0;
     sl.busy = false;
+    sl.err = cudaSuccess;
     return true;
 }
 
@@ -228,8 +244,15 @@ bool chl_server::launch(Slot &sl) {
     sl.count = used;
     sl.cap = B;
     if (B <= ZERO_COPY_MAX) sl.h_out[B] = 0;  // the kernel sets it on a bad id
-    cudaGraphLaunch(sl.graph[b], sl.s);
-    cudaEventRecord(sl.ev, sl.s);
+    uint64_t nth = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        nth = st.batches + 1;
+    }
+    cudaError_t e = nth == fail_batch ? cudaErrorLaunchFailure : cudaGraphLaunch(sl.graph[b], sl.s);
+    if (e == cudaSuccess) e = cudaEventRecord(sl.ev, sl.s);
+    if (e != cudaSuccess) (void)cudaGetLastError();  // not left for a later check to find
+    sl.err = e;  // retire() finishes a failed batch as failed
     sl.busy = true;
     {
         std::lock_guard<std::mutex> lk(mu);
@@ -342,6 +365,7 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
     if (!o.build_workers) o.build_workers = 2;
     chl_server *S = new (std::nothrow) chl_server;
     if (!S) return set_error(CHL_ENOMEM, "host allocation failed");
+    if (const char *f = std::getenv("CHL_FAULT_QUERY_BATCH")) S->fail_batch = std::strtoull(f, nullptr, 10);
     cudaError_t e = cudaGetDevice(&S->device);
     if (!e) e = cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
     if (!o.build_slots) o.build_slots = S->sms > 32 ? S->sms - 16 : S->sms;
@@ -403,8 +427,7 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
     }
     if (e) {
         chl_server_destroy(S);
-        return set_error(e == cudaErrorMemoryAllocation ? CHL_ENOMEM : CHL_ECUDA, "server setup: %s",
-                         cudaGetErrorString(e));
+        return cuda_status(e, "server setup");
     }
     S->batcher = std::thread([S] { S->run_batcher(); });
     for (int k = 0; k < o.build_workers; ++k) S->builders.emplace_back([S] { S->run_builder(); });
@@ -414,6 +437,9 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
 
 extern "C" chl_status chl_server_add_set(chl_server *S, const chl_labels *L, uint32_t *set_id) {
     if (!S || !L || !set_id) return set_error(CHL_EINVAL, "server, labels or set_id is NULL");
+    if (L->device != S->device)
+        return set_error(CHL_EINVAL, "labels live on device %d, the server on device %d", L->device,
+                         S->device);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->sets.size() >= MAX_SETS) return set_error(CHL_EINVAL, "too many label sets");
     QuerySet q{L->n, L->offsets, L->hubpos, L->dist};
@@ -422,7 +448,7 @@ extern "C" chl_status chl_server_add_set(chl_server *S, const chl_labels *L, uin
     // published before any query on it can be submitted (the id is returned after)
     cudaError_t e = cudaMemcpy(S->d_sets + k, &q, sizeof(q), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(S->d_nsets, &k1, sizeof(k1), cudaMemcpyHostToDevice);
-    if (e) return set_error(CHL_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e));
+    if (e) return cuda_status(e, "cudaMemcpy");
     S->sets.push_back(q);
     *set_id = k;
     return CHL_OK;
@@ -548,6 +574,7 @@ extern "C" chl_status chl_server_replay(chl_server *S, uint64_t nreq, const doub
         S->rp.lat = latency_s;
         S->rp.start = Clock::now();
         S->rp.last_done = S->rp.start;
+        S->rp.failed.store(0);
         S->rp.active = true;
     }
     S->cv_q.notify_one();
@@ -555,6 +582,7 @@ extern "C" chl_status chl_server_replay(chl_server *S, uint64_t nreq, const doub
     std::lock_guard<std::mutex> lk(S->mu);
     S->rp.active = false;
     if (wall_s) *wall_s = secs(S->rp.last_done - S->rp.start);
+    if (S->rp.failed.load()) return set_error(CHL_ECUDA, "a query batch of the replay failed on the device");
     return CHL_OK;
 }
 

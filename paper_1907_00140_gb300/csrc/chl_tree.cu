@@ -47,7 +47,6 @@
 // buffer.
 #include <algorithm>
 #include <cstdio>
-#include <cstdlib>
 
 #include "chl_common.cuh"
 
@@ -55,7 +54,6 @@ namespace chl {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr uint32_t MAX_ROUNDS_PER_TREE = 1u << 26;
 constexpr uint32_t NWIN_MAX = 64;
 constexpr int UNROLL = 4;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
@@ -1023,7 +1021,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                                      parity);  // ends with a barrier
                 if (S.abort) break;
                 ++rounds_all;
-                if (++rounds > MAX_ROUNDS_PER_TREE) {
+                if (++rounds > p.round_limit) {
                     if (threadIdx.x == 0) atomicExch(&p.flags[0], ERR_ROUND_LIMIT);
                     break;
                 }
@@ -1306,13 +1304,11 @@ uint32_t plant_dyn_budget(int tpt) {
     }
 }
 
-void plant_smem_split(int tpt, uint32_t n, bool staged, uint32_t *fin_words, uint32_t *stage_bytes) {
+void plant_smem_split(int tpt, uint32_t n, uint32_t stage_want, uint32_t *fin_words,
+                      uint32_t *stage_bytes) {
     const uint32_t budget = plant_dyn_budget(tpt);
     const uint32_t want = (n + 31) / 32;
-    uint32_t stage = 0;
-    if (staged) {
-        if (const char *x = std::getenv("CHL_STAGE_KB")) stage = std::min<uint32_t>(budget / 2, uint32_t(atoi(x)) << 10) & ~127u;
-    }
+    const uint32_t stage = std::min<uint32_t>(budget / 2, stage_want) & ~127u;
     const uint32_t room = budget > stage + 128 ? budget - stage - 128 : 0;
     uint32_t fw = std::min<uint32_t>(want, room / 4);
     if (fw < want) fw &= ~31u;
@@ -1344,7 +1340,7 @@ cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const 
                             uint32_t stride, uint32_t hubs, cudaStream_t s) {
     if (!count) return cudaSuccess;
     unsigned long long blocks = (count + 255) / 256;
-    if (blocks > 152ull * 32) blocks = 152ull * 32;
+    if (blocks > uint64_t(device_sms()) * 32) blocks = uint64_t(device_sms()) * 32;
     clt_fill_kernel<<<unsigned(blocks), 256, 0, s>>>(out_v, out_h, out_d, count, pos_of, hc, stride,
                                                      hubs);
     return cudaGetLastError();

@@ -114,3 +114,32 @@ def test_build_options_are_marshalled_by_field_type(monkeypatch):
     assert abs(o.psi_threshold - 0.5) < 1e-7 and o.bucket_delta == 7 and o.slots == 3
     with pytest.raises(TypeError):
         chl.build_labels(G, rank, no_such_option=1)
+
+
+class LabelsMirror(C.Structure):
+    """The library's handle layout (struct chl_labels in csrc/chl_common.cuh),
+    for forging handles in tests only."""
+    _fields_ = [("n", C.c_uint32), ("total", C.c_uint64), ("offsets", C.c_void_p),
+                ("hub", C.c_void_p), ("hubpos", C.c_void_p), ("dist", C.c_void_p),
+                ("parent", C.c_void_p), ("bytes", C.c_uint64), ("stats", chl.chl_build_stats),
+                ("device", C.c_int)]
+
+
+def test_forged_handle_is_refused_before_use(lib):
+    """Every call that takes labels checks the handle's device first: a handle
+    whose arrays are all null and whose device is not the current one comes
+    back with an error (CHL_ECUDA without a GPU, CHL_EINVAL with one) instead
+    of a dereference."""
+    import numpy as np
+    forged = LabelsMirror(n=4, total=0, parent=1, device=12345)
+    h = C.addressof(forged)
+    pairs = np.array([[0, 1]], np.uint32)
+    out = np.zeros(1, np.uint32)
+    offs = np.zeros(5, np.uint64)
+    lens = np.zeros(1, np.uint32)
+    for st in (lib.chl_query(h, pairs.ctypes.data, 1, out.ctypes.data, chl.CHL_MEM_HOST, None),
+               lib.chl_query_noalloc(h, pairs.ctypes.data, 1, out.ctypes.data, chl.CHL_MEM_HOST, None),
+               lib.chl_path(h, pairs.ctypes.data, 1, 0, None, lens.ctypes.data, chl.CHL_MEM_HOST, None),
+               lib.chl_labels_copy(h, offs.ctypes.data, None, None, chl.CHL_MEM_HOST, None),
+               lib.chl_labels_parents(h, out.ctypes.data, chl.CHL_MEM_HOST, None)):
+        assert st in (chl.CHL_EINVAL, chl.CHL_ECUDA)

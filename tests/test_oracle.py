@@ -530,3 +530,51 @@ def test_paths_are_canonical_shortest_paths(name, g, rank):
         on_sp = np.where(D[u, :] + D[:, v] == D[u, v])[0]
         top = int(on_sp[np.argmax(rank[on_sp])])
         assert top in path
+
+
+# ------------------------------------------------------------------ closed form: K_{2,m}
+def double_star_closed_form(g, rank):
+    """Labels of W.double_star by hand: c (vertex 0, lowest rank) reaches each
+    leaf l directly at w_l, and no other vertex lies on that edge, so l is its
+    hub; t (top rank) lies on every other shortest path (each leaf-to-leaf path
+    through c has a twin of equal length through t), so it is the only other
+    hub anywhere. L_c = t at 2 min(w), the leaves by rank descending, c; L_t =
+    t; L_l = t at w_l, l."""
+    m = g.n - 2
+    w = g.w[:m].astype(np.uint64)  # c's row: leaves 2..m+1 in order
+    leaves = np.arange(2, g.n)
+    by_rank = leaves[np.argsort(-rank[leaves].astype(np.int64), kind="stable")]
+    off = [0, m + 2, m + 3]
+    hub = [1, *by_rank, 0, 1]
+    dist = [2 * int(w.min()), *[int(w[l - 2]) for l in by_rank], 0, 0]
+    for l in leaves:
+        off.append(off[-1] + 2)
+        hub += [1, int(l)]
+        dist += [int(w[l - 2]), 0]
+    return np.array(off, np.uint64), np.array(hub, np.uint32), np.array(dist, np.uint32)
+
+
+@pytest.mark.parametrize("m,seed", [(1, 1), (7, 2), (300, 3)])
+def test_double_star_closed_form(m, seed):
+    g, rank = W.double_star(m, seed)
+    off, hub, dist = double_star_closed_form(g, rank)
+    for method in ("canonical", "plant", "pll"):
+        L = O.build_labels(g, rank, method)
+        assert np.array_equal(L.offsets, off) and np.array_equal(L.hub, hub), method
+        assert np.array_equal(L.dist, dist), method
+
+
+def test_phased_root_prefix_is_hub_partition():
+    """A phased build that stops after the top R roots gives exactly the
+    canonical labels whose hub ranks among the top R (trees are independent,
+    Sec. 5.2), whatever the schedule before R."""
+    g, rank = W.load("ba2k")
+    full = O.build_labels(g, rank, "canonical")
+    pos = g.n - 1 - rank.astype(np.int64)
+    for ends in ([37], [8, 16, 37], [1, 2, 3, 500], [304, 608, 1216, 1999]):
+        part = O.build_labels_phased(g, rank, ends, threads=3)
+        keep = pos[full.hub] < ends[-1]
+        assert np.array_equal(part.hub, full.hub[keep]), ends
+        assert np.array_equal(part.dist, full.dist[keep]), ends
+        cnt = np.add.reduceat(keep.astype(np.int64), full.offsets[:-1].astype(np.int64)) if full.total else 0
+        assert np.array_equal(np.diff(part.offsets.astype(np.int64)), np.where(np.diff(full.offsets.astype(np.int64)) > 0, cnt, 0)), ends

@@ -173,6 +173,32 @@ def unit_doubles(count: int, seed: int, stream: int = 0) -> np.ndarray:
     return out
 
 
+def double_star(m: int, seed: int) -> tuple:
+    """K_{2,m} with its ranking: vertex 0 (c, lowest rank) and vertex 1 (t,
+    highest rank) are both joined to the m leaves 2..m+1, and leaf l's two
+    edges carry the same weight U{1..100}, so every leaf-to-leaf shortest path
+    has a twin through t. The leaves' ranks are a seeded permutation of
+    [1, m]. Under this ranking c is the one vertex with a label list of length
+    m + 2 (every leaf, t and itself); the whole labeling has about 3m labels.
+    Returns (graph, rank)."""
+    n = m + 2
+    w = (1 + np.floor(unit_doubles(m, seed, 0) * 100)).astype(np.uint32)
+    perm = np.argsort(unit_doubles(m, seed, 1), kind="stable").astype(np.uint32)
+    deg = np.concatenate([[m, m], np.full(m, 2)]).astype(np.uint64)
+    row = np.concatenate([[0], np.cumsum(deg)]).astype(np.uint64)
+    col = np.empty(int(row[-1]), np.uint32)
+    ww = np.empty(int(row[-1]), np.uint32)
+    leaves = np.arange(2, n, dtype=np.uint32)
+    col[0:m], ww[0:m] = leaves, w          # c's row
+    col[m:2 * m], ww[m:2 * m] = leaves, w  # t's row
+    col[2 * m::2], col[2 * m + 1::2] = 0, 1  # each leaf: c, then t
+    ww[2 * m::2], ww[2 * m + 1::2] = w, w
+    rank = np.empty(n, np.uint32)
+    rank[0], rank[1] = 0, n - 1
+    rank[2:] = 1 + perm
+    return Graph(n, row, col, ww, f"double_star_m{m}", {"seed": seed}), rank
+
+
 # ---------------------------------------------------------------- named workloads
 # The five workloads of the benchmark plan. Each returns (graph, rank).
 
