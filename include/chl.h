@@ -370,6 +370,42 @@ chl_status chl_query_noalloc(const chl_labels *L, const uint32_t *pairs, uint64_
                              chl_mem mem, void *stream);
 
 /*
+ * chl_query_partitioned — PPSD queries over labels held as hub partitions: the
+ * paper's fully distributed query mode (QFDL, Sec. 6: every node holds the
+ * labels of its own hubs; each computes the partial minimum of
+ * d(u,h) + d(v,h) over its hubs h in L_u and L_v, and a min-reduction combines
+ * them) on one GPU. parts[k] holds the labels whose hubs lie in one rank
+ * range (chl_build with root_begin/root_end); trees are independent (Sec.
+ * 5.2), so disjoint ranges covering [0, n) partition the labeling by hub and
+ * the answer equals chl_query's on the whole labeling.
+ *   parts, nparts  1 <= nparts <= CHL_MAX_PARTS labels objects over the same n
+ *                  vertices, all on the current device (caller keeps them)
+ *   pairs, q, out, mem, stream  as for chl_query
+ * Each pair is answered by one warp that merges the pair's partial lists of
+ * every part and keeps the minimum.
+ * Errors: CHL_EINVAL (NULL, nparts out of range, parts of different n or on
+ * another device, a vertex id >= n), CHL_ENOMEM, CHL_ECUDA.
+ */
+#define CHL_MAX_PARTS 64
+chl_status chl_query_partitioned(const chl_labels *const *parts, uint32_t nparts, const uint32_t *pairs,
+                                 uint64_t q, uint32_t *out, chl_mem mem, void *stream);
+
+/*
+ * chl_query_grouped — the same answers as chl_query, with the batch answered
+ * in grouped order: the paper's distributed query mode with labels owned by
+ * vertex (QDOL, Sec. 6) sorts a batch by the vertex partitions its pairs need
+ * and rearranges the answers back; on one GPU the partitions are 64 blocks of
+ * vertex ids, a pair's key is the block pair (min(u,v), max(u,v)), the batch is
+ * counting-sorted by key on the GPU, answered in that order (pairs that read
+ * the lists of the same two blocks run together) and every answer is written
+ * to its pair's slot in arrival order.
+ *   L, pairs, q, out, mem, stream  as for chl_query (q < 2^32)
+ * Errors: as chl_query.
+ */
+chl_status chl_query_grouped(const chl_labels *L, const uint32_t *pairs, uint64_t q, uint32_t *out,
+                             chl_mem mem, void *stream);
+
+/*
  * Copy the SPT parent of every label (caller vertex ids, [T], aligned with the
  * hub/dist arrays of chl_labels_copy) to host or device memory (mem).
  * CHL_EINVAL when L was built without CHL_FLAG_PARENTS.
@@ -438,6 +474,10 @@ typedef struct chl_server chl_server;
  *                      so that query batches keep SMs while trees run.
  *   build_budget       bytes that running builds may hold by their estimate
  *                      (default: free device memory at creation minus 4 GiB)
+ *   query_order        0 = pairs of a batch answered in arrival order
+ *                      (default); 1 = grouped: a batch larger than 4096 pairs
+ *                      is sorted on the GPU by the vertex blocks its pairs
+ *                      read (as chl_query_grouped) before it is answered
  */
 typedef struct {
     int32_t query_slots;
@@ -446,6 +486,7 @@ typedef struct {
     int32_t build_workers;
     int32_t build_slots;
     uint64_t build_budget;
+    int32_t query_order;
 } chl_server_opts;
 
 /* Counters since creation: batches launched, pairs answered, largest batch,
@@ -467,6 +508,15 @@ chl_status chl_server_create(const chl_server_opts *opts, chl_server **out);
    at most 4096 sets). L stays owned by the caller and must outlive every query
    on it. Call before submitting queries on it. */
 chl_status chl_server_add_set(chl_server *S, const chl_labels *L, uint32_t *set_id);
+
+/* Make a label set held as hub partitions resident (as chl_query_partitioned:
+   parts[k] are labels of disjoint hub ranges over the same n vertices); its
+   queries are answered by the minimum over the parts. The parts stay owned by
+   the caller and must outlive every query on the set. Errors: CHL_EINVAL (NULL,
+   nparts outside [1, CHL_MAX_PARTS], parts of different n or on another
+   device, too many sets), CHL_ECUDA. */
+chl_status chl_server_add_partitioned_set(chl_server *S, const chl_labels *const *parts,
+                                          uint32_t nparts, uint32_t *set_id);
 
 /* Queue `count` pairs (host uint32 [count][2], caller vertex ids of the set)
    for answers into host `out[count]`; both arrays must stay valid until the

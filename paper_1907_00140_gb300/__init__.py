@@ -27,7 +27,8 @@ __all__ = [
     "CHL_EOVERFLOW", "CHL_MEM_DEVICE", "CHL_MEM_HOST", "CHL_FLAG_WIDE_KEYS", "CHL_FLAG_PARENTS", "CHL_FLAG_NO_HYBRID", "CHL_FLAG_DENSE_ROOT_LABELS", "ChlError", "chl_csr", "chl_build_opts",
     "chl_build_stats", "chl_build", "chl_query", "chl_labels_info", "chl_labels_stats",
     "chl_labels_view", "chl_labels_copy", "chl_labels_free", "chl_last_error", "chl_version",
-    "chl_query_noalloc", "chl_tune", "chl_tune_report", "tune",
+    "chl_query_noalloc", "chl_query_partitioned", "chl_query_grouped", "query_partitioned",
+    "chl_tune", "chl_tune_report", "tune",
     "Labels", "build_labels", "query",
 ]
 
@@ -112,7 +113,7 @@ class chl_tune_report(C.Structure):
 class chl_server_opts(C.Structure):
     _fields_ = [("query_slots", C.c_int32), ("max_batch", C.c_uint64), ("batching", C.c_int32),
                 ("build_workers", C.c_int32), ("build_slots", C.c_int32),
-                ("build_budget", C.c_uint64)]
+                ("build_budget", C.c_uint64), ("query_order", C.c_int32)]
 
 
 class chl_server_stats(C.Structure):
@@ -167,6 +168,12 @@ def lib():
             L.chl_query.restype = i32
             L.chl_query_noalloc.argtypes = [vp, vp, u64, vp, i32, vp]
             L.chl_query_noalloc.restype = i32
+            L.chl_query_partitioned.argtypes = [C.POINTER(vp), u32, vp, u64, vp, i32, vp]
+            L.chl_query_partitioned.restype = i32
+            L.chl_query_grouped.argtypes = [vp, vp, u64, vp, i32, vp]
+            L.chl_query_grouped.restype = i32
+            L.chl_server_add_partitioned_set.argtypes = [vp, C.POINTER(vp), u32, C.POINTER(u32)]
+            L.chl_server_add_partitioned_set.restype = i32
             L.chl_labels_free.argtypes = [vp]
             L.chl_labels_free.restype = None
             L.chl_last_error.argtypes = []
@@ -253,6 +260,15 @@ def chl_query_noalloc(handle: int, pairs: int, q: int, out: int, mem: int, strea
     """chl_query without any allocation: at most 2^20 pairs per call, staged
     in one fixed device array that all calls share (see include/chl.h)."""
     _check(lib().chl_query_noalloc(handle, pairs, q, out, mem, stream))
+
+
+def chl_query_partitioned(handles, pairs: int, q: int, out: int, mem: int, stream: int):
+    arr = (C.c_void_p * len(handles))(*handles)
+    _check(lib().chl_query_partitioned(arr, len(handles), pairs, q, out, mem, stream))
+
+
+def chl_query_grouped(handle: int, pairs: int, q: int, out: int, mem: int, stream: int):
+    _check(lib().chl_query_grouped(handle, pairs, q, out, mem, stream))
 
 
 def chl_labels_free(handle: int):
@@ -357,19 +373,35 @@ class Labels:
                               _current_stream() if stream is None else stream))
         return out, lens
 
-    def query(self, pairs, out=None, stream: int | None = None):
-        """Distances for pairs [q,2] (numpy -> numpy, CUDA tensor -> CUDA tensor)."""
-        p, mem, keep = _ptr_mem(pairs, np.uint32)
-        q = (keep.numel() if _is_torch(keep) else keep.size) // 2
-        if out is None:
-            if mem == CHL_MEM_DEVICE:
-                import torch
-                out = torch.empty(q, dtype=torch.int32, device=keep.device)
-            else:
-                out = np.empty(q, np.uint32)
-        op = out.data_ptr() if _is_torch(out) else out.ctypes.data
-        chl_query(self.handle, p, q, op, mem, _current_stream() if stream is None else stream)
+    def query(self, pairs, out=None, stream: int | None = None, grouped: bool = False):
+        """Distances for pairs [q,2] (numpy -> numpy, CUDA tensor -> CUDA tensor);
+        grouped=True answers the batch in grouped order (chl_query_grouped)."""
+        p, mem, q, out, op = _query_args(pairs, out)
+        fn = chl_query_grouped if grouped else chl_query
+        fn(self.handle, p, q, op, mem, _current_stream() if stream is None else stream)
         return out
+
+
+def _query_args(pairs, out):
+    p, mem, keep = _ptr_mem(pairs, np.uint32)
+    q = (keep.numel() if _is_torch(keep) else keep.size) // 2
+    if out is None:
+        if mem == CHL_MEM_DEVICE:
+            import torch
+            out = torch.empty(q, dtype=torch.int32, device=keep.device)
+        else:
+            out = np.empty(q, np.uint32)
+    op = out.data_ptr() if _is_torch(out) else out.ctypes.data
+    return p, mem, q, out, op
+
+
+def query_partitioned(parts, pairs, out=None, stream: int | None = None):
+    """Distances over labels held as hub partitions (a list of Labels built
+    over disjoint root ranges): chl_query_partitioned."""
+    p, mem, q, out, op = _query_args(pairs, out)
+    chl_query_partitioned([L.handle for L in parts], p, q, op, mem,
+                          _current_stream() if stream is None else stream)
+    return out
 
 
 def _csr_args(g, rank):
@@ -448,6 +480,14 @@ class Server:
         k = C.c_uint32()
         _check(lib().chl_server_add_set(self.handle, labels.handle, C.byref(k)))
         self._keep[("set", k.value)] = labels
+        return k.value
+
+    def add_partitioned_set(self, parts) -> int:
+        """A label set held as hub partitions (Labels over disjoint root ranges)."""
+        k = C.c_uint32()
+        arr = (C.c_void_p * len(parts))(*[L.handle for L in parts])
+        _check(lib().chl_server_add_partitioned_set(self.handle, arr, len(parts), C.byref(k)))
+        self._keep[("set", k.value)] = list(parts)
         return k.value
 
     def submit_query(self, set_id: int, pairs) -> int:

@@ -803,6 +803,12 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     cudaEventElapsedTime(&ms_total, ev[0], ev[3]);
     cudaEventElapsedTime(&ms_tree, ev[1], ev[2]);
     cudaEventElapsedTime(&ms_sort, ev[2], ev[3]);
+    if (trace) {
+        float ms_prep = 0;
+        cudaEventElapsedTime(&ms_prep, ev[0], ev[1]);
+        std::fprintf(stderr, "chl build total %.3f ms: inputs, checks and buffers %.3f ms, phases %.3f ms, "
+                     "label sort %.3f ms\n", ms_total, ms_prep, ms_tree, ms_sort);
+    }
     if (with_table && hybrid) cudaEventElapsedTime(&ms_table, ev[5], ev[6]);
     else if (with_table) cudaEventElapsedTime(&ms_table, ev[1], ev[4]);
 
@@ -924,6 +930,98 @@ extern "C" chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint
     if (hbad) st = set_error(CHL_EINVAL, "a query vertex id is >= n");
 done:
     return st;
+}
+
+// ------------------------------------------------------------------ query modes
+namespace {
+
+// a batch over one set (plain or partitioned) through the multi-set kernel:
+// device pairs and answers, the set descriptor and a flag in device memory
+chl_status run_set_query(const QuerySet &set, const QuerySet *parts_h, uint32_t nparts,
+                         const uint32_t *pairs, uint64_t q, uint32_t *out, chl_mem mem, bool grouped,
+                         cudaStream_t s) {
+    chl_status st = CHL_OK;
+    DevBuf b_set, b_p, b_o, b_perm, b_scr;
+    b_set.s = b_p.s = b_o.s = b_perm.s = b_scr.s = s;
+    const uint32_t *dp = pairs;
+    uint32_t *dout = out;
+    int hbad = 0;
+    // [set][nsets, bad][parts]
+    const size_t hdr = sizeof(QuerySet) + 16;
+    std::vector<uint8_t> host(hdr + size_t(nparts) * sizeof(QuerySet));
+    QuerySet top = set;
+    uint8_t *base = nullptr;
+    CUDA_TRY(cudaMallocAsync(&b_set.p, host.size(), s));
+    base = static_cast<uint8_t *>(b_set.p);
+    if (nparts) top.parts = reinterpret_cast<const QuerySet *>(base + hdr);
+    std::memcpy(host.data(), &top, sizeof(QuerySet));
+    {
+        const uint32_t one = 1, zero = 0;
+        std::memcpy(host.data() + sizeof(QuerySet), &one, 4);
+        std::memcpy(host.data() + sizeof(QuerySet) + 4, &zero, 4);
+    }
+    if (nparts) std::memcpy(host.data() + hdr, parts_h, size_t(nparts) * sizeof(QuerySet));
+    CUDA_TRY(cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, s));
+    if (mem == CHL_MEM_HOST) {
+        CUDA_TRY(cudaMallocAsync(&b_p.p, q * 8, s));
+        CUDA_TRY(cudaMallocAsync(&b_o.p, q * 4, s));
+        CUDA_TRY(cudaMemcpyAsync(b_p.p, pairs, q * 8, cudaMemcpyHostToDevice, s));
+        dp = (const uint32_t *)b_p.p;
+        dout = (uint32_t *)b_o.p;
+    }
+    if (grouped) {
+        CUDA_TRY(cudaMallocAsync(&b_perm.p, q * 4, s));
+        CUDA_TRY(cudaMallocAsync(&b_scr.p, GROUP_SCRATCH_WORDS * 4, s));
+        CUDA_TRY(launch_group_order(reinterpret_cast<const QuerySet *>(base),
+                                    reinterpret_cast<const uint32_t *>(base + sizeof(QuerySet)), dp,
+                                    nullptr, q, (uint32_t *)b_scr.p, (uint32_t *)b_perm.p, s));
+    }
+    CUDA_TRY(launch_query_sets(reinterpret_cast<const QuerySet *>(base),
+                               reinterpret_cast<const uint32_t *>(base + sizeof(QuerySet)), dp, nullptr,
+                               grouped ? (const uint32_t *)b_perm.p : nullptr, q, dout,
+                               reinterpret_cast<int *>(base + sizeof(QuerySet) + 4), device_sms() * 64, s));
+    if (mem == CHL_MEM_HOST) CUDA_TRY(cudaMemcpyAsync(out, dout, q * 4, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(&hbad, base + sizeof(QuerySet) + 4, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (hbad) st = set_error(CHL_EINVAL, "a query vertex id is >= n");
+done:
+    return st;
+}
+
+}  // namespace
+
+extern "C" chl_status chl_query_partitioned(const chl_labels *const *parts, uint32_t nparts,
+                                            const uint32_t *pairs, uint64_t q, uint32_t *out, chl_mem mem,
+                                            void *stream) {
+    ENTER();
+    if (!parts) return set_error(CHL_EINVAL, "parts is NULL");
+    if (nparts < 1 || nparts > CHL_MAX_PARTS)
+        return set_error(CHL_EINVAL, "nparts must be in [1, %d]", CHL_MAX_PARTS);
+    std::vector<QuerySet> h(nparts);
+    for (uint32_t k = 0; k < nparts; ++k) {
+        if (!parts[k]) return set_error(CHL_EINVAL, "part %u is NULL", k);
+        CHECK_DEVICE(parts[k]);
+        if (parts[k]->n != parts[0]->n) return set_error(CHL_EINVAL, "parts cover different vertex counts");
+        h[k] = QuerySet{parts[k]->n, parts[k]->offsets, parts[k]->hubpos, parts[k]->dist, 0, nullptr};
+    }
+    if (q == 0) return CHL_OK;
+    if (!pairs || !out) return set_error(CHL_EINVAL, "pairs or out is NULL");
+    if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
+    const QuerySet set{parts[0]->n, nullptr, nullptr, nullptr, nparts, nullptr};
+    return run_set_query(set, h.data(), nparts, pairs, q, out, mem, false, (cudaStream_t)stream);
+}
+
+extern "C" chl_status chl_query_grouped(const chl_labels *L, const uint32_t *pairs, uint64_t q,
+                                        uint32_t *out, chl_mem mem, void *stream) {
+    ENTER();
+    if (!L) return set_error(CHL_EINVAL, "labels is NULL");
+    CHECK_DEVICE(L);
+    if (q == 0) return CHL_OK;
+    if (!pairs || !out) return set_error(CHL_EINVAL, "pairs or out is NULL");
+    if (mem != CHL_MEM_DEVICE && mem != CHL_MEM_HOST) return set_error(CHL_EINVAL, "unknown memory kind");
+    if (q > 0xFFFFFFFFull) return set_error(CHL_EINVAL, "chl_query_grouped takes fewer than 2^32 pairs");
+    const QuerySet set{L->n, L->offsets, L->hubpos, L->dist, 0, nullptr};
+    return run_set_query(set, nullptr, 0, pairs, q, out, mem, true, (cudaStream_t)stream);
 }
 
 extern "C" void chl_labels_free(chl_labels *L) {

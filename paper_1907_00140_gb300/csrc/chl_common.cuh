@@ -171,18 +171,30 @@ cudaError_t launch_paths(uint32_t n, const uint64_t *offsets, const uint32_t *hu
                          const uint32_t *dist, const uint32_t *hub, const uint32_t *parent,
                          const uint32_t *pairs, uint64_t q, uint32_t max_len, uint32_t *paths,
                          uint32_t *lens, int *bad, cudaStream_t s);
-// one resident label set as the query kernels read it
+// one resident label set as the query kernels read it: its lists, or (nparts
+// > 0) its hub partitions, a device array of nparts sets over the same n
+// vertices whose answer is the minimum of theirs
 struct QuerySet {
     uint32_t n;
     const uint64_t *offsets;
     const uint32_t *hubpos;
     const uint32_t *dist;
+    uint32_t nparts;
+    const QuerySet *parts;
 };
 // a batch whose pair i asks set set_of[i] (sets: device array, *nsets in device
-// memory; set id 0xFFFF = padding, skipped)
+// memory; set id 0xFFFF = padding, skipped); perm (or null) is the order in
+// which the pairs are answered (launch_group_order)
 cudaError_t launch_query_sets(const QuerySet *sets, const uint32_t *nsets, const uint32_t *pairs,
-                              const uint16_t *set_of, uint64_t q, uint32_t *out, int *bad,
-                              int max_blocks, cudaStream_t s);
+                              const uint16_t *set_of, const uint32_t *perm, uint64_t q, uint32_t *out,
+                              int *bad, int max_blocks, cudaStream_t s);
+// grouped order of a batch: perm[0..q) = the pairs sorted by the block pair of
+// their two vertices (64 blocks per set); set_of may be null (all set 0);
+// scratch holds 4096 counters
+constexpr uint32_t GROUP_SCRATCH_WORDS = 4096;
+cudaError_t launch_group_order(const QuerySet *sets, const uint32_t *nsets, const uint32_t *pairs,
+                               const uint16_t *set_of, uint64_t q, uint32_t *scratch, uint32_t *perm,
+                               cudaStream_t s);
 
 // exclusive prefix sum of n uint64 values (out may alias in); chl_graph.cu
 cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,

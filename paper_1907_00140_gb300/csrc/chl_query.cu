@@ -205,18 +205,35 @@ __global__ void paths_kernel(uint32_t n, const uint64_t *__restrict__ off,
     }
 }
 
+// d(u, v) over a label set: its own lists, or, for a set held as hub
+// partitions (QFDL-style, Sec. 6: every partition holds the labels of a
+// disjoint hub range for all vertices), the minimum of the partial merges
+__device__ __forceinline__ uint32_t set_query(const QuerySet &S, uint32_t u, uint32_t v) {
+    if (!S.nparts) return merge_query(S.offsets, S.hubpos, S.dist, u, v);
+    uint32_t d = 0xFFFFFFFFu;
+    for (uint32_t k = 0; k < S.nparts; ++k) {
+        const QuerySet P = S.parts[k];
+        const uint32_t x = merge_query(P.offsets, P.hubpos, P.dist, u, v);
+        d = x < d ? x : d;
+    }
+    return d;
+}
+
 // a batch mixing label sets: pair i asks set set_of[i]
 // (the set count is read from device memory, so a captured launch stays valid
-// as sets are added; set id 0xFFFF marks padding that is skipped)
+// as sets are added; set id 0xFFFF marks padding that is skipped). With perm,
+// the j-th pair answered is perm[j] (grouped order); its answer still goes to
+// out[perm[j]].
 __global__ void query_sets_kernel(const QuerySet *__restrict__ sets, const uint32_t *nsets_p,
                                   const uint32_t *__restrict__ pairs,
-                                  const uint16_t *__restrict__ set_of, uint64_t q,
-                                  uint32_t *__restrict__ out, int *bad) {
+                                  const uint16_t *__restrict__ set_of, const uint32_t *__restrict__ perm,
+                                  uint64_t q, uint32_t *__restrict__ out, int *bad) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
     const uint32_t nsets = *nsets_p;
-    for (uint64_t i = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; i < q; i += warps) {
-        const uint32_t k = __ldg(&set_of[i]);
+    for (uint64_t j = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; j < q; j += warps) {
+        const uint64_t i = perm ? __ldg(&perm[j]) : j;
+        const uint32_t k = set_of ? __ldg(&set_of[i]) : 0u;
         if (k == 0xFFFFu) continue;
         const uint32_t u = __ldg(&pairs[2 * i]), v = __ldg(&pairs[2 * i + 1]);
         const QuerySet S = sets[k < nsets ? k : 0];
@@ -227,20 +244,115 @@ __global__ void query_sets_kernel(const QuerySet *__restrict__ sets, const uint3
             }
             continue;
         }
-        const uint32_t d = merge_query(S.offsets, S.hubpos, S.dist, u, v);
+        const uint32_t d = set_query(S, u, v);
         if (lane == 0) out[i] = d;
     }
 }
 
+// ---- grouped order (QDOL-style, Sec. 6: queries sorted and grouped by the
+// vertex partitions they touch, answers rearranged back into arrival order).
+// On one GPU a partition is a block of vertex ids: a pair's key is the block
+// pair (min(u, v), max(u, v)) over GROUP_BLOCKS blocks per label set, so pairs
+// that read the lists of the same two blocks run together. The order is a
+// counting sort by key: count, one-CTA exclusive scan, scatter of indices.
+// Pairs of an unknown set or with an id >= n go to key 0 (the query kernel
+// reports them).
+constexpr uint32_t GROUP_BLOCKS = 64;
+constexpr uint32_t GROUP_KEYS = GROUP_BLOCKS * GROUP_BLOCKS;
+
+__device__ __forceinline__ uint32_t group_key(const QuerySet *sets, uint32_t nsets, const uint32_t *pairs,
+                                              const uint16_t *set_of, uint64_t i) {
+    const uint32_t k = set_of ? __ldg(&set_of[i]) : 0;
+    if (k >= nsets) return 0;
+    const uint32_t n = sets[k].n;
+    uint32_t u = __ldg(&pairs[2 * i]), v = __ldg(&pairs[2 * i + 1]);
+    if (u >= n || v >= n) return 0;
+    if (u > v) {
+        const uint32_t t = u;
+        u = v;
+        v = t;
+    }
+    const uint32_t bu = uint32_t(uint64_t(u) * GROUP_BLOCKS / n), bv = uint32_t(uint64_t(v) * GROUP_BLOCKS / n);
+    return bu * GROUP_BLOCKS + bv;
+}
+
+__global__ void group_count_kernel(const QuerySet *sets, const uint32_t *nsets_p, const uint32_t *pairs,
+                                   const uint16_t *set_of, uint64_t q, uint32_t *cnt) {
+    const uint32_t nsets = *nsets_p;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < q;
+         i += uint64_t(gridDim.x) * blockDim.x)
+        atomicAdd(&cnt[group_key(sets, nsets, pairs, set_of, i)], 1u);
+}
+
+// exclusive prefix of the GROUP_KEYS counts, in place (one CTA of 1024 threads)
+__global__ void __launch_bounds__(1024) group_scan_kernel(uint32_t *cnt) {
+    constexpr uint32_t PER = GROUP_KEYS / 1024;
+    __shared__ uint32_t wsum[32];
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    uint32_t x[PER], s = 0;
+#pragma unroll
+    for (uint32_t k = 0; k < PER; ++k) {
+        x[k] = cnt[t * PER + k];
+        s += x[k];
+    }
+    uint32_t inc = s;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= uint32_t(o)) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, wi, o);
+            if (lane >= uint32_t(o)) wi += y;
+        }
+        wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    uint32_t run = wsum[warp] + inc - s;
+#pragma unroll
+    for (uint32_t k = 0; k < PER; ++k) {
+        cnt[t * PER + k] = run;
+        run += x[k];
+    }
+}
+
+__global__ void group_scatter_kernel(const QuerySet *sets, const uint32_t *nsets_p, const uint32_t *pairs,
+                                     const uint16_t *set_of, uint64_t q, uint32_t *fill, uint32_t *perm) {
+    const uint32_t nsets = *nsets_p;
+    for (uint64_t i = uint64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < q;
+         i += uint64_t(gridDim.x) * blockDim.x)
+        perm[atomicAdd(&fill[group_key(sets, nsets, pairs, set_of, i)], 1u)] = uint32_t(i);
+}
+
 }  // namespace
 
+cudaError_t launch_group_order(const QuerySet *sets, const uint32_t *nsets, const uint32_t *pairs,
+                               const uint16_t *set_of, uint64_t q, uint32_t *scratch, uint32_t *perm,
+                               cudaStream_t s) {
+    if (q == 0) return cudaSuccess;
+    if (q > 0xFFFFFFFFull) return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(scratch, 0, GROUP_KEYS * sizeof(uint32_t), s);
+    if (e) return e;
+    uint64_t blocks = (q + 255) / 256;
+    if (blocks > uint64_t(device_sms()) * 8) blocks = uint64_t(device_sms()) * 8;
+    group_count_kernel<<<unsigned(blocks), 256, 0, s>>>(sets, nsets, pairs, set_of, q, scratch);
+    group_scan_kernel<<<1, 1024, 0, s>>>(scratch);
+    group_scatter_kernel<<<unsigned(blocks), 256, 0, s>>>(sets, nsets, pairs, set_of, q, scratch, perm);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_query_sets(const QuerySet *sets, const uint32_t *nsets, const uint32_t *pairs,
-                              const uint16_t *set_of, uint64_t q, uint32_t *out, int *bad,
-                              int max_blocks, cudaStream_t s) {
+                              const uint16_t *set_of, const uint32_t *perm, uint64_t q, uint32_t *out,
+                              int *bad, int max_blocks, cudaStream_t s) {
     if (q == 0) return cudaSuccess;
     uint64_t blocks = (q * 32 + 255) / 256;
     if (blocks > uint64_t(max_blocks)) blocks = uint64_t(max_blocks);
-    query_sets_kernel<<<unsigned(blocks), 256, 0, s>>>(sets, nsets, pairs, set_of, q, out, bad);
+    query_sets_kernel<<<unsigned(blocks), 256, 0, s>>>(sets, nsets, pairs, set_of, perm, q, out, bad);
     return cudaGetLastError();
 }
 

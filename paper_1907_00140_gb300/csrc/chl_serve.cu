@@ -79,6 +79,8 @@ struct Slot {
     uint16_t *h_set = nullptr; // host scratch of set ids while a batch forms
     uint8_t *d_in = nullptr;
     uint32_t *d_out = nullptr;
+    uint32_t *d_perm = nullptr;     // grouped order of the batch (query_order 1)
+    uint32_t *d_scratch = nullptr;  // its key counters
     std::vector<uint64_t> bucket;            // batch sizes with a captured graph
     std::vector<cudaGraphExec_t> graph;      // one per bucket size
     std::vector<Part> parts;
@@ -119,6 +121,7 @@ struct chl_server {
     std::unordered_map<uint64_t, Req *> reqs;
     uint64_t next_id = 1;
     std::vector<chl::QuerySet> sets;
+    std::vector<chl::QuerySet *> part_arrays;  // device arrays of partitioned sets
     chl::QuerySet *d_sets = nullptr;
     uint32_t *d_nsets = nullptr;  // set count read by the (captured) query launches
     std::vector<Slot> slots;
@@ -356,7 +359,7 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
     chl_server_opts o{};
     if (opts) o = *opts;
     if (o.query_slots < 0 || o.query_slots > 16 || o.build_workers < 0 || o.build_workers > 16 ||
-        o.batching < 0 || o.batching > 1 || o.build_slots < 0)
+        o.batching < 0 || o.batching > 1 || o.build_slots < 0 || o.query_order < 0 || o.query_order > 1)
         return set_error(CHL_EINVAL, "bad server options");
     if (!o.query_slots) o.query_slots = 3;
     if (o.batching == 1) o.query_slots = 1;
@@ -392,6 +395,8 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
         if (!e && !sl.h_set) e = cudaErrorMemoryAllocation;
         if (!e) e = cudaMalloc(&sl.d_in, mb * 10 + 16);
         if (!e) e = cudaMalloc(&sl.d_out, mb * 4 + 16);
+        if (!e && o.query_order == 1) e = cudaMalloc(&sl.d_perm, mb * 4);
+        if (!e && o.query_order == 1) e = cudaMalloc(&sl.d_scratch, GROUP_SCRATCH_WORDS * 4);
         // bucket sizes 32, 64, ... up to max_batch, each captured as a graph
         for (uint64_t B = 32; !e; B *= 2) {
             if (B > mb) B = mb;
@@ -403,15 +408,20 @@ extern "C" chl_status chl_server_create(const chl_server_opts *opts, chl_server 
                 // the answers straight to host memory (no copies to wait for)
                 uint32_t *flag = sl.h_out + B;
                 launch_query_sets(S->d_sets, S->d_nsets, reinterpret_cast<const uint32_t *>(sl.h_in),
-                                  reinterpret_cast<const uint16_t *>(sl.h_in + 8 * B), B, sl.h_out,
-                                  reinterpret_cast<int *>(flag), S->sms * 64, sl.s);
+                                  reinterpret_cast<const uint16_t *>(sl.h_in + 8 * B), nullptr, B,
+                                  sl.h_out, reinterpret_cast<int *>(flag), S->sms * 64, sl.s);
                 e = cudaStreamEndCapture(sl.s, &gph);
             } else if (!e) {
                 uint32_t *flag = sl.d_out + B;
                 cudaMemsetAsync(flag, 0, sizeof(int), sl.s);
                 cudaMemcpyAsync(sl.d_in, sl.h_in, B * 10, cudaMemcpyHostToDevice, sl.s);
-                launch_query_sets(S->d_sets, S->d_nsets, reinterpret_cast<const uint32_t *>(sl.d_in),
-                                  reinterpret_cast<const uint16_t *>(sl.d_in + 8 * B), B, sl.d_out,
+                const uint32_t *pairs_d = reinterpret_cast<const uint32_t *>(sl.d_in);
+                const uint16_t *set_d = reinterpret_cast<const uint16_t *>(sl.d_in + 8 * B);
+                // grouped order: the batch sorted by the vertex blocks its pairs read
+                if (o.query_order == 1)
+                    launch_group_order(S->d_sets, S->d_nsets, pairs_d, set_d, B, sl.d_scratch, sl.d_perm, sl.s);
+                launch_query_sets(S->d_sets, S->d_nsets, pairs_d, set_d,
+                                  o.query_order == 1 ? sl.d_perm : nullptr, B, sl.d_out,
                                   reinterpret_cast<int *>(flag), S->sms * 64, sl.s);
                 cudaMemcpyAsync(sl.h_out, sl.d_out, B * 4 + 4, cudaMemcpyDeviceToHost, sl.s);
                 e = cudaStreamEndCapture(sl.s, &gph);
@@ -442,13 +452,48 @@ extern "C" chl_status chl_server_add_set(chl_server *S, const chl_labels *L, uin
                          S->device);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->sets.size() >= MAX_SETS) return set_error(CHL_EINVAL, "too many label sets");
-    QuerySet q{L->n, L->offsets, L->hubpos, L->dist};
+    QuerySet q{L->n, L->offsets, L->hubpos, L->dist, 0, nullptr};
     const uint32_t k = uint32_t(S->sets.size());
     const uint32_t k1 = k + 1;
     // published before any query on it can be submitted (the id is returned after)
     cudaError_t e = cudaMemcpy(S->d_sets + k, &q, sizeof(q), cudaMemcpyHostToDevice);
     if (!e) e = cudaMemcpy(S->d_nsets, &k1, sizeof(k1), cudaMemcpyHostToDevice);
     if (e) return cuda_status(e, "cudaMemcpy");
+    S->sets.push_back(q);
+    *set_id = k;
+    return CHL_OK;
+}
+
+extern "C" chl_status chl_server_add_partitioned_set(chl_server *S, const chl_labels *const *parts,
+                                                     uint32_t nparts, uint32_t *set_id) {
+    if (!S || !parts || !set_id) return set_error(CHL_EINVAL, "server, parts or set_id is NULL");
+    if (nparts < 1 || nparts > CHL_MAX_PARTS)
+        return set_error(CHL_EINVAL, "nparts must be in [1, %d]", CHL_MAX_PARTS);
+    std::vector<QuerySet> h(nparts);
+    for (uint32_t k = 0; k < nparts; ++k) {
+        const chl_labels *L = parts[k];
+        if (!L) return set_error(CHL_EINVAL, "part %u is NULL", k);
+        if (L->device != S->device)
+            return set_error(CHL_EINVAL, "part %u lives on device %d, the server on device %d", k,
+                             L->device, S->device);
+        if (L->n != parts[0]->n) return set_error(CHL_EINVAL, "parts cover different vertex counts");
+        h[k] = QuerySet{L->n, L->offsets, L->hubpos, L->dist, 0, nullptr};
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->sets.size() >= MAX_SETS) return set_error(CHL_EINVAL, "too many label sets");
+    QuerySet *d_parts = nullptr;
+    cudaError_t e = cudaMalloc(&d_parts, nparts * sizeof(QuerySet));
+    if (!e) e = cudaMemcpy(d_parts, h.data(), nparts * sizeof(QuerySet), cudaMemcpyHostToDevice);
+    const QuerySet q{parts[0]->n, nullptr, nullptr, nullptr, nparts, d_parts};
+    const uint32_t k = uint32_t(S->sets.size());
+    const uint32_t k1 = k + 1;
+    if (!e) e = cudaMemcpy(S->d_sets + k, &q, sizeof(q), cudaMemcpyHostToDevice);
+    if (!e) e = cudaMemcpy(S->d_nsets, &k1, sizeof(k1), cudaMemcpyHostToDevice);
+    if (e) {
+        if (d_parts) cudaFree(d_parts);
+        return cuda_status(e, "partitioned set");
+    }
+    S->part_arrays.push_back(d_parts);
     S->sets.push_back(q);
     *set_id = k;
     return CHL_OK;
@@ -617,10 +662,13 @@ extern "C" void chl_server_destroy(chl_server *S) {
         std::free(sl.h_set);
         cudaFree(sl.d_in);
         cudaFree(sl.d_out);
+        cudaFree(sl.d_perm);
+        cudaFree(sl.d_scratch);
         if (sl.ev) cudaEventDestroy(sl.ev);
         if (sl.s) cudaStreamDestroy(sl.s);
     }
     cudaFree(S->d_sets);
     cudaFree(S->d_nsets);
+    for (QuerySet *p : S->part_arrays) cudaFree(p);
     delete S;
 }
