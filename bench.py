@@ -302,8 +302,7 @@ def roofline(name, stats, tree_ms, opts, peak, peak_kind):
     if hybrid:
         algo += 8.0 * wu.get("Q", 0.0)
     ach = algo / (tree_ms / 1000.0) / 1e9
-    key = (name, opts.get("threads_per_tree", 1024), opts.get("bucket_delta", 0),
-           opts.get("window_buckets", 32), bool(hybrid))
+    key = (name, tuple(sorted(opts.items())), bool(hybrid))
     traffic = TREE_DRAM_BYTES_PER_BUILD.get(key)
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": traffic,
@@ -507,7 +506,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="rmat18")
     ap.add_argument("--queries", type=int, default=1_000_000)
-    ap.add_argument("--cpu-budget", type=float, default=20.0,
+    ap.add_argument("--cpu-budget", type=float, default=30.0,
                     help="seconds of host work a CPU baseline may take")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip plain/cpu/e2e/no-hybrid/serving legs")
@@ -573,7 +572,7 @@ def main():
     if args.serve_only:
         L = chl.build_labels(DG, R, **opts)
         res = {"metric": "serving", "config": {"workload": name, "tuned": opts},
-               "serving": serving_leg(args, chl, g, L, {})}
+               "serving": serving_leg(args, chl, g, L, {}, DG, R, P)}
         L.free()
         print(json.dumps(res), flush=True)
         return
@@ -705,7 +704,7 @@ def main():
             if keep:
                 kept[c] = keep
     if not args.no_extras and rank_id == 0:
-        res["serving"] = serving_leg(args, chl, g, L, kept)
+        res["serving"] = serving_leg(args, chl, g, L, kept, DG, R, P)
     L.free()
     for _, Lk in kept.values():
         Lk.free()
@@ -805,7 +804,71 @@ def run_serving(chl, sets, rates, duration, builds, seed=40):
     return out
 
 
-def serving_leg(args, chl, g, L, kept):
+def query_modes(chl, g, L, DG, R, sets, duration, pairs_d):
+    """The paper's query modes (Sec. 6) on one GPU beside the default merge:
+    - partitioned (QFDL-style): the main labels built again as hub partitions
+      (disjoint root ranges), each query the minimum over the parts;
+    - grouped (QDOL-style): batches counting-sorted by the vertex blocks their
+      pairs read, answers put back in arrival order.
+    Reported: the bench's query batch through each entry point (device
+    buffers, CUDA events), and the server under open-loop load at 1e7 and 1e8
+    queries/s with each mode on the main label set."""
+    import torch
+    n = g.n
+    cuts = sorted({min(n, c) for c in (0, 152, 1216, 9728, n)})
+    t0 = time.perf_counter()
+    parts = [chl.build_labels(DG, R, root_begin=b, root_end=e) for b, e in zip(cuts[:-1], cuts[1:])]
+    build_s = time.perf_counter() - t0
+    out = {"partition_root_ranges": [[b, e] for b, e in zip(cuts[:-1], cuts[1:])],
+           "partition_build_s": build_s}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o = torch.empty(pairs_d.shape[0], dtype=torch.int32, device=pairs_d.device)
+
+    def batch(fn):
+        ms = []
+        for _ in range(4):
+            ev0.record()
+            fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            ms.append(ev0.elapsed_time(ev1))
+        best = min(ms[1:])
+        return {"batch_ms": best, "queries_per_s": pairs_d.shape[0] / (best / 1000.0)}
+
+    q = pairs_d.shape[0]
+    out["batch"] = {"pairs": q,
+                    "merge": batch(lambda: L.query(pairs_d, out=o)),
+                    "grouped": batch(lambda: L.query(pairs_d, out=o, grouped=True)),
+                    "partitioned": batch(lambda: chl.query_partitioned(parts, pairs_d, out=o))}
+    main = [(g, L)]
+    res = {}
+    for mode, make in (("merge", lambda: chl.Server(query_slots=3)),
+                       ("grouped", lambda: chl.Server(query_slots=3, query_order=1)),
+                       ("partitioned", lambda: chl.Server(query_slots=3))):
+        S = make()
+        if mode == "partitioned":
+            S.add_partitioned_set(parts)
+        else:
+            S.add_set(L)
+        S.replay(*make_stream(main, 1e6, 0.01, 699))  # warm-up
+        rows = []
+        for i, lam in enumerate((1e7, 1e8)):
+            arr, so, off, pairs = make_stream(main, lam, duration, 700 + i)
+            ans, lat, wall = S.replay(arr, so, off, pairs)
+            rows.append({"offered_qps": lam, "queries": int(off[-1]),
+                         "achieved_qps": float(off[-1]) / max(wall, 1e-9),
+                         "p50_us": float(np.percentile(lat, 50) * 1e6),
+                         "p99_us": float(np.percentile(lat, 99) * 1e6),
+                         "p999_us": float(np.percentile(lat, 99.9) * 1e6)})
+        S.close()
+        res[mode] = rows
+    out["serving"] = res
+    for x in parts:
+        x.free()
+    return out
+
+
+def serving_leg(args, chl, g, L, kept, DG, R, P):
     """Serving run over the bench's labels and other workloads' labels (those
     the config legs kept, else built here)."""
     import workloads as W
@@ -827,6 +890,7 @@ def serving_leg(args, chl, g, L, kept):
         sets.append((g2, L2))
     t0 = time.perf_counter()
     out = run_serving(chl, sets, [1e6, 3e6, 1e7, 3e7, 1e8], args.serve_duration, args.serve_builds)
+    out["modes"] = query_modes(chl, g, L, DG, R, sets, args.serve_duration, P)
     out["leg_s"] = time.perf_counter() - t0
     out["label_sets"] = [{"workload": gg.name, "n": gg.n, "labels": LL.total, "bytes": LL.nbytes}
                          for gg, LL in sets]

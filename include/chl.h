@@ -159,6 +159,15 @@ typedef struct chl_labels chl_labels;
  *                          (cp.async.bulk) instead of register loads; 0 = off
  *                          (measured slower on the R-MAT and grid workloads,
  *                          kept for other graphs and hardware)
+ *   small_tree_expansions  frontier-size switch of the label-pruned phases:
+ *                          once a phase's trees averaged fewer expansions than
+ *                          this, the later phases (whose trees are smaller
+ *                          still) run small_threads_per_tree threads per tree,
+ *                          so that more trees share each SM and hide each
+ *                          other's per-tree latency. 0 = 8192
+ *   small_threads_per_tree threads per tree after that switch (a power of two
+ *                          in [32, 1024]); 0 = 256 (or pruned_threads_per_tree
+ *                          when smaller)
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
@@ -202,6 +211,8 @@ typedef struct {
     float switch_ratio;
     uint32_t round_limit;
     int32_t query_stage_kb;
+    uint32_t small_tree_expansions;
+    int32_t small_threads_per_tree;
 } chl_build_opts;
 
 #define CHL_MAX_COMMON_HUBS 64
@@ -276,12 +287,17 @@ chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opt
  * sample has the build's mix of large and small trees) for candidate bucket
  * widths, then block sizes, then window sizes (coordinate search), and the
  * fastest is kept. For a whole build (no root range set in base) the block
- * size is then settled by two whole builds (512 and 1024 threads), since the
- * hybrid phases prune later trees far below the sample's sizes.
+ * size is then settled by whole builds (256, 512 and 1024 threads), since the
+ * hybrid phases prune later trees far below the sample's sizes, and then the
+ * phases' two switch points, each by whole builds: the first-phase switch
+ * (switch_ratio default or off) and the frontier size of the small-tree
+ * switch (small_tree_expansions 2048, 8192 or 32768).
  *   g, rank, stream   as for chl_build
  *   base              fields set (non-zero) are kept fixed; NULL = tune all
  *   best              receives base with threads_per_tree, bucket_delta and
- *                     window_buckets filled in; pass it to chl_build
+ *                     window_buckets filled in (and, for a whole build,
+ *                     switch_ratio and small_tree_expansions when base left
+ *                     them 0); pass it to chl_build
  *   report            optional: trials run, sample size, best trial time
  * Errors: as chl_build.
  */

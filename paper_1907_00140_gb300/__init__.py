@@ -99,7 +99,8 @@ class chl_build_opts(C.Structure):
                 ("flags", C.c_int32), ("label_capacity", C.c_uint64), ("common_hubs", C.c_int32),
                 ("pruned_bucket_delta", C.c_int32), ("psi_threshold", C.c_float),
                 ("pruned_threads_per_tree", C.c_int32), ("switch_ratio", C.c_float),
-                ("round_limit", C.c_uint32), ("query_stage_kb", C.c_int32)]
+                ("round_limit", C.c_uint32), ("query_stage_kb", C.c_int32),
+                ("small_tree_expansions", C.c_uint32), ("small_threads_per_tree", C.c_int32)]
 
 
 class chl_tune_report(C.Structure):
@@ -429,12 +430,18 @@ def _build_opts(**kw) -> chl_build_opts:
 
 def tune(g, rank, stream: int | None = None, **fixed):
     """Measured choice of threads_per_tree, bucket_delta and window_buckets
-    for this graph (chl_tune). Returns (build options for build_labels,
-    tuning report)."""
+    for this graph, and for a whole build the phases' switch points
+    switch_ratio and small_tree_expansions (chl_tune). Returns (build options
+    for build_labels: the tuned fields, those set non-zero, and the fixed
+    ones; tuning report)."""
     csr, rkp, keep = _csr_args(g, rank)
     base = _build_opts(**fixed)
     best, rep = chl_tune(csr, rkp, base, _current_stream() if stream is None else stream)
     out = {k: getattr(best, k) for k in ("threads_per_tree", "bucket_delta", "window_buckets")}
+    for k in ("switch_ratio", "small_tree_expansions"):
+        if getattr(best, k):
+            out[k] = getattr(best, k)
+    out.update(fixed)
     return out, rep.as_dict()
 
 

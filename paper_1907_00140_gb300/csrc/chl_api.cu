@@ -39,6 +39,45 @@ chl_status cuda_status(cudaError_t e, const char *what) {
 cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cudaStream_t s,
                                int *launches);
 
+// Device memory of the library's stream-ordered allocations comes from one
+// pool per device that keeps up to POOL_KEEP bytes cached after a
+// synchronisation (the default pool keeps none, so each build would map its
+// gigabytes of tree-slot state again).
+constexpr uint64_t POOL_KEEP = uint64_t(32) << 30;
+
+cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t s) {
+    constexpr int MAXDEV = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[MAXDEV] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    if (dev < 0 || dev >= MAXDEV) return cudaMallocAsync(ptr, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.handleTypes = cudaMemHandleTypeNone;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t p = nullptr;
+            e = cudaMemPoolCreate(&p, &props);
+            if (e) return e;
+            uint64_t keep = POOL_KEEP;
+            e = cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e) {
+                cudaMemPoolDestroy(p);
+                return e;
+            }
+            pools[dev] = p;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, s);
+}
+
 int device_sms() {
     constexpr int MAXDEV = 64;
     static std::atomic<int> cached[MAXDEV];
@@ -81,7 +120,7 @@ uint64_t records_kept(const Control &c) { return c.flags[1] ? c.out_valid : c.ou
 cudaError_t grow_records(void **bufs, int nbufs, uint64_t T, uint64_t ncap, cudaStream_t s) {
     for (int k = 0; k < nbufs; ++k) {
         void *nb = nullptr;
-        cudaError_t e = cudaMallocAsync(&nb, ncap * 4, s);
+        cudaError_t e = dmalloc(&nb, ncap * 4, s);
         if (!e && T) e = cudaMemcpyAsync(nb, bufs[k], T * 4, cudaMemcpyDeviceToDevice, s);
         if (e) {
             if (nb) cudaFreeAsync(nb, s);
@@ -95,14 +134,26 @@ cudaError_t grow_records(void **bufs, int nbufs, uint64_t T, uint64_t ncap, cuda
 
 // expansion rounds one tree may take (far above any real tree)
 constexpr uint32_t DEFAULT_ROUND_LIMIT = 1u << 26;
+// a label-pruned phase whose trees averaged fewer expansions than this hands
+// the later phases to the small-tree launch
+constexpr uint32_t DEFAULT_SMALL_TREE_EXPANSIONS = 8192;
+// shared memory per tree slot for the root's table distances by hub position in
+// the label-pruned phases: phases whose table holds at most 16,384 hubs look
+// each entry up with one load instead of a hash probe
+constexpr uint32_t ROOT_ARRAY_BYTES = 64u << 10;
 
 struct Params {
     int tpt;
     int tpt_lt;          // threads per tree in the label-pruned phases
     int slots_lt;        // ... and their slots
     uint32_t fin_words_lt;
-    uint32_t stage_lt;   // staging bytes of the queried lists in those phases
-    uint32_t stage_want; // ... as requested
+    uint32_t aux_lt;     // auxiliary shared memory of those phases (staging or root distances)
+    // label-pruned phases of small trees (after a phase whose trees averaged
+    // fewer than small_exp expansions): smaller blocks, more trees per SM
+    int tpt_sm, slots_sm;
+    uint32_t fin_words_sm, aux_sm, small_exp;
+    uint32_t nwin_sm;  // window buckets of the small-tree launch (its trees span few buckets)
+    uint32_t stage_want; // staging of the queried lists, as requested (0 = none)
     uint32_t round_limit;
     uint32_t delta;
     uint32_t delta_lt;  // bucket width of the phases that prune with the label table
@@ -113,6 +164,11 @@ struct Params {
     uint32_t fin_words;  // settled-filter bitmap words per CTA
     uint32_t w_min;
     uint32_t n;
+    int max_slots() const { return std::max(slots, std::max(slots_lt, slots_sm)); }
+    // list words per vertex over all slots, the largest of the launches' layouts
+    size_t list_words() const {
+        return std::max(size_t(std::max(slots, slots_lt)) * (4 + nwin), size_t(slots_sm) * (4 + nwin_sm));
+    }
 };
 
 // Untuned defaults of the search parameters from graph statistics (chl_tune
@@ -150,12 +206,23 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     p.w_min = g.w_min ? g.w_min : 1;
     p.n = g.n;
     p.tpt_lt = o.pruned_threads_per_tree ? o.pruned_threads_per_tree : p.tpt;
+    // the label-pruned phases' auxiliary area: the staging of queried lists
+    // when asked for, else the root's table distances by hub position
     p.stage_want = o.query_stage_kb > 0 ? uint32_t(o.query_stage_kb) << 10 : 0u;
-    plant_smem_split(p.tpt_lt, g.n, p.stage_want, &p.fin_words_lt, &p.stage_lt);
+    plant_smem_split(p.tpt_lt, g.n, p.stage_want ? p.stage_want : ROOT_ARRAY_BYTES, &p.fin_words_lt,
+                     &p.aux_lt);
     p.round_limit = o.round_limit ? o.round_limit : DEFAULT_ROUND_LIMIT;
     int per_sm = plant_max_slots_per_sm(p.tpt, p.fin_words, 0);
     if (per_sm < 1) per_sm = 1;
-    int per_sm_lt = plant_max_slots_per_sm(p.tpt_lt, p.fin_words_lt, p.stage_lt);
+    int per_sm_lt = plant_max_slots_per_sm(p.tpt_lt, p.fin_words_lt, p.aux_lt);
+    p.tpt_sm = o.small_threads_per_tree ? o.small_threads_per_tree : std::min(p.tpt_lt, 256);
+    p.nwin_sm = std::min<uint32_t>(p.nwin, 8);
+    p.small_exp = o.small_tree_expansions ? o.small_tree_expansions : DEFAULT_SMALL_TREE_EXPANSIONS;
+    plant_smem_split(p.tpt_sm, g.n, p.stage_want ? p.stage_want : ROOT_ARRAY_BYTES, &p.fin_words_sm,
+                     &p.aux_sm);
+    int per_sm_sm = plant_max_slots_per_sm(p.tpt_sm, p.fin_words_sm, p.aux_sm);
+    if (per_sm_sm < 1) per_sm_sm = 1;
+    long long slots_sm = o.slots > 0 ? o.slots : (long long)sms * per_sm_sm;
     if (per_sm_lt < 1) per_sm_lt = 1;
     long long slots = o.slots > 0 ? o.slots : (long long)sms * per_sm;
     long long slots_lt = o.slots > 0 ? o.slots : (long long)sms * per_sm_lt;
@@ -168,6 +235,13 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     if (slots < 1) slots = 1;
     if (o.slots <= 0 && slots_lt > cap) slots_lt = cap;
     if (slots_lt < 1) slots_lt = 1;
+    {
+        const double per_slot_sm = (p.kb + 8.0 + 4.0 * (4 + p.nwin_sm)) * double(g.n) + 64.0;
+        const long long cap_sm = (long long)(budget / per_slot_sm);
+        if (o.slots <= 0 && slots_sm > cap_sm) slots_sm = cap_sm;
+    }
+    if (slots_sm < 1) slots_sm = 1;
+    p.slots_sm = int(slots_sm);
     p.slots = int(slots);
     p.slots_lt = int(slots_lt);
     return p;
@@ -198,15 +272,15 @@ struct SlotState {
     DevBuf key, tags, lists, ctr;
     cudaError_t alloc(const Params &P, uint32_t n, cudaStream_t s) {
         key.s = tags.s = lists.s = ctr.s = s;
-        const size_t sn = size_t(std::max(P.slots, P.slots_lt)) * n;
+        const size_t sn = size_t(P.max_slots()) * n;
         cudaError_t e;
-        if ((e = cudaMallocAsync(&key.p, sn * P.kb, s))) return e;
+        if ((e = dmalloc(&key.p, sn * P.kb, s))) return e;
         if ((e = cudaMemsetAsync(key.p, 0xFF, sn * P.kb, s))) return e;
-        if ((e = cudaMallocAsync(&tags.p, sn * 4, s))) return e;
+        if ((e = dmalloc(&tags.p, sn * 4, s))) return e;
         if ((e = cudaMemsetAsync(tags.p, 0, sn * 4, s))) return e;
-        if ((e = cudaMallocAsync(&lists.p, sn * 4 * (4 + P.nwin), s))) return e;
-        if ((e = cudaMallocAsync(&ctr.p, size_t(std::max(P.slots, P.slots_lt)) * 16, s))) return e;
-        if ((e = cudaMemsetAsync(ctr.p, 0, size_t(std::max(P.slots, P.slots_lt)) * 16, s))) return e;
+        if ((e = dmalloc(&lists.p, P.list_words() * n * 4, s))) return e;
+        if ((e = dmalloc(&ctr.p, size_t(P.max_slots()) * 16, s))) return e;
+        if ((e = cudaMemsetAsync(ctr.p, 0, size_t(P.max_slots()) * 16, s))) return e;
         return cudaSuccess;
     }
     void fill(const Params &P, uint32_t n, TreeLaunch &tl) const {
@@ -296,13 +370,13 @@ chl_status build_common_table(const RankGraph &rg, const Params &P, const SlotSt
     TreeLaunch tl{};
     t.hubs = P.eta;
     t.stride = (P.eta + 3) & ~3u;
-    CUDA_TRY(cudaMallocAsync(&t.buf.p, size_t(n) * t.stride * 4, s));
+    CUDA_TRY(dmalloc(&t.buf.p, size_t(n) * t.stride * 4, s));
     CUDA_TRY(cudaMemsetAsync(t.buf.p, 0xFF, size_t(n) * t.stride * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_ov.p, cap * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_oh.p, cap * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_fail.p, (size_t(P.eta) + 1) * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
+    CUDA_TRY(dmalloc(&b_ov.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_oh.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_od.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_fail.p, (size_t(P.eta) + 1) * 4, s));
+    CUDA_TRY(dmalloc(&b_ctl.p, sizeof(Control), s));
     CUDA_TRY(cudaMemsetAsync(b_ctl.p, 0, sizeof(Control), s));
     ctl = (Control *)b_ctl.p;
     tl.n = n;
@@ -351,7 +425,7 @@ chl_status table_from_records(const RankGraph &rg, const Params &P, const uint32
     t.buf.s = s;
     t.hubs = P.eta;
     t.stride = (P.eta + 3) & ~3u;
-    CUDA_TRY(cudaMallocAsync(&t.buf.p, size_t(n) * t.stride * 4, s));
+    CUDA_TRY(dmalloc(&t.buf.p, size_t(n) * t.stride * 4, s));
     CUDA_TRY(cudaMemsetAsync(t.buf.p, 0xFF, size_t(n) * t.stride * 4, s));
     CUDA_TRY(launch_clt_fill(ov, oh, od, count, rg.pos_of, (uint32_t *)t.buf.p, t.stride, t.hubs, s));
     ++*launches;
@@ -402,6 +476,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (o.threads_per_tree && (o.threads_per_tree < 32 || o.threads_per_tree > 1024 ||
                                (o.threads_per_tree & (o.threads_per_tree - 1))))
         return set_error(CHL_EINVAL, "threads_per_tree must be a power of two in [32, 1024]");
+    if (o.small_threads_per_tree && (o.small_threads_per_tree < 32 || o.small_threads_per_tree > 1024 ||
+                                     (o.small_threads_per_tree & (o.small_threads_per_tree - 1))))
+        return set_error(CHL_EINVAL, "small_threads_per_tree must be a power of two in [32, 1024]");
     if (o.pruned_threads_per_tree &&
         (o.pruned_threads_per_tree < 32 || o.pruned_threads_per_tree > 1024 ||
          (o.pruned_threads_per_tree & (o.pruned_threads_per_tree - 1))))
@@ -448,6 +525,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     std::vector<std::pair<uint32_t, uint32_t>> phases;
     LabelTable lt;  // labels of earlier phases (hybrid)
     bool use_lt = false, hybrid = false, hybrid_off = false;
+    bool small = false;  // later label-pruned phases run the small-tree launch
     uint64_t lt_phases = 0;
     uint64_t lt_records = 0;  // output records the label table holds
     const double psi_th = o.psi_threshold > 0.0f ? double(o.psi_threshold) : PSI_TH;
@@ -474,10 +552,10 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
 
     // inputs on the device
     if (g->mem == CHL_MEM_HOST) {
-        CUDA_TRY(cudaMallocAsync(&b_row.p, (size_t(n) + 1) * 8, s));
-        CUDA_TRY(cudaMallocAsync(&b_col.p, (m2 ? m2 : 1) * 4, s));
-        CUDA_TRY(cudaMallocAsync(&b_w.p, (m2 ? m2 : 1) * 4, s));
-        CUDA_TRY(cudaMallocAsync(&b_rank.p, size_t(n) * 4, s));
+        CUDA_TRY(dmalloc(&b_row.p, (size_t(n) + 1) * 8, s));
+        CUDA_TRY(dmalloc(&b_col.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(dmalloc(&b_w.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(dmalloc(&b_rank.p, size_t(n) * 4, s));
         CUDA_TRY(cudaMemcpyAsync(b_row.p, g->row_ptr, (size_t(n) + 1) * 8, cudaMemcpyHostToDevice, s));
         if (m2) {
             CUDA_TRY(cudaMemcpyAsync(b_col.p, g->col, m2 * 4, cudaMemcpyHostToDevice, s));
@@ -511,32 +589,39 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             P.slots = 1;
             P.slots_lt = 1;
             P.tpt_lt = P.tpt;
-            plant_smem_split(P.tpt_lt, rg.n, P.stage_want, &P.fin_words_lt, &P.stage_lt);
+            plant_smem_split(P.tpt_lt, rg.n, P.stage_want ? P.stage_want : ROOT_ARRAY_BYTES,
+                             &P.fin_words_lt, &P.aux_lt);
+            P.slots_sm = 1;
+            P.tpt_sm = P.tpt;
+            P.nwin_sm = P.nwin;
+            P.fin_words_sm = P.fin_words_lt;
+            P.aux_sm = P.aux_lt;
         }
     }
 
     CUDA_TRY(slot.alloc(P, n, s));
-    CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
+    CUDA_TRY(dmalloc(&b_ctl.p, sizeof(Control), s));
     ctl = (Control *)b_ctl.p;
-    CUDA_TRY(cudaMallocAsync(&b_fail.p, size_t(re - rb + 1) * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_roots.p, size_t(re - rb + 1) * 4, s));
+    CUDA_TRY(dmalloc(&b_fail.p, size_t(re - rb + 1) * 4, s));
+    CUDA_TRY(dmalloc(&b_roots.p, size_t(re - rb + 1) * 4, s));
 
     // label buffer: an estimate, grown (x2) when a tree does not fit
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    // label buffer: generous (up to 1024 labels per root within a quarter of the
-    // free memory); it doubles and the roots that did not fit are rebuilt
+    // label buffer: 512 labels per root (within a quarter of the free memory),
+    // above the average list length of the workloads measured (104 to 460); it
+    // doubles and the roots that did not fit are rebuilt
     cap = o.label_capacity;
     if (!cap) {
-        cap = uint64_t(re - rb) * 1024 + 1024;
+        cap = uint64_t(re - rb) * 512 + 1024;
         const uint64_t fit = uint64_t(0.25 * double(free_b)) / 12;
         if (cap > fit) cap = fit;
         if (cap < 1024) cap = 1024;
     }
     if (cap < 1) cap = 1;
-    CUDA_TRY(cudaMallocAsync(&b_ov.p, cap * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_oh.p, cap * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
-    if (parents) CUDA_TRY(cudaMallocAsync(&b_op.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_ov.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_oh.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_od.p, cap * 4, s));
+    if (parents) CUDA_TRY(dmalloc(&b_op.p, cap * 4, s));
 
     CUDA_TRY(cudaEventRecord(ev[1], s));
     // Hybrid phases (Sec. 5.2): a build that starts at the top root runs its
@@ -561,6 +646,8 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     for (size_t ph = 0; ph < phases.size(); ++ph) {
     const uint32_t pb = phases[ph].first, pe = phases[ph].second;
     const uint64_t exp0 = agg[0], T0 = T, arc0 = agg[1], pr0 = agg[6], rd0 = agg[4], bk0 = agg[5];
+    const uint64_t tr0 = agg[3], triv0 = agg[2];
+    const bool ph_small = small;
     const int ph_lt = lt.offsets ? 1 : 0;
     if (trace) t_ph = now_ms();
     if (lt.offsets) ++lt_phases;
@@ -581,9 +668,19 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             tl.lt_root = (uint32_t *)b_ltroot.p;
             tl.lt_hash_max = (o.flags & CHL_FLAG_DENSE_ROOT_LABELS) ? 0 : 0xFFFFFFFFu;
             set_delta(tl, P.delta_lt);
-            tl.fin_words = P.fin_words_lt;
-            tl.fin_bits = P.fin_words_lt * 32 < n ? P.fin_words_lt * 32 : n;
-            tl.stage_bytes = P.stage_lt;
+            // dynamic shared memory of this phase's launch: the root's table
+            // distances need 4 bytes per hub of the table (or the staging
+            // area when asked for); the settled bitmap takes the rest
+            {
+                const int tpt = small ? P.tpt_sm : P.tpt_lt;
+                const uint32_t need = ((pb * 4u) + 127u) & ~127u;
+                uint32_t want = P.stage_want ? P.stage_want : (need <= ROOT_ARRAY_BYTES ? need : 0u);
+                plant_smem_split(tpt, n, want, &tl.fin_words, &tl.aux_bytes);
+                if (!P.stage_want && tl.aux_bytes < need) plant_smem_split(tpt, n, 0, &tl.fin_words, &tl.aux_bytes);
+            }
+            tl.fin_bits = tl.fin_words * 32 < n ? tl.fin_words * 32 : n;
+            tl.stage_bytes = P.stage_want ? tl.aux_bytes : 0;
+            if (small) tl.nwin = P.nwin_sm;
         }
         // the batched form first writes the labels of the phase's trivial
         // roots and lists the others: room for one record per root
@@ -650,7 +747,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
                     ++launches;
                 }
             } else if (lt.offsets) {
-                CUDA_TRY(launch_plant_trees(tl, P.tpt_lt, P.slots_lt, s));
+                CUDA_TRY(launch_plant_trees(tl, small ? P.tpt_sm : P.tpt_lt, small ? P.slots_sm : P.slots_lt, s));
                 ++launches;
             } else {
                 CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
@@ -729,6 +826,14 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         else if (pe >= std::max<uint64_t>(uint64_t(P.slots) * 8, 8192) && psi < psi_th / 2)
             hybrid_off = true;
     }
+    // The small-tree switch: once a label-pruned phase's trees averaged fewer
+    // than small_exp expansions (trees only shrink further down the ranking),
+    // the later phases run more, smaller blocks per SM, which hides the
+    // per-tree latency of start, rounds and emission.
+    if (hybrid && ph_lt && !small && o.mode == 0) {
+        const uint64_t built = (agg[3] - tr0) - (agg[2] - triv0);
+        if (built && double(agg[0] - exp0) / double(built) < double(P.small_exp)) small = true;
+    }
     if (hybrid && !table.buf.p) {
         // the first phase built the table's trees: the Common Label Table from
         // their labels, for every later phase
@@ -754,8 +859,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         // every label so far, as CSR, for the next phase's pruning: the first
         // time sorted from all records, then grown by each phase's new ones
         if (!b_ltroot.p) {
-            CUDA_TRY(cudaMallocAsync(&b_ltroot.p, size_t(P.slots_lt) * n * 4, s));
-            CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, size_t(P.slots_lt) * n * 4, s));
+            const size_t ls = size_t(std::max(P.slots_lt, P.slots_sm));
+            CUDA_TRY(dmalloc(&b_ltroot.p, ls * n * 4, s));
+            CUDA_TRY(cudaMemsetAsync(b_ltroot.p, 0xFF, ls * n * 4, s));
         }
         // hubs of the Common Label Table are left out: every tree of a label-
         // pruned phase also queries that table, which holds all their labels
@@ -772,9 +878,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (trace) {
         CUDA_TRY(cudaStreamSynchronize(s));
         std::fprintf(stderr,
-                     "chl phase %zu roots [%u, %u) table %d trees %.3f ms assemble %.3f ms "
+                     "chl phase %zu roots [%u, %u) table %d%s trees %.3f ms assemble %.3f ms "
                      "expanded %llu arcs %llu labels %llu rounds %llu buckets %llu pruned %llu\n",
-                     ph, pb, pe, ph_lt, t_tree, now_ms() - t_ph - t_tree,
+                     ph, pb, pe, ph_lt, ph_small ? " small" : "", t_tree, now_ms() - t_ph - t_tree,
                      (unsigned long long)(agg[0] - exp0), (unsigned long long)(agg[1] - arc0),
                      (unsigned long long)(T - T0), (unsigned long long)(agg[4] - rd0),
                      (unsigned long long)(agg[5] - bk0), (unsigned long long)(agg[6] - pr0));
@@ -794,7 +900,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         goto done;
     }
     if (parents) {
-        CUDA_TRY(cudaMallocAsync(&csr_parent, (T ? T : 1) * 4, s));
+        CUDA_TRY(dmalloc(&csr_parent, (T ? T : 1) * 4, s));
         CUDA_TRY(place_parents(T, (const uint32_t *)b_ov.p, (const uint32_t *)b_oh.p,
                                (const uint32_t *)b_op.p, csr, csr_parent, s, &launches));
     }
@@ -914,11 +1020,11 @@ extern "C" chl_status chl_query(const chl_labels *L, const uint32_t *pairs, uint
     const uint32_t *dp = pairs;
     uint32_t *dout = out;
     int hbad = 0;
-    CUDA_TRY(cudaMallocAsync(&b_bad.p, sizeof(int), s));
+    CUDA_TRY(dmalloc(&b_bad.p, sizeof(int), s));
     CUDA_TRY(cudaMemsetAsync(b_bad.p, 0, sizeof(int), s));
     if (mem == CHL_MEM_HOST) {
-        CUDA_TRY(cudaMallocAsync(&b_p.p, q * 8, s));
-        CUDA_TRY(cudaMallocAsync(&b_o.p, q * 4, s));
+        CUDA_TRY(dmalloc(&b_p.p, q * 8, s));
+        CUDA_TRY(dmalloc(&b_o.p, q * 4, s));
         CUDA_TRY(cudaMemcpyAsync(b_p.p, pairs, q * 8, cudaMemcpyHostToDevice, s));
         dp = (const uint32_t *)b_p.p;
         dout = (uint32_t *)b_o.p;
@@ -951,7 +1057,7 @@ chl_status run_set_query(const QuerySet &set, const QuerySet *parts_h, uint32_t 
     std::vector<uint8_t> host(hdr + size_t(nparts) * sizeof(QuerySet));
     QuerySet top = set;
     uint8_t *base = nullptr;
-    CUDA_TRY(cudaMallocAsync(&b_set.p, host.size(), s));
+    CUDA_TRY(dmalloc(&b_set.p, host.size(), s));
     base = static_cast<uint8_t *>(b_set.p);
     if (nparts) top.parts = reinterpret_cast<const QuerySet *>(base + hdr);
     std::memcpy(host.data(), &top, sizeof(QuerySet));
@@ -963,15 +1069,15 @@ chl_status run_set_query(const QuerySet &set, const QuerySet *parts_h, uint32_t 
     if (nparts) std::memcpy(host.data() + hdr, parts_h, size_t(nparts) * sizeof(QuerySet));
     CUDA_TRY(cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, s));
     if (mem == CHL_MEM_HOST) {
-        CUDA_TRY(cudaMallocAsync(&b_p.p, q * 8, s));
-        CUDA_TRY(cudaMallocAsync(&b_o.p, q * 4, s));
+        CUDA_TRY(dmalloc(&b_p.p, q * 8, s));
+        CUDA_TRY(dmalloc(&b_o.p, q * 4, s));
         CUDA_TRY(cudaMemcpyAsync(b_p.p, pairs, q * 8, cudaMemcpyHostToDevice, s));
         dp = (const uint32_t *)b_p.p;
         dout = (uint32_t *)b_o.p;
     }
     if (grouped) {
-        CUDA_TRY(cudaMallocAsync(&b_perm.p, q * 4, s));
-        CUDA_TRY(cudaMallocAsync(&b_scr.p, GROUP_SCRATCH_WORDS * 4, s));
+        CUDA_TRY(dmalloc(&b_perm.p, q * 4, s));
+        CUDA_TRY(dmalloc(&b_scr.p, GROUP_SCRATCH_WORDS * 4, s));
         CUDA_TRY(launch_group_order(reinterpret_cast<const QuerySet *>(base),
                                     reinterpret_cast<const uint32_t *>(base + sizeof(QuerySet)), dp,
                                     nullptr, q, (uint32_t *)b_scr.p, (uint32_t *)b_perm.p, s));
@@ -1073,12 +1179,12 @@ extern "C" chl_status chl_path(const chl_labels *L, const uint32_t *pairs, uint6
     const uint32_t *dp = pairs;
     uint32_t *dpath = paths, *dlen = lens;
     int hbad = 0;
-    CUDA_TRY(cudaMallocAsync(&b_bad.p, sizeof(int), s));
+    CUDA_TRY(dmalloc(&b_bad.p, sizeof(int), s));
     CUDA_TRY(cudaMemsetAsync(b_bad.p, 0, sizeof(int), s));
     if (mem == CHL_MEM_HOST) {
-        CUDA_TRY(cudaMallocAsync(&b_p.p, q * 8, s));
-        CUDA_TRY(cudaMallocAsync(&b_path.p, q * max_len * 4 + 4, s));
-        CUDA_TRY(cudaMallocAsync(&b_len.p, q * 4, s));
+        CUDA_TRY(dmalloc(&b_p.p, q * 8, s));
+        CUDA_TRY(dmalloc(&b_path.p, q * max_len * 4 + 4, s));
+        CUDA_TRY(dmalloc(&b_len.p, q * 4, s));
         CUDA_TRY(cudaMemcpyAsync(b_p.p, pairs, q * 8, cudaMemcpyHostToDevice, s));
         dp = (const uint32_t *)b_p.p;
         dpath = (uint32_t *)b_path.p;
@@ -1196,12 +1302,12 @@ chl_status tree_trial(const RankGraph &rg, const Params &P, const CommonTable &t
     CUDA_TRY(cudaEventCreate(&e0));
     CUDA_TRY(cudaEventCreate(&e1));
     CUDA_TRY(slot.alloc(P, n, s));
-    CUDA_TRY(cudaMallocAsync(&b_ctl.p, sizeof(Control), s));
+    CUDA_TRY(dmalloc(&b_ctl.p, sizeof(Control), s));
     CUDA_TRY(cudaMemsetAsync(b_ctl.p, 0, sizeof(Control), s));
-    CUDA_TRY(cudaMallocAsync(&b_fail.p, size_t(count + 1) * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_ov.p, cap * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_oh.p, cap * 4, s));
-    CUDA_TRY(cudaMallocAsync(&b_od.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_fail.p, size_t(count + 1) * 4, s));
+    CUDA_TRY(dmalloc(&b_ov.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_oh.p, cap * 4, s));
+    CUDA_TRY(dmalloc(&b_od.p, cap * 4, s));
     ctl = (Control *)b_ctl.p;
     tl.n = n;
     tl.row = rg.row;
@@ -1277,10 +1383,10 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     CUDA_TRY(cudaGetDevice(&dev));
     CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     if (g->mem == CHL_MEM_HOST) {
-        CUDA_TRY(cudaMallocAsync(&b_row.p, (size_t(n) + 1) * 8, s));
-        CUDA_TRY(cudaMallocAsync(&b_col.p, (m2 ? m2 : 1) * 4, s));
-        CUDA_TRY(cudaMallocAsync(&b_w.p, (m2 ? m2 : 1) * 4, s));
-        CUDA_TRY(cudaMallocAsync(&b_rank.p, size_t(n) * 4, s));
+        CUDA_TRY(dmalloc(&b_row.p, (size_t(n) + 1) * 8, s));
+        CUDA_TRY(dmalloc(&b_col.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(dmalloc(&b_w.p, (m2 ? m2 : 1) * 4, s));
+        CUDA_TRY(dmalloc(&b_rank.p, size_t(n) * 4, s));
         CUDA_TRY(cudaMemcpyAsync(b_row.p, g->row_ptr, (size_t(n) + 1) * 8, cudaMemcpyHostToDevice, s));
         if (m2) {
             CUDA_TRY(cudaMemcpyAsync(b_col.p, g->col, m2 * 4, cudaMemcpyHostToDevice, s));
@@ -1303,7 +1409,7 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
         if (K < 1) K = 1;
         roots.resize(K);
         for (uint32_t i = 0; i < K; ++i) roots[i] = uint32_t((uint64_t(i) * n) / K);
-        CUDA_TRY(cudaMallocAsync(&b_roots.p, size_t(K) * 4, s));
+        CUDA_TRY(dmalloc(&b_roots.p, size_t(K) * 4, s));
         CUDA_TRY(cudaMemcpyAsync(b_roots.p, roots.data(), size_t(K) * 4, cudaMemcpyHostToDevice, s));
         cap = uint64_t(K) * 256 + 4 * uint64_t(n);
         const uint64_t fit = uint64_t(0.15 * double(free_b)) / 12;
@@ -1390,22 +1496,52 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     best->window_buckets = int32_t(bestP.nwin);
     best->slots = o.slots;  // 0 keeps the memory-budgeted default at build time
     // A whole build runs in hybrid phases whose pruned trees are far smaller
-    // than the sample's: the block size is settled by whole builds.
-    if (!o.threads_per_tree && !o.root_begin && !o.root_end && !(o.flags & CHL_FLAG_NO_HYBRID)) {
+    // than the sample's: the block size, then the two switch points of the
+    // phases (the first-phase switch on labels per arc, on or off; the
+    // frontier size below which later phases run the small-tree launch) are
+    // settled by whole builds, one knob at a time.
+    if (!o.root_begin && !o.root_end && !(o.flags & CHL_FLAG_NO_HYBRID)) {
         double best_build = -1.0;
-        int best_tpt = bestP.tpt;
-        for (int t : {256, 512, 1024}) {
-            chl_build_opts q = *best;
-            q.threads_per_tree = t;
+        auto whole = [&](const chl_build_opts &q, double *ms) -> chl_status {
             chl_labels *Lt = nullptr;
-            st = chl_build(g, rank, &q, stream, &Lt);
-            if (st != CHL_OK) goto done;
-            const double ms = Lt->stats.tree_ms;
+            const chl_status r = chl_build(g, rank, &q, stream, &Lt);
+            if (r != CHL_OK) return r;
+            *ms = Lt->stats.tree_ms;
             chl_labels_free(Lt);
             ++trials;
-            if (best_build < 0 || ms < best_build) { best_build = ms; best_tpt = t; }
+            return CHL_OK;
+        };
+        if (!o.threads_per_tree) {
+            int best_tpt = bestP.tpt;
+            for (int t : {256, 512, 1024}) {
+                chl_build_opts q = *best;
+                q.threads_per_tree = t;
+                double ms = 0;
+                if ((st = whole(q, &ms)) != CHL_OK) goto done;
+                if (best_build < 0 || ms < best_build) { best_build = ms; best_tpt = t; }
+            }
+            best->threads_per_tree = best_tpt;
+        } else {
+            if ((st = whole(*best, &best_build)) != CHL_OK) goto done;
         }
-        best->threads_per_tree = best_tpt;
+        if (o.switch_ratio == 0.0f && o.psi_threshold == 0.0f) {
+            chl_build_opts q = *best;
+            q.switch_ratio = -1.0f;  // Psi rule alone
+            double ms = 0;
+            if ((st = whole(q, &ms)) != CHL_OK) goto done;
+            if (ms < best_build) { best_build = ms; best->switch_ratio = -1.0f; }
+        }
+        if (!o.small_tree_expansions) {
+            uint32_t best_small = 0;
+            for (uint32_t x : {2048u, 32768u}) {
+                chl_build_opts q = *best;
+                q.small_tree_expansions = x;
+                double ms = 0;
+                if ((st = whole(q, &ms)) != CHL_OK) goto done;
+                if (ms < best_build) { best_build = ms; best_small = x; }
+            }
+            best->small_tree_expansions = best_small;
+        }
     }
     if (report) {
         report->trials = trials;

@@ -70,7 +70,9 @@ struct TreeLaunch {
     const uint64_t *lt_off;
     const uint2 *lt_e;     // {hub position, distance}
     uint32_t lt_hubs;
-    uint32_t stage_bytes;  // shared-memory staging of the queried lists (multiple of 16)
+    uint32_t aux_bytes;    // dynamic shared memory after the settled bitmap (multiple of 128):
+                           // the staging area, or the root's table distances by hub position
+    uint32_t stage_bytes;  // aux_bytes when the queried lists are staged there, else 0
     // per slot [n], all ones when idle, or null: the root's table labels by
     // hub position, for roots with more of them than the shared-memory hash holds
     uint32_t *lt_root;
@@ -102,8 +104,8 @@ enum : int { ERR_NONE = 0, ERR_DIST_OVERFLOW = 1, ERR_ROUND_LIMIT = 2, ERR_WAIT_
 // launches (defined in chl_tree.cu)
 cudaError_t launch_plant_trees(const TreeLaunch &p, int threads_per_tree, int slots,
                                cudaStream_t s);
-// CTAs per SM of a launch with that bitmap and staging area
-int plant_max_slots_per_sm(int threads_per_tree, uint32_t fin_words, uint32_t stage_bytes);
+// CTAs per SM of a launch with that bitmap and auxiliary area
+int plant_max_slots_per_sm(int threads_per_tree, uint32_t fin_words, uint32_t aux_bytes);
 // roots [begin, begin + count): the label of every trivial root is written to
 // the output (p.out_*, p.out_count; the caller guarantees room for count
 // records), the other roots are appended to list (*list_n of them)
@@ -112,11 +114,11 @@ cudaError_t launch_split_trivial(const TreeLaunch &p, uint32_t begin, uint32_t c
 // dynamic shared memory per CTA (bytes) that keeps the CTAs per SM of a launch
 // without any
 uint32_t plant_dyn_budget(int threads_per_tree);
-// that budget split between the staging area of the queried lists (phases
-// that prune with the label table; at most stage_want bytes, at most half the
-// budget) and the settled-filter bitmap (at most one bit per vertex)
-void plant_smem_split(int threads_per_tree, uint32_t n, uint32_t stage_want, uint32_t *fin_words,
-                      uint32_t *stage_bytes);
+// that budget split between the auxiliary area of phases that prune with the
+// label table (at most aux_want bytes, at most half the budget) and the
+// settled-filter bitmap (at most one bit per vertex)
+void plant_smem_split(int threads_per_tree, uint32_t n, uint32_t aux_want, uint32_t *fin_words,
+                      uint32_t *aux_bytes);
 // Common Label Table entries from label records (those of hub positions < hubs)
 cudaError_t launch_clt_fill(const uint32_t *out_v, const uint32_t *out_h, const uint32_t *out_d,
                             unsigned long long count, const uint32_t *pos_of, uint32_t *hc,
@@ -213,6 +215,14 @@ chl_status set_error(chl_status st, const char *fmt, ...);
 // a failed CUDA call as a status (CHL_ENOMEM for an allocation failure, else
 // CHL_ECUDA) with its message; clears the thread's CUDA last-error state
 chl_status cuda_status(cudaError_t e, const char *what);
+
+// stream-ordered device allocation from the library's pool of the current
+// device (free with cudaFreeAsync or cudaFree)
+cudaError_t dmalloc(void **ptr, size_t bytes, cudaStream_t s);
+template <typename T>
+cudaError_t dmalloc(T **ptr, size_t bytes, cudaStream_t s) {
+    return dmalloc(reinterpret_cast<void **>(ptr), bytes, s);
+}
 
 // SMs of the current device (queried once per device; 1 if the query fails),
 // for sizing grid-stride launches

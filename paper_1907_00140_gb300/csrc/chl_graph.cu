@@ -68,7 +68,7 @@ cudaError_t exclusive_scan_u64(const uint64_t *in, uint64_t *out, uint64_t n, cu
         return cudaGetLastError();
     }
     uint64_t *sums = nullptr;
-    cudaError_t e = cudaMallocAsync(&sums, nb * sizeof(uint64_t), s);
+    cudaError_t e = dmalloc(&sums, nb * sizeof(uint64_t), s);
     if (e != cudaSuccess) return e;
     scan_blocks_kernel<<<unsigned(nb), SCAN_TPB, 0, s>>>(in, out, sums, n);
     if (launches) *launches += 1;
@@ -240,12 +240,12 @@ chl_status prepare_graph(uint32_t n, uint64_t m2, const uint64_t *row, const uin
     g = RankGraph{};
     g.n = n;
     g.m2 = m2;
-    CK(cudaMallocAsync(&chk, sizeof(Check), s));
+    CK(dmalloc(&chk, sizeof(Check), s));
     CK(cudaMemsetAsync(chk, 0, sizeof(Check), s));
-    CK(cudaMallocAsync(&cnt, size_t(n) * sizeof(uint32_t), s));
+    CK(dmalloc(&cnt, size_t(n) * sizeof(uint32_t), s));
     CK(cudaMemsetAsync(cnt, 0, size_t(n) * sizeof(uint32_t), s));
-    CK(cudaMallocAsync(&g.pos_of, size_t(n) * sizeof(uint32_t), s));
-    CK(cudaMallocAsync(&g.vert_at, size_t(n) * sizeof(uint32_t), s));
+    CK(dmalloc(&g.pos_of, size_t(n) * sizeof(uint32_t), s));
+    CK(dmalloc(&g.vert_at, size_t(n) * sizeof(uint32_t), s));
     check_rows_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, m2, row, chk);
     rank_count_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, rank, cnt, chk);
     rank_perm_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, rank, cnt, g.pos_of, g.vert_at, chk);
@@ -276,10 +276,10 @@ chl_status prepare_graph(uint32_t n, uint64_t m2, const uint64_t *row, const uin
         goto done;
     }
     // renumber by rank position
-    CK(cudaMallocAsync(&deg, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CK(cudaMallocAsync(&g.row, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CK(cudaMallocAsync(&g.arc, (m2 ? m2 : 1) * sizeof(uint2), s));
-    CK(cudaMallocAsync(&ws, sizeof(WStats), s));
+    CK(dmalloc(&deg, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CK(dmalloc(&g.row, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CK(dmalloc(&g.arc, (m2 ? m2 : 1) * sizeof(uint2), s));
+    CK(dmalloc(&ws, sizeof(WStats), s));
     CK(cudaMemcpyAsync(ws, &hws, sizeof(WStats), cudaMemcpyHostToDevice, s));
     rank_degree_kernel<<<grid_for(n, 256), 256, 0, s>>>(n, row, g.vert_at, deg);
     *launches += 1;

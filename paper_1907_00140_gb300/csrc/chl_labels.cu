@@ -277,15 +277,15 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
     *too_long = 0;
     out = LabelCSR{};
     const size_t Tb = (T ? T : 1);
-    CKE(cudaMallocAsync(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&out.hub, Tb * sizeof(uint32_t), s));
-    CKE(cudaMallocAsync(&out.hubpos, Tb * sizeof(uint32_t), s));
-    CKE(cudaMallocAsync(&out.dist, Tb * sizeof(uint32_t), s));
-    CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&tmp, Tb * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&lists, 4 * size_t(n) * sizeof(uint32_t), s));
-    CKE(cudaMallocAsync(&counts, 4 * sizeof(uint32_t), s));
-    CKE(cudaMallocAsync(&maxlen, sizeof(unsigned long long), s));
+    CKE(dmalloc(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(dmalloc(&out.hub, Tb * sizeof(uint32_t), s));
+    CKE(dmalloc(&out.hubpos, Tb * sizeof(uint32_t), s));
+    CKE(dmalloc(&out.dist, Tb * sizeof(uint32_t), s));
+    CKE(dmalloc(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(dmalloc(&tmp, Tb * sizeof(uint64_t), s));
+    CKE(dmalloc(&lists, 4 * size_t(n) * sizeof(uint32_t), s));
+    CKE(dmalloc(&counts, 4 * sizeof(uint32_t), s));
+    CKE(dmalloc(&maxlen, sizeof(unsigned long long), s));
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
     CKE(cudaMemsetAsync(counts, 0, 4 * sizeof(uint32_t), s));
     CKE(cudaMemsetAsync(maxlen, 0, sizeof(unsigned long long), s));
@@ -315,7 +315,7 @@ cudaError_t assemble_labels(uint32_t n, uint64_t T, const uint32_t *in_v, const 
         *launches += 1;
     }
     if (hmax > MAX_SEGMENT) {
-        CKE(cudaMallocAsync(&tmp2, Tb * sizeof(uint64_t), s));
+        CKE(dmalloc(&tmp2, Tb * sizeof(uint64_t), s));
         sort_long_kernel<<<sms, 1024, 0, s>>>(lists + 3 * size_t(n), counts + 3, out.offsets, tmp, tmp2);
         *launches += 1;
         CKE(cudaGetLastError());
@@ -348,10 +348,10 @@ cudaError_t assemble_table(uint32_t n, uint64_t T, const uint32_t *in_v, const u
     cudaError_t e = cudaSuccess;
     uint64_t *cnt = nullptr;
     out = LabelTable{};
-    CKE(cudaMallocAsync(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&out.e, (size_t(T) + 2) * sizeof(uint2), s));
+    CKE(dmalloc(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(dmalloc(&out.e, (size_t(T) + 2) * sizeof(uint2), s));
     CKE(cudaMemsetAsync(out.e, 0xFF, (size_t(T) + 2) * sizeof(uint2), s));
-    CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(dmalloc(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
     count_table_kernel<<<grid_for(T, 256), 256, 0, s>>>(T, in_v, in_h, pos_of, min_hub, cnt);
     *launches += 1;
@@ -379,10 +379,10 @@ cudaError_t grow_table(uint32_t n, LabelTable &lt, uint64_t T0, uint64_t T, cons
     uint64_t *cnt = nullptr;
     LabelTable out;
     const uint64_t dT = T - T0;
-    CKE(cudaMallocAsync(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
-    CKE(cudaMallocAsync(&out.e, (size_t(T) + 2) * sizeof(uint2), s));
+    CKE(dmalloc(&out.offsets, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(dmalloc(&out.e, (size_t(T) + 2) * sizeof(uint2), s));
     CKE(cudaMemsetAsync(out.e, 0xFF, (size_t(T) + 2) * sizeof(uint2), s));
-    CKE(cudaMallocAsync(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
+    CKE(dmalloc(&cnt, (size_t(n) + 1) * sizeof(uint64_t), s));
     CKE(cudaMemsetAsync(cnt, 0, (size_t(n) + 1) * sizeof(uint64_t), s));
     if (dT) {
         count_table_kernel<<<grid_for(dT, 256), 256, 0, s>>>(dT, in_v + T0, in_h + T0, pos_of, min_hub,

@@ -132,7 +132,7 @@ struct Shared {
     int fuse_live;         // the current list's first stage also counts its live entries
     int prune;             // this tree prunes by the Common Label Table
     int lt_prune;          // ... and by the label table of earlier phases
-    int lt_dense;          // the root's table labels are in p.lt_root, not the hash
+    int lt_dense;          // the root's table labels: 0 hashed, 1 in p.lt_root, 2 in the shared array
     uint32_t qn;           // table queries queued by the current chunk
     uint32_t stage_used;   // bytes of the staging area reserved by the current batch
     uint32_t bn;           // queries staged in the current batch
@@ -396,6 +396,7 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, Fron
 #pragma unroll
     for (int k = 0; k < UNROLL; ++k)
         if (q[k].live && q[k].cand < q[k].seen && q[k].cand < old[k]) im |= 1u << k;
+    if (!__any_sync(FULL, im != 0)) return;
     const uint32_t c = __popc(im);
     uint32_t x = c;  // inclusive prefix of the per-lane counts
 #pragma unroll
@@ -565,7 +566,9 @@ __device__ void lt_answer(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, u
     constexpr int NW = TPB / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = threadIdx.x;
-    const uint32_t *rootd = S.lt_dense ? p.lt_root + size_t(blockIdx.x) * p.n : nullptr;
+    const uint32_t *rootd = S.lt_dense == 1 ? p.lt_root + size_t(blockIdx.x) * p.n
+                            : S.lt_dense == 2 ? reinterpret_cast<const uint32_t *>(stage)
+                                              : nullptr;
     // the batch's staged queries; the staging keys are free during stage A
     uint32_t *blist = reinterpret_cast<uint32_t *>(F.kv);
     uint64_t la = 0;
@@ -956,19 +959,30 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 for (uint32_t c = threadIdx.x; c < p.hc_stride; c += TPB)
                     S.hch[c] = __ldg(&p.hc[size_t(h) * p.hc_stride + c]);
             if (threadIdx.x == 0) S.prune = prune;
-            // the label table of earlier phases: the root's labels in it, hashed
-            // or (more than the hash holds) in the slot's dense array
+            // the label table of earlier phases: the root's labels in it, as
+            // distances by hub position in shared memory when the table's hubs
+            // fit the auxiliary area (no staging), else hashed or (more than
+            // the hash holds) in the slot's dense array
             bool lt_prune = p.lt_off && h >= p.lt_hubs;
             bool lt_dense = false;
+            const bool lt_shared = lt_prune && !p.stage_bytes && p.lt_hubs <= p.aux_bytes / 4;
             uint64_t lt_a = 0, lt_b = 0;
             if (lt_prune) {
                 lt_a = __ldg(&p.lt_off[h]);
                 lt_b = __ldg(&p.lt_off[h + 1]);
-                lt_dense = lt_b - lt_a > min(LTH_MAX, p.lt_hash_max);  // uniform over the CTA
+                lt_dense = !lt_shared && lt_b - lt_a > min(LTH_MAX, p.lt_hash_max);  // uniform over the CTA
                 lt_prune = !lt_dense || p.lt_root;
                 lt_dense = lt_dense && lt_prune;
             }
-            if (lt_dense) {
+            if (lt_shared) {
+                uint32_t *rs = reinterpret_cast<uint32_t *>(stage);
+                for (uint32_t c = threadIdx.x; c < p.lt_hubs; c += TPB) rs[c] = NONE;
+                __syncthreads();
+                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) {
+                    const uint2 e = __ldg(&p.lt_e[j]);  // hub positions of the table lie below lt_hubs
+                    rs[e.x] = e.y;
+                }
+            } else if (lt_dense) {
                 uint32_t *rootd = p.lt_root + so;
                 for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) {
                     const uint2 e = __ldg(&p.lt_e[j]);
@@ -991,7 +1005,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             }
             if (threadIdx.x == 0) {
                 S.lt_prune = lt_prune;
-                S.lt_dense = lt_dense;
+                S.lt_dense = lt_shared ? 2 : lt_dense ? 1 : 0;
             }
             if (threadIdx.x == 0) {
                 S.cur_n = 1;
@@ -1208,16 +1222,15 @@ cudaError_t allow_smem() {
 
 // dynamic shared memory of a launch: the settled bitmap, then (label-pruned
 // phases) the staging area at the next multiple of 128 bytes
-size_t dyn_bytes(uint32_t fin_words, uint32_t stage_bytes) {
-    return stage_bytes ? ((size_t(fin_words) * 4 + 127) & ~size_t(127)) + stage_bytes
-                       : size_t(fin_words) * 4;
+size_t dyn_bytes(uint32_t fin_words, uint32_t aux_bytes) {
+    return aux_bytes ? ((size_t(fin_words) * 4 + 127) & ~size_t(127)) + aux_bytes : size_t(fin_words) * 4;
 }
 
 template <int TPB>
 cudaError_t launch_t(const TreeLaunch &p, int slots, cudaStream_t s) {
     cudaError_t e = allow_smem<TPB>();
     if (e) return e;
-    const size_t smem = dyn_bytes(p.fin_words, p.stage_bytes);
+    const size_t smem = dyn_bytes(p.fin_words, p.aux_bytes);
     if (p.out_p)
         plant_trees_kernel<TPB, KeyP><<<slots, TPB, smem, s>>>(p);
     else if (p.key_bytes == 4)
@@ -1268,6 +1281,7 @@ cudaError_t launch_plant_trees(const TreeLaunch &p, int tpt, int slots, cudaStre
     // the staging copies read the label table in 16-byte units
     if (p.lt_off && ((reinterpret_cast<uintptr_t>(p.lt_e) & 15) || (p.stage_bytes & 15)))
         return cudaErrorMisalignedAddress;
+    if (p.stage_bytes > p.aux_bytes) return cudaErrorInvalidValue;
     switch (tpt) {
         case 32: return launch_t<32>(p, slots, s);
         case 64: return launch_t<64>(p, slots, s);
@@ -1279,8 +1293,8 @@ cudaError_t launch_plant_trees(const TreeLaunch &p, int tpt, int slots, cudaStre
     }
 }
 
-int plant_max_slots_per_sm(int tpt, uint32_t fin_words, uint32_t stage_bytes) {
-    const size_t bytes = dyn_bytes(fin_words, stage_bytes);
+int plant_max_slots_per_sm(int tpt, uint32_t fin_words, uint32_t aux_bytes) {
+    const size_t bytes = dyn_bytes(fin_words, aux_bytes);
     switch (tpt) {
         case 32: return occ<32>(bytes);
         case 64: return occ<64>(bytes);
@@ -1304,16 +1318,16 @@ uint32_t plant_dyn_budget(int tpt) {
     }
 }
 
-void plant_smem_split(int tpt, uint32_t n, uint32_t stage_want, uint32_t *fin_words,
-                      uint32_t *stage_bytes) {
+void plant_smem_split(int tpt, uint32_t n, uint32_t aux_want, uint32_t *fin_words,
+                      uint32_t *aux_bytes) {
     const uint32_t budget = plant_dyn_budget(tpt);
     const uint32_t want = (n + 31) / 32;
-    const uint32_t stage = std::min<uint32_t>(budget / 2, stage_want) & ~127u;
+    const uint32_t stage = std::min<uint32_t>(budget / 2, aux_want) & ~127u;
     const uint32_t room = budget > stage + 128 ? budget - stage - 128 : 0;
     uint32_t fw = std::min<uint32_t>(want, room / 4);
     if (fw < want) fw &= ~31u;
     *fin_words = fw;
-    *stage_bytes = stage;
+    *aux_bytes = stage;
 }
 
 }  // namespace chl
