@@ -62,6 +62,9 @@ constexpr uint32_t LTH_SLOTS = 1024;  // hash of the root's labels in the label 
 constexpr uint32_t LTH_MAX = 512;     // most root labels the hash holds
 constexpr int QSTEPS = 4;             // label-table query from global memory: loads in flight per lane
 constexpr uint32_t WAIT_LIMIT = 1u << 22;  // polls of a staging barrier before it counts as hung
+#ifndef SMEM_CAP_BYTES
+#define SMEM_CAP_BYTES (132u << 10)
+#endif
 
 // ------------------------------------------------------------------ keys
 // Vertices are numbered by rank position (pos 0 = most important), so in the
@@ -1255,8 +1258,17 @@ int occ(size_t bytes) {
     return b < bp ? b : bp;
 }
 
+// Shared memory per SM that the tree launches may take. The SM's L1 and
+// shared memory are one store: what shared memory does not take is L1, which
+// the kernel's read-only loads (arcs, rows, table rows and entries) go
+// through. Measured on rmat21 (1024-thread slots, one per SM): a settled
+// bitmap of all 1.24M vertices (155 KB) plus a 2-39 KB table area made the
+// label-pruned phases 1.5x slower than the bitmap alone, and a bitmap capped
+// at 100 KB was 11% faster than the whole one.
+constexpr uint32_t SMEM_PER_SM_CAP = SMEM_CAP_BYTES;
+
 // the most dynamic shared memory (a multiple of 128 bytes) that keeps the
-// register-limited number of CTAs per SM
+// register-limited number of CTAs per SM, within SMEM_PER_SM_CAP per SM
 template <int TPB>
 uint32_t dyn_budget_t() {
     const int full = occ<TPB>(0);
@@ -1265,13 +1277,21 @@ uint32_t dyn_budget_t() {
     if (cudaGetDevice(&dev) || cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))
         return 0;
     uint32_t lo = 0, hi = uint32_t(optin) & ~127u;  // occ(lo) == full holds for lo = 0
-    if (occ<TPB>(hi) >= full) return hi;
-    while (hi - lo > 128) {
-        const uint32_t mid = (lo + (hi - lo) / 2) & ~127u;
-        if (mid <= lo) break;
-        if (occ<TPB>(mid) >= full) lo = mid; else hi = mid;
+    if (occ<TPB>(hi) >= full) {
+        lo = hi;
+    } else {
+        while (hi - lo > 128) {
+            const uint32_t mid = (lo + (hi - lo) / 2) & ~127u;
+            if (mid <= lo) break;
+            if (occ<TPB>(mid) >= full) lo = mid; else hi = mid;
+        }
     }
-    return lo;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, plant_trees_kernel<TPB, KeyN>)) return lo;
+    // per CTA: the cap's share, less the static part and the 1 KiB the SM reserves per CTA
+    const int64_t cap = int64_t(SMEM_PER_SM_CAP) / full - int64_t(fa.sharedSizeBytes) - 1024;
+    const uint32_t c = cap > 0 ? uint32_t(cap) & ~127u : 0u;
+    return c < lo ? c : lo;
 }
 
 }  // namespace
