@@ -59,8 +59,9 @@ QUERIES = {"ba2k": 100_000}  # per-step query batch of each workload (default: -
 
 # DRAM read + write bytes of plant_trees_kernel over one whole build (the sum
 # of dram__bytes_read.sum + dram__bytes_write.sum over its launches, one ncu
-# capture of the current kernel source), keyed by workload and the launch
-# parameters it was taken with; other builds report no traffic
+# capture of the current kernel source), keyed by workload, threads per tree,
+# bucket width and whether the build ran label-pruned phases; other builds
+# report no traffic
 TREE_DRAM_BYTES_PER_BUILD = {}
 
 
@@ -302,7 +303,7 @@ def roofline(name, stats, tree_ms, opts, peak, peak_kind):
     if hybrid:
         algo += 8.0 * wu.get("Q", 0.0)
     ach = algo / (tree_ms / 1000.0) / 1e9
-    key = (name, tuple(sorted(opts.items())), bool(hybrid))
+    key = (name, opts.get("threads_per_tree", 0), opts.get("bucket_delta", 0), bool(hybrid))
     traffic = TREE_DRAM_BYTES_PER_BUILD.get(key)
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": traffic,

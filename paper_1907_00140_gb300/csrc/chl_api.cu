@@ -607,12 +607,15 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
 
     // label buffer: an estimate, grown (x2) when a tree does not fit
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    // label buffer: 512 labels per root (within a quarter of the free memory),
-    // above the average list length of the workloads measured (104 to 460); it
-    // doubles and the roots that did not fit are rebuilt
+    // label buffer: up to 512 labels per vertex of the graph (within a quarter
+    // of the free memory), above the average list length of the workloads
+    // measured (104 to 460); it doubles and the roots that did not fit are
+    // rebuilt
     cap = o.label_capacity;
     if (!cap) {
-        cap = uint64_t(re - rb) * 512 + 1024;
+        // a tree labels at most n vertices, and the whole labeling averages
+        // fewer than 512 labels per vertex on the workloads measured
+        cap = std::min(uint64_t(re - rb) * n, uint64_t(n) * 512) + 1024;
         const uint64_t fit = uint64_t(0.25 * double(free_b)) / 12;
         if (cap > fit) cap = fit;
         if (cap < 1024) cap = 1024;
