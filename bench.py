@@ -62,7 +62,9 @@ QUERIES = {"ba2k": 100_000}  # per-step query batch of each workload (default: -
 # capture of the current kernel source), keyed by workload, threads per tree,
 # bucket width and whether the build ran label-pruned phases; other builds
 # report no traffic
-TREE_DRAM_BYTES_PER_BUILD = {}
+TREE_DRAM_BYTES_PER_BUILD = {
+    ("rmat18", 1024, 1, True): 37.766e9 + 10.872e9,
+}
 
 
 def load_peaks():
