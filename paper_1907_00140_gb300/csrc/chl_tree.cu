@@ -55,7 +55,6 @@ namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr uint32_t NWIN_MAX = 64;
-constexpr int UNROLL = 4;
 constexpr uint32_t NONE = 0xFFFFFFFFu;
 constexpr uint32_t CLT_MAX = 64;  // largest Common Label Table (hubs)
 constexpr uint32_t LTH_SLOTS = 1024;  // hash of the root's labels in the label table
@@ -91,9 +90,12 @@ constexpr uint32_t WAIT_LIMIT = 1u << 22;  // polls of a staging barrier before 
 //                 deterministic choice. A candidate carries its source
 //                 vertex in the parent field.
 // All ones is "unreached".
-struct KeyN { using T = uint32_t; static constexpr int S = 1; };
-struct KeyW { using T = uint64_t; static constexpr int S = 1; };
-struct KeyP { using T = uint64_t; static constexpr int S = 32; };
+// U: arcs a lane relaxes per step of the arc pass (its loads in flight); the
+// 8-byte layouts take two, so that a thread's probe state fits its registers
+// at 1024 threads per SM.
+struct KeyN { using T = uint32_t; static constexpr int S = 1; static constexpr int U = 4; };
+struct KeyW { using T = uint64_t; static constexpr int S = 1; static constexpr int U = 2; };
+struct KeyP { using T = uint64_t; static constexpr int S = 32; static constexpr int U = 2; };
 
 template <typename K>
 __device__ __forceinline__ typename K::T key_inf() { return ~typename K::T(0); }
@@ -146,6 +148,11 @@ struct Shared {
     uint32_t lth_val[LTH_SLOTS];
     unsigned long long base;
     uint32_t sub_n[NWIN_MAX];
+    // launch statistics of this CTA, reported once at exit (kept here, not in
+    // registers, which the arc pass needs)
+    unsigned long long n_exp, n_arcs, n_pruned, n_rounds, n_buckets;
+    uint64_t lt_a, lt_b;   // the root's entries in the label table
+    uint32_t n_trees, n_trivial;
 };
 
 // bucket of a distance: a shift when the width is a power of two
@@ -153,11 +160,20 @@ __device__ __forceinline__ uint32_t bucket_of(const TreeLaunch &p, uint32_t d) {
     return p.delta_shift >= 0 ? d >> p.delta_shift : d / p.delta;
 }
 
+// A slot's lists sit back to back, n entries each: l0, l1, far, touch, then
+// the nwin window lists; their addresses are formed where used (fewer
+// registers held across the tree than one pointer per list).
 template <typename K>
 struct Slot {
     typename K::T *key;
     uint32_t *rtag;
-    uint32_t *l0, *l1, *far, *touch, *sub;  // sub: nwin lists of n entries
+    uint32_t *lists;
+    uint32_t n;
+    __device__ __forceinline__ uint32_t *l0() const { return lists; }
+    __device__ __forceinline__ uint32_t *l1() const { return lists + n; }
+    __device__ __forceinline__ uint32_t *far() const { return lists + 2 * size_t(n); }
+    __device__ __forceinline__ uint32_t *touch() const { return lists + 3 * size_t(n); }
+    __device__ __forceinline__ uint32_t *sub(uint32_t s) const { return lists + (4 + size_t(s)) * n; }
 };
 
 template <typename K>
@@ -183,7 +199,7 @@ template <typename K>
 __device__ __forceinline__ void sub_append(Shared &S, const Slot<K> &sl, uint32_t n, uint32_t u,
                                            uint32_t b) {
     const uint32_t s = b - S.win_base;
-    sl.sub[size_t(s) * n + atomicAdd(&S.sub_n[s], 1u)] = u;
+    sl.sub(s)[atomicAdd(&S.sub_n[s], 1u)] = u;
 }
 
 // Relaxation of one arc (v -> u, weight w) of a vertex expanded with distance
@@ -311,7 +327,7 @@ struct Frontier {
 };
 
 // Commit of one warp step, called by all 32 lanes. The atomicMins of all
-// UNROLL probes are issued together (independent, so their round trips
+// K::U probes are issued together (independent, so their round trips
 // overlap). The improvements (typically a few per step of 128 arcs) are then
 // compacted through the warp's shared buffer, so that each is classified by
 // one lane, and the appends to the touched list, nxt, far and the window
@@ -361,16 +377,16 @@ __device__ __forceinline__ void commit_one(const TreeLaunch &p, Shared &S, const
     }
     if (mt) {
         bt = __shfl_sync(FULL, bt, 0);
-        if (touch) sl.touch[bt + __popc(mt & lt)] = u;
+        if (touch) sl.touch()[bt + __popc(mt & lt)] = u;
     }
     if (mn) {
         bn = __shfl_sync(FULL, bn, 0);
-        uint32_t *nxt = S.sel ? sl.l0 : sl.l1;
+        uint32_t *nxt = S.sel ? sl.l0() : sl.l1();
         if (cls == 1) nxt[bn + __popc(mn & lt)] = u;
     }
     if (mf) {
         bf = __shfl_sync(FULL, bf, 0);
-        if (cls == 3) sl.far[bf + __popc(mf & lt)] = u;
+        if (cls == 3) sl.far()[bf + __popc(mf & lt)] = u;
     }
     if (mw) {
         // lanes joining the same window bucket share one counter update
@@ -379,25 +395,25 @@ __device__ __forceinline__ void commit_one(const TreeLaunch &p, Shared &S, const
         uint32_t base = 0;
         if (cls == 2 && lane == ld) base = atomicAdd(&S.sub_n[sx], uint32_t(__popc(g)));
         base = __shfl_sync(FULL, base, ld);
-        if (cls == 2) sl.sub[size_t(sx) * p.n + base + __popc(g & lt)] = u;
+        if (cls == 2) sl.sub(sx)[base + __popc(g & lt)] = u;
     }
 }
 
 template <int TPB, typename K>
 __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F,
                                             const Slot<K> &sl, uint32_t h,
-                                            const Probe<K> (&q)[UNROLL]) {
+                                            const Probe<K> (&q)[K::U]) {
     using KS = typename K::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    KS old[UNROLL];
+    KS old[K::U];
     unsigned im = 0;
 #pragma unroll
-    for (int k = 0; k < UNROLL; ++k) {
+    for (int k = 0; k < K::U; ++k) {
         old[k] = 0;
         if (q[k].live && q[k].cand < q[k].seen) old[k] = atomic_min_key(&sl.key[q[k].u], q[k].cand);
     }
 #pragma unroll
-    for (int k = 0; k < UNROLL; ++k)
+    for (int k = 0; k < K::U; ++k)
         if (q[k].live && q[k].cand < q[k].seen && q[k].cand < old[k]) im |= 1u << k;
     if (!__any_sync(FULL, im != 0)) return;
     const uint32_t c = __popc(im);
@@ -411,7 +427,7 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, Fron
     for (uint32_t b0 = 0; b0 < total; b0 += 32) {
         uint32_t j = x - c;
 #pragma unroll
-        for (int k = 0; k < UNROLL; ++k) {
+        for (int k = 0; k < K::U; ++k) {
             if ((im >> k) & 1u) {
                 if (j >= b0 && j < b0 + 32) {
                     F.iu[warp][j - b0] = q[k].u;
@@ -446,17 +462,6 @@ __device__ __forceinline__ uint32_t owner(const Frontier<TPB, K> &F, uint64_t j,
     return lo;
 }
 
-// Expand the current list once, in chunks of TPB entries. In the first round
-// of a bucket the list is the bucket's window list, whose stale entries (keys
-// since lowered into an earlier bucket) are skipped.
-//
-// Arc pass: a warp walks its piece in steps of STEP = 32 * UNROLL consecutive
-// arcs [i0, i0 + STEP). The rows starting inside a step are found with one
-// ballot per 32 rows and recorded as a STEP-bit mask of start positions; the
-// row of position q is then oa + (set bits at positions <= q), oa being the
-// row that covers i0 (the last row of the previous step). Lanes first load
-// UNROLL arcs, then UNROLL keys, then commit, so each lane has UNROLL
-// independent loads in flight at each stage.
 // Common Label Table pruning (Sec. 5.3): the distance query between the root
 // and v over the table hubs, min_c d(h, c) + d(c, v); the table row of v is
 // read as 16-byte vectors (rows are padded to a multiple of 4 hubs)
@@ -629,27 +634,36 @@ __device__ void lt_answer(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, u
     }
 }
 
+// Expand the current list once, in chunks of TPB entries. In the first round
+// of a bucket the list is the bucket's window list, whose stale entries (keys
+// since lowered into an earlier bucket) are skipped.
+//
+// Arc pass: a warp walks its piece in steps of STEP = 32 * K::U consecutive
+// arcs [i0, i0 + STEP). The rows starting inside a step are found with one
+// ballot per 32 rows and recorded as a STEP-bit mask of start positions; the
+// row of position q is then oa + (set bits at positions <= q), oa being the
+// row that covers i0 (the last row of the previous step). Lanes first load
+// K::U arcs, then K::U keys, then commit, so each lane has K::U
+// independent loads in flight at each stage.
 template <int TPB, typename K>
 __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, const Slot<K> &sl,
-                             uint32_t h, unsigned long long &expanded, unsigned long long &arcs,
-                             unsigned long long &pruned, uint8_t *stage, uint32_t &parity) {
+                             uint32_t h, uint8_t *stage, uint32_t &parity) {
     using KS = typename K::T;
     constexpr int NW = TPB / 32;
-    constexpr uint32_t STEP = 32 * UNROLL;
+    constexpr uint32_t STEP = 32 * K::U;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t *cur = S.cur_slot != NONE ? sl.sub + size_t(S.cur_slot) * p.n
-                                             : (S.sel ? sl.l1 : sl.l0);
-    const uint32_t n_cur = S.cur_n;
-    const uint64_t t_lo = S.t_lo;
-    // the bucket's live entries stop counting as pending when it is entered;
-    // for a list of one chunk this stage counts them (no commit has run yet)
-    const bool fuse = S.fuse_live != 0;
-    for (uint32_t cb = 0; cb < n_cur; cb += TPB) {
+    // The round's list, its length and the bucket start do not change during
+    // the round; they are read from shared memory per chunk rather than held
+    // in registers across the arc pass.
+    for (uint32_t cb = 0; cb < S.cur_n; cb += TPB) {
         // ---- stage the chunk: rows, distances, liveness, degree prefix
+        const uint32_t n_cur = S.cur_n;
+        const uint64_t t_lo = S.t_lo;
+        const uint32_t *cur = S.cur_slot != NONE ? sl.sub(S.cur_slot) : (S.sel ? sl.l1() : sl.l0());
         const uint32_t i = cb + threadIdx.x;
         uint64_t deg = 0, rs = 0;
         uint32_t dv = 0, vid = 0;
-        bool lv = false, clean = false, cut = false, ask = false;
+        bool lv = false, clean = false, cut = false, ask = false, ex = false;
         if (i < n_cur) {
             const uint32_t v = cur[i];
             const KS k = __ldcg(&sl.key[v]);
@@ -662,7 +676,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                 clean = key_clean<K>(k);
                 if (v < p.fin_bits && uint64_t(dv) < t_lo + p.w_min)
                     atomicOr(&fin_bitmap[v >> 5], 1u << (v & 31));
-                ++expanded;
+                ex = true;
                 cut = S.prune && clt_query(p, S, v) <= dv;
                 // a hub of the label table meets the root at the top vertex of
                 // their shortest paths, which outranks v and so is a table hub
@@ -703,13 +717,19 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
         if (cut) {
             // a table hub, which outranks h, lies on a shortest h-v path:
             // v gets no label and is not expanded (Sec. 5.3)
-            ++pruned;
             deg = 0;
             if (clean) atomic_min_key(&sl.key[vid], make_key<K>(dv, false, 0));
         }
         const bool ok = deg != 0;
         const unsigned okm = __ballot_sync(FULL, ok);
-        if (fuse) {
+        {
+            const unsigned em = __ballot_sync(FULL, ex), pm = __ballot_sync(FULL, cut);
+            if (lane == 0 && em) atomicAdd(&S.n_exp, (unsigned long long)__popc(em));
+            if (lane == 0 && pm) atomicAdd(&S.n_pruned, (unsigned long long)__popc(pm));
+        }
+        // the bucket's live entries stop counting as pending when it is entered;
+        // for a list of one chunk this stage counts them (no commit has run yet)
+        if (S.fuse_live) {
             const int c = __popc(__ballot_sync(FULL, lv));
             if (lane == 0 && c) atomicSub(&S.cnt, c);
         }
@@ -757,11 +777,12 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
         const uint64_t lo = per * warp;
         const uint64_t hi = lo + per < total ? lo + per : total;
         if (lo < hi) {
+            if (lane == 0) atomicAdd(&S.n_arcs, (unsigned long long)(hi - lo));
             uint32_t oa = owner(F, lo, 0, nrows);
             for (uint64_t i0 = lo; i0 < hi; i0 += STEP) {
                 const uint32_t span = hi - i0 < STEP ? uint32_t(hi - i0) : STEP;  // positions in this step
-                uint2 a[UNROLL];
-                KS kv[UNROLL];
+                uint2 a[K::U];
+                KS kv[K::U];
                 uint32_t ob = oa;
                 const uint64_t next = oa + 1 < nrows ? F.pre[oa + 1] : ~0ull;
                 if (next >= i0 + span) {
@@ -769,16 +790,16 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                     const uint64_t base = F.base[oa] + i0;
                     const KS k0 = F.kv[oa];
 #pragma unroll
-                    for (int k = 0; k < UNROLL; ++k) {
+                    for (int k = 0; k < K::U; ++k) {
                         const uint32_t q = k * 32 + lane;
                         kv[k] = k0;
                         if (q < span) a[k] = __ldg(&p.arc[base + q]);
                     }
                 } else {
                     // start positions (0..span-1) of rows oa+1, oa+2, ... inside the step
-                    uint32_t wm[UNROLL];
+                    uint32_t wm[K::U];
 #pragma unroll
-                    for (int k = 0; k < UNROLL; ++k) wm[k] = 0;
+                    for (int k = 0; k < K::U; ++k) wm[k] = 0;
                     for (;;) {
                         const uint32_t o = ob + 1 + lane;
                         uint32_t q = STEP;
@@ -788,14 +809,14 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                         }
                         const unsigned m = __ballot_sync(FULL, q < STEP);
 #pragma unroll
-                        for (int k = 0; k < UNROLL; ++k)
+                        for (int k = 0; k < K::U; ++k)
                             wm[k] |= __reduce_or_sync(FULL, (q >> 5) == uint32_t(k) ? 1u << (q & 31) : 0u);
                         ob += __popc(m);
                         if (m != FULL) break;
                     }
                     uint32_t cum = 0;
 #pragma unroll
-                    for (int k = 0; k < UNROLL; ++k) {
+                    for (int k = 0; k < K::U; ++k) {
                         const uint32_t q = k * 32 + lane;
                         if (q < span) {
                             const uint32_t o = oa + cum + __popc(wm[k] & ((2u << lane) - 1u));
@@ -805,13 +826,12 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                         cum += __popc(wm[k]);
                     }
                 }
-                Probe<K> pr[UNROLL];
+                Probe<K> pr[K::U];
 #pragma unroll
-                for (int k = 0; k < UNROLL; ++k) {
+                for (int k = 0; k < K::U; ++k) {
                     pr[k].live = false;
                     if (uint32_t(k * 32 + lane) < span) probe(p, S, sl, kv[k], a[k], pr[k]);
                 }
-                if (lane == 0) arcs += span;
                 commit_step<TPB, K>(p, S, F, sl, h, pr);
                 oa = ob;
             }
@@ -849,7 +869,7 @@ __device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint
         bool keep = false;
         uint32_t u = 0;
         if (i < n_in) {
-            u = sl.far[i];
+            u = sl.far()[i];
             const uint32_t b = bucket_of(p, key_dist<K>(__ldcg(&sl.key[u])));
             if (b < drop_below) {
                 // stale: lowered into the window (and listed there) or expanded
@@ -861,7 +881,7 @@ __device__ void far_pass(const TreeLaunch &p, Shared &S, const Slot<K> &sl, uint
             }
         }
         __syncthreads();  // every entry of this chunk is read before any is rewritten
-        warp_append(keep, u, sl.far, &S.out_n);
+        warp_append(keep, u, sl.far(), &S.out_n);
     }
     __syncthreads();
     mn = warp_min(mn);
@@ -878,7 +898,7 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot<
     __syncthreads();
     if (threadIdx.x == 0) S.live_sum = 0;
     __syncthreads();
-    const uint32_t *lst = sl.sub + size_t(slot) * p.n;
+    const uint32_t *lst = sl.sub(slot);
     const uint32_t cnt = S.sub_n[slot];
     int c = 0;
     for (uint32_t i = threadIdx.x; i < cnt; i += TPB) {
@@ -892,8 +912,11 @@ __device__ void count_live_in_bucket(const TreeLaunch &p, Shared &S, const Slot<
     __syncthreads();
 }
 
+// Register bound: 1024 threads per SM (64 registers a thread). A 32-thread
+// block asks for half that many blocks: shared memory holds fewer than 32 such
+// CTAs per SM anyway, and the thread gets the registers its probe state needs.
 template <int TPB, typename K>
-__global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch p) {
+__global__ void __launch_bounds__(TPB, TPB >= 64 ? 1024 / TPB : 16) plant_trees_kernel(TreeLaunch p) {
     __shared__ Shared S;
     __shared__ Frontier<TPB, K> F;
     const uint32_t n = p.n;
@@ -901,20 +924,16 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
     Slot<K> sl;
     sl.key = (typename K::T *)p.key + so;
     sl.rtag = p.rtag + so;
-    uint32_t *lb = p.lists + so * (4 + p.nwin);
-    sl.l0 = lb;
-    sl.l1 = lb + n;
-    sl.far = lb + 2 * size_t(n);
-    sl.touch = lb + 3 * size_t(n);
-    sl.sub = lb + 4 * size_t(n);
+    sl.lists = p.lists + so * (4 + p.nwin);
+    sl.n = n;
 
-    unsigned long long expanded = 0, arcs = 0, trivial = 0, trees = 0, rounds_all = 0, buckets = 0;
-    unsigned long long pruned = 0;
     uint8_t *stage = reinterpret_cast<uint8_t *>(fin_bitmap) + stage_offset(p.fin_words);
     uint32_t parity = 0;  // phase of S.mbar the next staging batch completes
     if (threadIdx.x == 0) {
         S.rid = p.slot_ctr[blockIdx.x * 4 + 0];
         mbar_init(&S.mbar, TPB);
+        S.n_exp = S.n_arcs = S.n_pruned = S.n_rounds = S.n_buckets = 0;
+        S.n_trees = S.n_trivial = 0;
     }
 
     for (;;) {
@@ -929,7 +948,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
         __syncthreads();
         const uint32_t h = S.root;
         if (h == NONE) break;
-        ++trees;
+        if (threadIdx.x == 0) ++S.n_trees;
 
         // trivial tree: every neighbour outranks the root, so after the root is
         // popped no queued vertex has the root as ancestor (cnt = 0)
@@ -942,12 +961,12 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
 
         uint32_t nlab = 0;
         if (!nontrivial) {
-            ++trivial;
+            if (threadIdx.x == 0) ++S.n_trivial;
             if (threadIdx.x == 0) {
                 S.out_n = 1;
-                sl.l0[0] = h;
-                sl.l1[0] = 0;
-                sl.far[0] = h;  // the root is its own parent
+                sl.l0()[0] = h;
+                sl.l1()[0] = 0;
+                sl.far()[0] = h;  // the root is its own parent
             }
             __syncthreads();
             nlab = 1;
@@ -1009,6 +1028,8 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             if (threadIdx.x == 0) {
                 S.lt_prune = lt_prune;
                 S.lt_dense = lt_shared ? 2 : lt_dense ? 1 : 0;
+                S.lt_a = lt_a;
+                S.lt_b = lt_b;
             }
             if (threadIdx.x == 0) {
                 S.cur_n = 1;
@@ -1027,17 +1048,16 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 S.abort = 0;
                 S.fuse_live = 0;
                 S.qn = 0;
-                sl.l0[0] = h;
-                sl.touch[0] = h;
+                sl.l0()[0] = h;
+                sl.touch()[0] = h;
                 atomic_set_key(&sl.key[h], make_key<K>(0, true, h));
             }
             __syncthreads();
             uint32_t rounds = 0;
             for (;;) {
-                expand_round<TPB, K>(p, S, F, sl, h, expanded, arcs, pruned, stage,
-                                     parity);  // ends with a barrier
+                expand_round<TPB, K>(p, S, F, sl, h, stage, parity);  // ends with a barrier
                 if (S.abort) break;
-                ++rounds_all;
+                if (threadIdx.x == 0) ++S.n_rounds;
                 if (++rounds > p.round_limit) {
                     if (threadIdx.x == 0) atomicExch(&p.flags[0], ERR_ROUND_LIMIT);
                     break;
@@ -1090,7 +1110,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 }
                 // enter bucket min_b: its live vertices stop counting as pending
                 const uint32_t nb = S.min_b, slot = nb - S.win_base;
-                ++buckets;
+                if (threadIdx.x == 0) ++S.n_buckets;
                 const bool fuse = S.sub_n[slot] <= TPB;
                 if (!fuse) count_live_in_bucket<TPB, K>(p, S, sl, h, slot, nb);
                 if (threadIdx.x == 0) {
@@ -1108,9 +1128,9 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
             __syncthreads();
             if (S.abort) {
                 // reset and give up on this tree; the host reports the error
-                for (uint32_t i = threadIdx.x; i < S.touch_n; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
-                if (lt_dense)
-                    for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_e[j]).x] = NONE;
+                for (uint32_t i = threadIdx.x; i < S.touch_n; i += TPB) sl.key[sl.touch()[i]] = key_inf<K>();
+                if (S.lt_dense == 1)
+                    for (uint64_t j = S.lt_a + threadIdx.x; j < S.lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_e[j]).x] = NONE;
                 __threadfence();
                 __syncthreads();
                 break;
@@ -1126,7 +1146,7 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                 bool lv = false;
                 uint32_t u = 0, d = 0, par = 0;
                 if (i < nt) {
-                    u = sl.touch[i];
+                    u = sl.touch()[i];
                     const typename K::T k = __ldcg(&sl.key[u]);
                     lv = is_live<K>(k, u, h);
                     d = key_dist<K>(k);
@@ -1140,18 +1160,18 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
                     b = __shfl_sync(FULL, b, leader);
                     if (lv) {
                         const uint32_t o = b + __popc(m & ((1u << lane) - 1));
-                        sl.l0[o] = u;
-                        sl.l1[o] = d;
-                        if (p.out_p) sl.far[o] = par;  // far is free once the tree stopped
+                        sl.l0()[o] = u;
+                        sl.l1()[o] = d;
+                        if (p.out_p) sl.far()[o] = par;  // far is free once the tree stopped
                     }
                 }
             }
             __syncthreads();
             nlab = S.out_n;
             // reset exactly what this tree modified
-            for (uint32_t i = threadIdx.x; i < nt; i += TPB) sl.key[sl.touch[i]] = key_inf<K>();
-            if (lt_dense)
-                for (uint64_t j = lt_a + threadIdx.x; j < lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_e[j]).x] = NONE;
+            for (uint32_t i = threadIdx.x; i < nt; i += TPB) sl.key[sl.touch()[i]] = key_inf<K>();
+            if (S.lt_dense == 1)
+                for (uint64_t j = S.lt_a + threadIdx.x; j < S.lt_b; j += TPB) p.lt_root[so + __ldg(&p.lt_e[j]).x] = NONE;
             // the next tree reads keys with L2 loads and L2 atomics: the plain
             // reset stores must be visible there first, not only inside the CTA
             __threadfence();
@@ -1173,31 +1193,24 @@ __global__ void __launch_bounds__(TPB, 1024 / TPB) plant_trees_kernel(TreeLaunch
         if (S.ok) {
             const unsigned long long b = S.base;
             for (uint32_t i = threadIdx.x; i < nlab; i += TPB) {
-                p.out_v[b + i] = __ldg(&p.vert_at[sl.l0[i]]);
+                p.out_v[b + i] = __ldg(&p.vert_at[sl.l0()[i]]);
                 p.out_h[b + i] = h;
-                p.out_d[b + i] = sl.l1[i];
-                if (p.out_p) p.out_p[b + i] = __ldg(&p.vert_at[sl.far[i]]);
+                p.out_d[b + i] = sl.l1()[i];
+                if (p.out_p) p.out_p[b + i] = __ldg(&p.vert_at[sl.far()[i]]);
             }
         }
         __syncthreads();
     }
 
-    // counters
-    for (int o = 16; o; o >>= 1) {
-        expanded += __shfl_xor_sync(FULL, expanded, o);
-        arcs += __shfl_xor_sync(FULL, arcs, o);
-        pruned += __shfl_xor_sync(FULL, pruned, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(&p.stats[0], expanded);
-        atomicAdd(&p.stats[1], arcs);
-        if (pruned) atomicAdd(&p.stats[6], pruned);
-    }
+    // counters (every warp's shared-memory adds came before the last barrier)
     if (threadIdx.x == 0) {
-        atomicAdd(&p.stats[2], trivial);
-        atomicAdd(&p.stats[3], trees);
-        atomicAdd(&p.stats[4], rounds_all);
-        atomicAdd(&p.stats[5], buckets);
+        atomicAdd(&p.stats[0], S.n_exp);
+        atomicAdd(&p.stats[1], S.n_arcs);
+        if (S.n_pruned) atomicAdd(&p.stats[6], S.n_pruned);
+        atomicAdd(&p.stats[2], (unsigned long long)S.n_trivial);
+        atomicAdd(&p.stats[3], (unsigned long long)S.n_trees);
+        atomicAdd(&p.stats[4], S.n_rounds);
+        atomicAdd(&p.stats[5], S.n_buckets);
         p.slot_ctr[blockIdx.x * 4 + 0] = S.rid;
     }
 }
