@@ -240,6 +240,8 @@ typedef struct {
  *   phases         tree phases run (1 unless the build is hybrid)
  *   label_table_phases  phases whose trees pruned with the label table of the
  *                  earlier ones (0: the switch threshold was never passed)
+ *   small_tree_phases  label-pruned phases run with the small-tree launch
+ *                  (the switch on small_tree_expansions; 0: it never fired)
  */
 typedef struct {
     uint64_t trees;
@@ -257,6 +259,7 @@ typedef struct {
     double table_ms;
     uint64_t phases;
     uint64_t label_table_phases;
+    uint64_t small_tree_phases;
 } chl_build_stats;
 
 /*

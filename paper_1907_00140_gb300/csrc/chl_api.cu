@@ -526,7 +526,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     LabelTable lt;  // labels of earlier phases (hybrid)
     bool use_lt = false, hybrid = false, hybrid_off = false;
     bool small = false;  // later label-pruned phases run the small-tree launch
-    uint64_t lt_phases = 0;
+    uint64_t lt_phases = 0, small_phases = 0;
     uint64_t lt_records = 0;  // output records the label table holds
     const double psi_th = o.psi_threshold > 0.0f ? double(o.psi_threshold) : PSI_TH;
     uint32_t claimed_upto = 0;
@@ -654,6 +654,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const int ph_lt = lt.offsets ? 1 : 0;
     if (trace) t_ph = now_ms();
     if (lt.offsets) ++lt_phases;
+    if (small) ++small_phases;
     first = true;
     pending.clear();
     for (int attempt = 0;; ++attempt) {
@@ -950,6 +951,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     L->stats.table_ms = ms_table;
     L->stats.phases = phases.size();
     L->stats.label_table_phases = lt_phases;
+    L->stats.small_tree_phases = small_phases;
     L->stats.launches = uint64_t(launches);
     csr = LabelCSR{};
     *out = L;
