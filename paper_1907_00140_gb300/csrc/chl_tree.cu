@@ -320,7 +320,7 @@ struct Frontier {
     typename K::T kv[TPB];  // make_key(distance, liveness, vertex) of the row's vertex
     uint32_t wrows[TPB / 32];
     uint64_t wdeg[TPB / 32];
-    // per warp: the improvements of one step, compacted (vertex, new key, old key)
+    // per warp: improvements waiting to be classified (vertex, new key, old key)
     uint32_t iu[TPB / 32][32];
     typename K::T ic[TPB / 32][32];
     typename K::T io[TPB / 32][32];
@@ -328,12 +328,14 @@ struct Frontier {
 
 // Commit of one warp step, called by all 32 lanes. The atomicMins of all
 // K::U probes are issued together (independent, so their round trips
-// overlap). The improvements (typically a few per step of 128 arcs) are then
-// compacted through the warp's shared buffer, so that each is classified by
-// one lane, and the appends to the touched list, nxt, far and the window
-// buckets take one shared atomic per warp and list (per bucket for the
-// window), the live-pending count one per warp; more than 32 improvements
-// take several passes.
+// overlap). The improvements (typically a few per step of 128 arcs) are
+// appended to the warp's shared buffer, and classified 32 at a time, one per
+// lane: the appends to the touched list, nxt, far and the window buckets then
+// take one shared atomic per warp and list (per bucket for the window), the
+// live-pending count one per warp. Each improvement is classified once with
+// its own old and new key, so the order of classification does not matter;
+// what it appends is read only after the chunk's last barrier, before which
+// the warp classifies what its buffer still holds.
 template <typename K>
 __device__ __forceinline__ void commit_one(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
                                            uint32_t h, bool has, uint32_t u, typename K::T cand,
@@ -399,12 +401,33 @@ __device__ __forceinline__ void commit_one(const TreeLaunch &p, Shared &S, const
     }
 }
 
+// classify the first cnt entries of the warp's buffer
 template <int TPB, typename K>
-__device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F,
-                                            const Slot<K> &sl, uint32_t h,
-                                            const Probe<K> (&q)[K::U]) {
+__device__ __forceinline__ void commit_buffer(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F,
+                                              const Slot<K> &sl, uint32_t h, uint32_t cnt) {
     using KS = typename K::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncwarp();  // every lane's entries are written
+    const bool has = uint32_t(lane) < cnt;
+    uint32_t u = 0;
+    KS cand = 0, o = 0;
+    if (has) {
+        u = F.iu[warp][lane];
+        cand = F.ic[warp][lane];
+        o = F.io[warp][lane];
+    }
+    __syncwarp();  // the buffer is free again
+    commit_one<K>(p, S, sl, h, has, u, cand, o);
+}
+
+// returns the warp's new buffer count (bn before the step, warp-uniform)
+template <int TPB, typename K>
+__device__ __forceinline__ uint32_t commit_step(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F,
+                                                const Slot<K> &sl, uint32_t h,
+                                                const Probe<K> (&q)[K::U], uint32_t bn) {
+    using KS = typename K::T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1;
     KS old[K::U];
     unsigned im = 0;
 #pragma unroll
@@ -415,40 +438,34 @@ __device__ __forceinline__ void commit_step(const TreeLaunch &p, Shared &S, Fron
 #pragma unroll
     for (int k = 0; k < K::U; ++k)
         if (q[k].live && q[k].cand < q[k].seen && q[k].cand < old[k]) im |= 1u << k;
-    if (!__any_sync(FULL, im != 0)) return;
-    const uint32_t c = __popc(im);
-    uint32_t x = c;  // inclusive prefix of the per-lane counts
+    if (!__any_sync(FULL, im != 0)) return bn;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y = __shfl_up_sync(FULL, x, o);
-        if (lane >= o) x += y;
-    }
-    const uint32_t total = __shfl_sync(FULL, x, 31);
-    for (uint32_t b0 = 0; b0 < total; b0 += 32) {
-        uint32_t j = x - c;
-#pragma unroll
-        for (int k = 0; k < K::U; ++k) {
-            if ((im >> k) & 1u) {
-                if (j >= b0 && j < b0 + 32) {
-                    F.iu[warp][j - b0] = q[k].u;
-                    F.ic[warp][j - b0] = q[k].cand;
-                    F.io[warp][j - b0] = old[k];
-                }
-                ++j;
+    for (int k = 0; k < K::U; ++k) {
+        const bool has = (im >> k) & 1u;
+        const unsigned m = __ballot_sync(FULL, has);
+        if (!m) continue;
+        const uint32_t cnt = __popc(m);
+        int pos = int(bn + __popc(m & lt));
+        if (has && pos < 32) {
+            F.iu[warp][pos] = q[k].u;
+            F.ic[warp][pos] = q[k].cand;
+            F.io[warp][pos] = old[k];
+        }
+        if (bn + cnt >= 32) {
+            // the buffer is full: classify it, then keep what did not fit
+            commit_buffer<TPB, K>(p, S, F, sl, h, 32);
+            pos -= 32;
+            if (has && pos >= 0) {
+                F.iu[warp][pos] = q[k].u;
+                F.ic[warp][pos] = q[k].cand;
+                F.io[warp][pos] = old[k];
             }
+            bn = bn + cnt - 32;
+        } else {
+            bn += cnt;
         }
-        __syncwarp();
-        const bool has = lane < total - b0;
-        uint32_t u = 0;
-        KS cand = 0, o = 0;
-        if (has) {
-            u = F.iu[warp][lane];
-            cand = F.ic[warp][lane];
-            o = F.io[warp][lane];
-        }
-        __syncwarp();  // the buffer is free for the next pass
-        commit_one<K>(p, S, sl, h, has, u, cand, o);
     }
+    return bn;
 }
 
 // largest o in [lo, hi) with pre[o] <= j, given pre[lo] <= j
@@ -779,6 +796,7 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
         if (lo < hi) {
             if (lane == 0) atomicAdd(&S.n_arcs, (unsigned long long)(hi - lo));
             uint32_t oa = owner(F, lo, 0, nrows);
+            uint32_t bn = 0;  // improvements in the warp's buffer
             for (uint64_t i0 = lo; i0 < hi; i0 += STEP) {
                 const uint32_t span = hi - i0 < STEP ? uint32_t(hi - i0) : STEP;  // positions in this step
                 uint2 a[K::U];
@@ -832,9 +850,10 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                     pr[k].live = false;
                     if (uint32_t(k * 32 + lane) < span) probe(p, S, sl, kv[k], a[k], pr[k]);
                 }
-                commit_step<TPB, K>(p, S, F, sl, h, pr);
+                bn = commit_step<TPB, K>(p, S, F, sl, h, pr, bn);
                 oa = ob;
             }
+            if (bn) commit_buffer<TPB, K>(p, S, F, sl, h, bn);
         }
         __syncthreads();  // the next chunk rewrites the staging arrays
     }
