@@ -168,6 +168,12 @@ typedef struct chl_labels chl_labels;
  *   small_threads_per_tree threads per tree after that switch (a power of two
  *                          in [32, 1024]); 0 = 256 (or pruned_threads_per_tree
  *                          when smaller)
+ *   big_tree_bucket_delta  bucket width of a label-pruned phase whose previous
+ *                          phase's trees averaged at least 45% of the vertices
+ *                          (big trees: narrow buckets cut the re-expansions of
+ *                          a label-correcting search by more than they add in
+ *                          rounds); 0 = pruned_bucket_delta / 16 (at least 1),
+ *                          negative = pruned_bucket_delta for every phase
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
@@ -213,6 +219,7 @@ typedef struct {
     int32_t query_stage_kb;
     uint32_t small_tree_expansions;
     int32_t small_threads_per_tree;
+    int32_t big_tree_bucket_delta;
 } chl_build_opts;
 
 #define CHL_MAX_COMMON_HUBS 64
@@ -292,15 +299,17 @@ chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opt
  * fastest is kept. For a whole build (no root range set in base) the block
  * size is then settled by whole builds (256, 512 and 1024 threads), since the
  * hybrid phases prune later trees far below the sample's sizes, and then the
- * phases' two switch points, each by whole builds: the first-phase switch
- * (switch_ratio default or off) and the frontier size of the small-tree
- * switch (small_tree_expansions 2048, 8192 or 32768).
+ * phases' switch points, each by whole builds: the first-phase switch
+ * (switch_ratio default or off), the frontier size of the small-tree switch
+ * (small_tree_expansions 2048, 8192 or 32768) and the narrow bucket width
+ * after big trees (big_tree_bucket_delta default or off).
  *   g, rank, stream   as for chl_build
  *   base              fields set (non-zero) are kept fixed; NULL = tune all
  *   best              receives base with threads_per_tree, bucket_delta and
  *                     window_buckets filled in (and, for a whole build,
- *                     switch_ratio and small_tree_expansions when base left
- *                     them 0); pass it to chl_build
+ *                     switch_ratio, small_tree_expansions and
+ *                     big_tree_bucket_delta when base left them 0); pass it
+ *                     to chl_build
  *   report            optional: trials run, sample size, best trial time
  * Errors: as chl_build.
  */

@@ -100,7 +100,8 @@ class chl_build_opts(C.Structure):
                 ("pruned_bucket_delta", C.c_int32), ("psi_threshold", C.c_float),
                 ("pruned_threads_per_tree", C.c_int32), ("switch_ratio", C.c_float),
                 ("round_limit", C.c_uint32), ("query_stage_kb", C.c_int32),
-                ("small_tree_expansions", C.c_uint32), ("small_threads_per_tree", C.c_int32)]
+                ("small_tree_expansions", C.c_uint32), ("small_threads_per_tree", C.c_int32),
+                ("big_tree_bucket_delta", C.c_int32)]
 
 
 class chl_tune_report(C.Structure):
@@ -438,7 +439,7 @@ def tune(g, rank, stream: int | None = None, **fixed):
     base = _build_opts(**fixed)
     best, rep = chl_tune(csr, rkp, base, _current_stream() if stream is None else stream)
     out = {k: getattr(best, k) for k in ("threads_per_tree", "bucket_delta", "window_buckets")}
-    for k in ("switch_ratio", "small_tree_expansions"):
+    for k in ("switch_ratio", "small_tree_expansions", "big_tree_bucket_delta"):
         if getattr(best, k):
             out[k] = getattr(best, k)
     out.update(fixed)

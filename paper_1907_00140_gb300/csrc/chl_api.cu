@@ -137,6 +137,11 @@ constexpr uint32_t DEFAULT_ROUND_LIMIT = 1u << 26;
 // a label-pruned phase whose trees averaged fewer expansions than this hands
 // the later phases to the small-tree launch
 constexpr uint32_t DEFAULT_SMALL_TREE_EXPANSIONS = 8192;
+// a label-pruned phase after one whose trees averaged at least this share of
+// the vertices takes the narrow big-tree bucket width (measured on R-MAT
+// scale 18 and 21: the phases after trees of 0.48 n and more gained, those
+// after trees of 0.43 n and less lost)
+constexpr double BIG_TREE_COVER = 0.45;
 // shared memory per tree slot for the root's table distances by hub position in
 // the label-pruned phases: phases whose table holds at most 16,384 hubs look
 // each entry up with one load instead of a hash probe
@@ -157,6 +162,7 @@ struct Params {
     uint32_t round_limit;
     uint32_t delta;
     uint32_t delta_lt;  // bucket width of the phases that prune with the label table
+    uint32_t delta_big; // ... of such a phase after big trees (0: no separate width)
     uint32_t nwin;
     int slots;
     int kb;  // bytes per tree key: 4 or 8
@@ -189,6 +195,9 @@ Params choose_params(const RankGraph &g, const chl_build_opts &o, int sms, size_
     uint32_t dl = 1;
     while (double(dl) * 1.5 < 2.0 * g.w_mean && dl < (1u << 30)) dl <<= 1;
     p.delta_lt = o.pruned_bucket_delta > 0 ? uint32_t(o.pruned_bucket_delta) : dl;
+    p.delta_big = o.big_tree_bucket_delta > 0   ? uint32_t(o.big_tree_bucket_delta)
+                  : o.big_tree_bucket_delta < 0 ? 0u
+                                                : std::max<uint32_t>(1u, p.delta_lt / 16);
     p.nwin = o.window_buckets > 0 ? uint32_t(o.window_buckets) : 32;
     // 4-byte keys hold distances up to 2^31 - 2; every tentative distance of a
     // tree search is at most w_max * n (a simple path plus one arc)
@@ -526,6 +535,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     LabelTable lt;  // labels of earlier phases (hybrid)
     bool use_lt = false, hybrid = false, hybrid_off = false;
     bool small = false;  // later label-pruned phases run the small-tree launch
+    bool big = false;    // the previous phase's trees were big (BIG_TREE_COVER)
     uint64_t lt_phases = 0, small_phases = 0;
     uint64_t lt_records = 0;  // output records the label table holds
     const double psi_th = o.psi_threshold > 0.0f ? double(o.psi_threshold) : PSI_TH;
@@ -651,6 +661,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const uint64_t exp0 = agg[0], T0 = T, arc0 = agg[1], pr0 = agg[6], rd0 = agg[4], bk0 = agg[5];
     const uint64_t tr0 = agg[3], triv0 = agg[2];
     const bool ph_small = small;
+    const bool ph_narrow = big && P.delta_big && lt.offsets;
     const int ph_lt = lt.offsets ? 1 : 0;
     if (trace) t_ph = now_ms();
     if (lt.offsets) ++lt_phases;
@@ -671,7 +682,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             tl.lt_hubs = pb;
             tl.lt_root = (uint32_t *)b_ltroot.p;
             tl.lt_hash_max = (o.flags & CHL_FLAG_DENSE_ROOT_LABELS) ? 0 : 0xFFFFFFFFu;
-            set_delta(tl, P.delta_lt);
+            set_delta(tl, big && P.delta_big ? P.delta_big : P.delta_lt);
             // dynamic shared memory of this phase's launch: the root's table
             // distances need 4 bytes per hub of the table (or the staging
             // area when asked for); the settled bitmap takes the rest
@@ -838,6 +849,12 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         const uint64_t built = (agg[3] - tr0) - (agg[2] - triv0);
         if (built && double(agg[0] - exp0) / double(built) < double(P.small_exp)) small = true;
     }
+    // the bucket-width switch: the next label-pruned phase's trees are big
+    // when this phase's averaged BIG_TREE_COVER of the vertices
+    {
+        const uint64_t built = (agg[3] - tr0) - (agg[2] - triv0);
+        big = built && double(agg[0] - exp0) / double(built) >= BIG_TREE_COVER * double(n);
+    }
     if (hybrid && !table.buf.p) {
         // the first phase built the table's trees: the Common Label Table from
         // their labels, for every later phase
@@ -882,9 +899,10 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (trace) {
         CUDA_TRY(cudaStreamSynchronize(s));
         std::fprintf(stderr,
-                     "chl phase %zu roots [%u, %u) table %d%s trees %.3f ms assemble %.3f ms "
+                     "chl phase %zu roots [%u, %u) table %d%s%s trees %.3f ms assemble %.3f ms "
                      "expanded %llu arcs %llu labels %llu rounds %llu buckets %llu pruned %llu\n",
-                     ph, pb, pe, ph_lt, ph_small ? " small" : "", t_tree, now_ms() - t_ph - t_tree,
+                     ph, pb, pe, ph_lt, ph_small ? " small" : "", ph_narrow ? " narrow" : "", t_tree,
+                     now_ms() - t_ph - t_tree,
                      (unsigned long long)(agg[0] - exp0), (unsigned long long)(agg[1] - arc0),
                      (unsigned long long)(T - T0), (unsigned long long)(agg[4] - rd0),
                      (unsigned long long)(agg[5] - bk0), (unsigned long long)(agg[6] - pr0));
@@ -1501,10 +1519,11 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     best->window_buckets = int32_t(bestP.nwin);
     best->slots = o.slots;  // 0 keeps the memory-budgeted default at build time
     // A whole build runs in hybrid phases whose pruned trees are far smaller
-    // than the sample's: the block size, then the two switch points of the
-    // phases (the first-phase switch on labels per arc, on or off; the
-    // frontier size below which later phases run the small-tree launch) are
-    // settled by whole builds, one knob at a time.
+    // than the sample's: the block size, then the switch points of the phases
+    // (the first-phase switch on labels per arc, on or off; the frontier size
+    // below which later phases run the small-tree launch; the narrow bucket
+    // width after big trees, on or off) are settled by whole builds, one knob
+    // at a time.
     if (!o.root_begin && !o.root_end && !(o.flags & CHL_FLAG_NO_HYBRID)) {
         double best_build = -1.0;
         auto whole = [&](const chl_build_opts &q, double *ms) -> chl_status {
@@ -1546,6 +1565,13 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
                 if (ms < best_build) { best_build = ms; best_small = x; }
             }
             best->small_tree_expansions = best_small;
+        }
+        if (!o.big_tree_bucket_delta) {
+            chl_build_opts q = *best;
+            q.big_tree_bucket_delta = -1;  // one bucket width for every label-pruned phase
+            double ms = 0;
+            if ((st = whole(q, &ms)) != CHL_OK) goto done;
+            if (ms < best_build) { best_build = ms; best->big_tree_bucket_delta = -1; }
         }
     }
     if (report) {

@@ -1,6 +1,7 @@
 """GPU parity across the hybrid's switch points (Sec. 5.2): wherever the
 first-phase switch (labels per arc, switch_ratio), the Psi switch
-(psi_threshold) and the small-tree switch (small_tree_expansions) fire, the
+(psi_threshold), the small-tree switch (small_tree_expansions) and the
+narrow bucket width after big trees (big_tree_bucket_delta) fire, the
 labels are the canonical ones, bit-exact with the CPU oracle. Only the amount
 of work changes: the label table of earlier phases covers a rank-closed hub
 set whenever it is used (Sec. 5.3), and the small-tree launch runs the same
@@ -67,6 +68,10 @@ SWEEP = [
      lambda s: s["small_tree_phases"] == s["label_table_phases"] - 1),
     (dict(switch_ratio=1e6, small_tree_expansions=ALWAYS_SMALL, small_threads_per_tree=1024,
           pruned_threads_per_tree=256), lambda s: s["small_tree_phases"] == s["label_table_phases"] - 1),
+    # the narrow bucket width after big trees: default, off, set
+    (dict(switch_ratio=1e6, big_tree_bucket_delta=-1), None),
+    (dict(switch_ratio=1e6, big_tree_bucket_delta=1), None),
+    (dict(switch_ratio=1e6, big_tree_bucket_delta=3, pruned_bucket_delta=4096), None),
     # both switches with the other block sizes and bucket widths
     (dict(threads_per_tree=256, switch_ratio=1e6, small_tree_expansions=ALWAYS_SMALL,
           pruned_bucket_delta=1), None),
@@ -94,7 +99,7 @@ def test_tuned_switch_points_are_exact(family):
     name, g, rank, ref, G, R = family
     opts, rep = chl.tune(G, R)
     assert rep["trials"] >= 3
-    for k in ("switch_ratio", "small_tree_expansions"):
+    for k in ("switch_ratio", "small_tree_expansions", "big_tree_bucket_delta"):
         assert k not in opts or opts[k] != 0
     L = chl.build_labels(G, R, **opts)
     assert_same(ref, *L.to_numpy())
