@@ -60,10 +60,9 @@ QUERIES = {"ba2k": 100_000}  # per-step query batch of each workload (default: -
 # DRAM read + write bytes of plant_trees_kernel over one whole build (the sum
 # of dram__bytes_read.sum + dram__bytes_write.sum over its launches, one ncu
 # capture of the current kernel source), keyed by workload, threads per tree,
-# bucket width and whether the build ran label-pruned phases; other builds
-# report no traffic
+# bucket width, whether the build ran label-pruned phases and the big-tree
+# bucket width setting; other builds report no traffic
 TREE_DRAM_BYTES_PER_BUILD = {
-    ("rmat18", 1024, 1, True): 37.766e9 + 10.872e9,
 }
 
 
@@ -305,7 +304,8 @@ def roofline(name, stats, tree_ms, opts, peak, peak_kind):
     if hybrid:
         algo += 8.0 * wu.get("Q", 0.0)
     ach = algo / (tree_ms / 1000.0) / 1e9
-    key = (name, opts.get("threads_per_tree", 0), opts.get("bucket_delta", 0), bool(hybrid))
+    key = (name, opts.get("threads_per_tree", 0), opts.get("bucket_delta", 0), bool(hybrid),
+           opts.get("big_tree_bucket_delta", 0))
     traffic = TREE_DRAM_BYTES_PER_BUILD.get(key)
     return {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
             "traffic": traffic,

@@ -98,6 +98,7 @@ enum : uint32_t {
 struct Check {
     uint32_t bits;
     uint32_t where;  // a vertex where the first failure was seen (any)
+    unsigned long long fp;  // symmetry fingerprint: sum of h(v, u, w) - h(u, v, w) over the arcs
 };
 
 __device__ void fail(Check *c, uint32_t bit, uint32_t v) {
@@ -112,12 +113,27 @@ __global__ void check_rows_kernel(uint32_t n, uint64_t m2, const uint64_t *row, 
     }
 }
 
-// one warp per vertex: ids, weights, strictly increasing rows, no self-loop,
-// and the reverse arc with the same weight (binary search in the target row)
+// 64-bit mix of an arc (the splitmix64 finaliser of Steele, Lea and Flood)
+__device__ __forceinline__ unsigned long long arc_hash(uint32_t a, uint32_t b, uint32_t wt) {
+    unsigned long long x = ((unsigned long long)a << 32 | b) ^ ((unsigned long long)wt * 0x9E3779B97F4A7C15ull);
+    x ^= x >> 30;
+    x *= 0xBF58476D1CE4E5B9ull;
+    x ^= x >> 27;
+    x *= 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// One warp per vertex: ids, weights, strictly increasing rows, no self-loop,
+// in one streaming pass. Symmetry by fingerprint: the arcs (v, u, w) form
+// the same multiset as their reverses (u, v, w) iff the graph is undirected
+// with equal weights both ways, so the sum of h(v, u, w) - h(u, v, w) is 0
+// for every undirected graph; any other sum proves an arc without its
+// reverse, which check_symm_kernel then locates.
 __global__ void check_arcs_kernel(uint32_t n, const uint64_t *row, const uint32_t *col,
                                   const uint32_t *w, Check *c) {
     const int lane = threadIdx.x & 31;
     const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    unsigned long long fp = 0;
     for (uint64_t v = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
         const uint64_t a = row[v], b = row[v + 1];
         for (uint64_t e = a + lane; e < b; e += 32) {
@@ -126,6 +142,25 @@ __global__ void check_arcs_kernel(uint32_t n, const uint64_t *row, const uint32_
             if (wt == 0) fail(c, BAD_WEIGHT, uint32_t(v));
             if (u == v) fail(c, BAD_SELF, uint32_t(v));
             if (e > a && col[e - 1] >= u) fail(c, BAD_ORDER, uint32_t(v));
+            fp += arc_hash(uint32_t(v), u, wt) - arc_hash(u, uint32_t(v), wt);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) fp += __shfl_xor_sync(0xffffffffu, fp, o);
+    if (lane == 0 && fp) atomicAdd(&c->fp, fp);
+}
+
+// exact symmetry check, run only when the fingerprint is not 0: the reverse
+// arc with the same weight by binary search in the target row
+__global__ void check_symm_kernel(uint32_t n, const uint64_t *row, const uint32_t *col,
+                                  const uint32_t *w, Check *c) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+    for (uint64_t v = (uint64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; v < n; v += warps) {
+        const uint64_t a = row[v], b = row[v + 1];
+        for (uint64_t e = a + lane; e < b; e += 32) {
+            const uint32_t u = col[e], wt = w[e];
+            if (u >= n) continue;
             uint64_t lo = row[u], hi = row[u + 1];
             bool found = false;
             while (lo < hi) {
@@ -232,7 +267,7 @@ chl_status prepare_graph(uint32_t n, uint64_t m2, const uint64_t *row, const uin
                          int *launches) {
     chl_status st = CHL_OK;
     Check *chk = nullptr;
-    Check hchk{0, 0};
+    Check hchk{0, 0, 0};
     uint32_t *cnt = nullptr;
     uint64_t *deg = nullptr;
     WStats *ws = nullptr;
@@ -266,6 +301,15 @@ chl_status prepare_graph(uint32_t n, uint64_t m2, const uint64_t *row, const uin
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&hchk, chk, sizeof(Check), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    if (!(hchk.bits & BAD_COL) && hchk.fp) {
+        // some arc has no reverse of equal weight: find a vertex that shows it
+        check_symm_kernel<<<grid_for(uint64_t(n) * 32, 256), 256, 0, s>>>(n, row, col, w, chk);
+        *launches += 1;
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(&hchk, chk, sizeof(Check), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (!hchk.bits) hchk.bits = BAD_SYMM;  // (a non-zero sum always has a cause)
+    }
     if (hchk.bits) {
         const char *what = (hchk.bits & BAD_COL)      ? "a neighbour id is >= n"
                            : (hchk.bits & BAD_WEIGHT) ? "a weight is 0 (weights must be positive)"

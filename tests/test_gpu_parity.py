@@ -259,6 +259,32 @@ def test_rejects_malformed_inputs():
     assert _status(row, rank) == chl.CHL_EINVAL
 
 
+def test_asymmetric_arcs_found_in_a_large_graph(ba2k):
+    """The symmetry check streams a fingerprint of the arcs and their
+    reverses; an arc whose reverse differs in weight, or is missing, still
+    comes back as CHL_EINVAL naming a vertex with such an arc."""
+    g, rank, _ = ba2k
+    W_ = type(g)
+    heavy = W_(g.n, g.row_ptr, g.col, g.w.copy())
+    heavy.w[len(g.w) // 2] += 1
+    with pytest.raises(chl.ChlError) as e:
+        chl.build_labels(heavy, rank)
+    assert e.value.status == chl.CHL_EINVAL and "reverse arc" in str(e.value)
+    # drop the last arc of a middle row: the row stays sorted, its reverse is left alone
+    v = g.n // 2
+    a, b = int(g.row_ptr[v]), int(g.row_ptr[v + 1])
+    keep = np.ones(len(g.col), bool)
+    keep[b - 1] = False
+    row = g.row_ptr.copy()
+    row[v + 1:] -= 1
+    missing = W_(g.n, row, g.col[keep].copy(), g.w[keep].copy())
+    with pytest.raises(chl.ChlError) as e:
+        chl.build_labels(missing, rank)
+    assert e.value.status == chl.CHL_EINVAL and "reverse arc" in str(e.value)
+    # the unchanged graph passes the same check
+    chl.build_labels(g, rank).free()
+
+
 def test_distance_overflow_is_reported():
     big = 2 ** 31
     g = from_edges(4, [(0, 1, big), (1, 2, big), (2, 3, 5)])
