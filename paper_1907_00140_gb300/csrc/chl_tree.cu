@@ -288,21 +288,22 @@ __device__ __forceinline__ void bulk_to_shared(void *dst, const void *src, uint3
 // (u, w) is kv + 2w (the clean bit rides along in bit 0). With 4-byte keys
 // the host has proven every tentative distance below the key limit
 // (w_max * n < 2^31 - 1), so only the wide form checks for overflow.
+// Written without early exits (predicates instead), so that a step's K::U
+// probes form no divergent regions; valid: the lane has an arc at this index.
 template <typename K>
 __device__ __forceinline__ void probe(const TreeLaunch &p, Shared &S, const Slot<K> &sl,
-                                      typename K::T kv, uint2 a, Probe<K> &q) {
+                                      typename K::T kv, uint2 a, bool valid, Probe<K> &q) {
     using KS = typename K::T;
     q.u = a.x;
-    q.live = false;
-    if (sizeof(KS) == 8 && uint64_t(key_dist<K>(kv)) + a.y > key_dist_limit<K>()) {
+    if (sizeof(KS) == 8 && valid && uint64_t(key_dist<K>(kv)) + a.y > key_dist_limit<K>()) {
         atomicExch(&p.flags[0], ERR_DIST_OVERFLOW);
         S.abort = 1;
-        return;
+        valid = false;
     }
-    if (q.u < p.fin_bits && ((fin_bitmap[q.u >> 5] >> (q.u & 31)) & 1u)) return;
+    const uint32_t word = valid && q.u < p.fin_bits ? fin_bitmap[q.u >> 5] : 0u;
+    q.live = valid && !((word >> (q.u & 31)) & 1u);
     q.cand = kv + (KS(a.y) << K::S);
-    q.seen = __ldcg(&sl.key[q.u]);
-    q.live = true;
+    q.seen = q.live ? __ldcg(&sl.key[q.u]) : KS(0);
 }
 
 // Frontier staging of one chunk of up to TPB list entries, compacted to the
@@ -801,6 +802,11 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                 const uint32_t span = hi - i0 < STEP ? uint32_t(hi - i0) : STEP;  // positions in this step
                 uint2 a[K::U];
                 KS kv[K::U];
+#pragma unroll
+                for (int k = 0; k < K::U; ++k) {
+                    a[k] = make_uint2(0, 0);
+                    kv[k] = 0;
+                }
                 uint32_t ob = oa;
                 const uint64_t next = oa + 1 < nrows ? F.pre[oa + 1] : ~0ull;
                 if (next >= i0 + span) {
@@ -846,10 +852,8 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                 }
                 Probe<K> pr[K::U];
 #pragma unroll
-                for (int k = 0; k < K::U; ++k) {
-                    pr[k].live = false;
-                    if (uint32_t(k * 32 + lane) < span) probe(p, S, sl, kv[k], a[k], pr[k]);
-                }
+                for (int k = 0; k < K::U; ++k)
+                    probe(p, S, sl, kv[k], a[k], uint32_t(k * 32 + lane) < span, pr[k]);
                 bn = commit_step<TPB, K>(p, S, F, sl, h, pr, bn);
                 oa = ob;
             }
