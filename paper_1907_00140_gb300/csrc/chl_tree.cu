@@ -219,6 +219,26 @@ struct Probe {
 };
 
 __device__ __forceinline__ uint32_t atomic_min_key(uint32_t *a, uint32_t v) { return atomicMin(a, v); }
+// atomicMin under a predicate, as one predicated instruction (no branch
+// around it); returns `none` where the predicate is false
+__device__ __forceinline__ uint32_t atomic_min_key_if(bool on, uint32_t *a, uint32_t v, uint32_t none) {
+    uint32_t old = none;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t@p atom.global.min.u32 %0, [%1], %2;\n\t}"
+        : "+r"(old)
+        : "l"(a), "r"(v), "r"(uint32_t(on))
+        : "memory");
+    return old;
+}
+__device__ __forceinline__ uint64_t atomic_min_key_if(bool on, uint64_t *a, uint64_t v, uint64_t none) {
+    uint64_t old = none;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %3, 0;\n\t@p atom.global.min.u64 %0, [%1], %2;\n\t}"
+        : "+l"(old)
+        : "l"(a), "l"(v), "r"(uint32_t(on))
+        : "memory");
+    return old;
+}
 __device__ __forceinline__ uint64_t atomic_min_key(uint64_t *a, uint64_t v) {
     return atomicMin((unsigned long long *)a, (unsigned long long)v);
 }
@@ -432,10 +452,8 @@ __device__ __forceinline__ uint32_t commit_step(const TreeLaunch &p, Shared &S, 
     KS old[K::U];
     unsigned im = 0;
 #pragma unroll
-    for (int k = 0; k < K::U; ++k) {
-        old[k] = 0;
-        if (q[k].live && q[k].cand < q[k].seen) old[k] = atomic_min_key(&sl.key[q[k].u], q[k].cand);
-    }
+    for (int k = 0; k < K::U; ++k)
+        old[k] = atomic_min_key_if(q[k].live && q[k].cand < q[k].seen, &sl.key[q[k].u], q[k].cand, KS(0));
 #pragma unroll
     for (int k = 0; k < K::U; ++k)
         if (q[k].live && q[k].cand < q[k].seen && q[k].cand < old[k]) im |= 1u << k;
@@ -838,15 +856,17 @@ __device__ void expand_round(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F
                         ob += __popc(m);
                         if (m != FULL) break;
                     }
+                    // every lane's row index stays below nrows (only row starts
+                    // inside the span are counted), so the shared-memory reads
+                    // need no guard; the arc load does
                     uint32_t cum = 0;
 #pragma unroll
                     for (int k = 0; k < K::U; ++k) {
                         const uint32_t q = k * 32 + lane;
-                        if (q < span) {
-                            const uint32_t o = oa + cum + __popc(wm[k] & ((2u << lane) - 1u));
-                            kv[k] = F.kv[o];
-                            a[k] = __ldg(&p.arc[F.base[o] + i0 + q]);
-                        }
+                        const uint32_t o = oa + cum + __popc(wm[k] & ((2u << lane) - 1u));
+                        kv[k] = F.kv[o];
+                        const uint64_t ai = F.base[o] + i0 + q;
+                        if (q < span) a[k] = __ldg(&p.arc[ai]);
                         cum += __popc(wm[k]);
                     }
                 }
