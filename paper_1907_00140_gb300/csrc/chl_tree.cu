@@ -560,8 +560,20 @@ __device__ __forceinline__ bool lt_prunes_warp(const TreeLaunch &p, const Shared
             x[u] = j < b ? __ldg(&p.lt_e[j]) : make_uint2(0, NONE);
         }
         bool hit = false;
+        if (rootd) {
+            // the root's distances by hub position: one predicated load per
+            // entry (no divergent region); fillers and entries beyond dv
+            // read nothing
 #pragma unroll
-        for (int u = 0; u < QSTEPS; ++u) hit |= lt_hit(S, rootd, x[u].x, x[u].y, dv);
+            for (int u = 0; u < QSTEPS; ++u) {
+                const bool near = x[u].y <= dv;
+                const uint32_t dhc = near ? rootd[x[u].x] : NONE;
+                hit |= dhc != NONE && uint64_t(dhc) + x[u].y <= dv;
+            }
+        } else {
+#pragma unroll
+            for (int u = 0; u < QSTEPS; ++u) hit |= lt_hit(S, rootd, x[u].x, x[u].y, dv);
+        }
         if (__any_sync(0xffffffffu, hit)) return true;
     }
     return false;
