@@ -63,6 +63,7 @@ QUERIES = {"ba2k": 100_000}  # per-step query batch of each workload (default: -
 # bucket width, whether the build ran label-pruned phases and the big-tree
 # bucket width setting; other builds report no traffic
 TREE_DRAM_BYTES_PER_BUILD = {
+    ("rmat18", 1024, 1, True, 0): 31.903e9 + 8.797e9,
 }
 
 
