@@ -174,6 +174,11 @@ typedef struct chl_labels chl_labels;
  *                          a label-correcting search by more than they add in
  *                          rounds); 0 = pruned_bucket_delta / 16 (at least 1),
  *                          negative = pruned_bucket_delta for every phase
+ *   overlap_phases         0 = on: while a label-pruned phase's last trees run,
+ *                          the SMs they leave idle start the next phase's
+ *                          first trees on a second stream, pruned by the
+ *                          current (older) table; the labels are the same.
+ *                          Negative = off (each phase waits for the last)
  */
 /* chl_build_opts.flags: use 8-byte tree keys even where 4-byte keys hold
    every distance (the library picks 4 bytes when w_max * n < 2^31 - 1; the
@@ -220,6 +225,7 @@ typedef struct {
     uint32_t small_tree_expansions;
     int32_t small_threads_per_tree;
     int32_t big_tree_bucket_delta;
+    int32_t overlap_phases;
 } chl_build_opts;
 
 #define CHL_MAX_COMMON_HUBS 64

@@ -101,7 +101,7 @@ class chl_build_opts(C.Structure):
                 ("pruned_threads_per_tree", C.c_int32), ("switch_ratio", C.c_float),
                 ("round_limit", C.c_uint32), ("query_stage_kb", C.c_int32),
                 ("small_tree_expansions", C.c_uint32), ("small_threads_per_tree", C.c_int32),
-                ("big_tree_bucket_delta", C.c_int32)]
+                ("big_tree_bucket_delta", C.c_int32), ("overlap_phases", C.c_int32)]
 
 
 class chl_tune_report(C.Structure):

@@ -304,6 +304,7 @@ struct SlotState {
         tl.rtag = (uint32_t *)tags.p;
         tl.lists = (uint32_t *)lists.p;
         tl.slot_ctr = (uint32_t *)ctr.p;
+        tl.dyn_slots = 1;  // each CTA takes a free slot, so that launches may overlap
     }
     void release() {
         key.release();
@@ -311,6 +312,25 @@ struct SlotState {
         lists.release();
         ctr.release();
     }
+};
+
+// The next phase's first trees, started in the tail of a label-pruned phase on
+// a second stream: while the phase's last trees run, most SMs would idle. They
+// prune with the current phase's table (its hubs are a rank-closed set, so
+// the labels are the same; the next phase's fresher table would only prune
+// more), take roots from the counter the rest of their phase then shares, and
+// write their labels to buffers of their own, appended after their phase, so
+// that every phase's records stay one range for the table's growth. They stop
+// claiming roots once the current phase's launch is done.
+struct Filler {
+    DevBuf ctl, fail, roots, ov, oh, od, op, stop;
+    uint64_t cap = 0;     // records the output buffers hold
+    uint32_t roots_cap = 0;
+    bool active = false;
+    uint32_t pb = 0, pe = 0;  // the phase whose first trees these are
+    cudaEvent_t ev_clear = nullptr, ev_split = nullptr, ev_done = nullptr;
+    LabelTable old;           // a table grown while these trees read it: freed after them
+    Control hc{};
 };
 
 // default expansions per label of a phase above which the next phases prune
@@ -541,6 +561,9 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     const double psi_th = o.psi_threshold > 0.0f ? double(o.psi_threshold) : PSI_TH;
     uint32_t claimed_upto = 0;
     bool first = true;
+    Filler fill[2];                  // next-phase trees in a phase's tail, by phase parity
+    cudaStream_t s2 = nullptr;       // ... and their stream
+    bool overlap = false;
     bool listed = false;             // the current attempt runs from the device root list
     std::vector<uint32_t> list_h;    // ... whose host copy, when needed
     uint32_t list_n = 0;
@@ -642,6 +665,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     // earlier phases (a rank-closed hub set, so the labels stay canonical)
     // once the switch has fired. Other builds run as one phase.
     hybrid = rb == 0 && P.eta && !(o.flags & CHL_FLAG_NO_HYBRID) && re > P.eta;
+    overlap = hybrid && o.mode == 0 && o.overlap_phases >= 0;
     // the Common Label Table is needed when some requested tree lies outside
     // it; a hybrid build takes it from its first phase instead
     if (P.eta && re > P.eta && !hybrid) {
@@ -668,6 +692,19 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     if (small) ++small_phases;
     first = true;
     pending.clear();
+    // a filler launched in the previous phase's tail built this phase's first trees
+    Filler &fin = fill[(ph + 1) & 1];
+    const bool from_filler = fin.active && fin.pb == pb && fin.pe == pe;
+    bool filler_merged = false;
+    for (Filler &f : fill) {
+        if (f.active && !(from_filler && &f == &fin)) {
+            // trees for a phase that did not follow: their roots are built
+            // again by their own phase, their labels are dropped
+            CUDA_TRY(cudaEventSynchronize(f.ev_done));
+            f.active = false;
+            free_table(f.old, s);
+        }
+    }
     for (int attempt = 0;; ++attempt) {
         TreeLaunch tl{};
         tl.n = n;
@@ -699,7 +736,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         }
         // the batched form first writes the labels of the phase's trivial
         // roots and lists the others: room for one record per root
-        const bool split = first && o.mode == 0 && pe > pb;
+        const bool split = first && o.mode == 0 && pe > pb && !from_filler;
         if (split && cap < T + (pe - pb)) {
             uint64_t ncap = cap;
             while (ncap < T + (pe - pb)) ncap *= 2;
@@ -726,7 +763,20 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         }
         uint32_t count = 0;
         listed = !first;
-        if (split) {
+        if (first && from_filler) {
+            // the filler's split listed this phase's roots and counts them on
+            // the device; the filler's claim counter is shared
+            CUDA_TRY(cudaStreamWaitEvent(s, fin.ev_split, 0));
+            if (small) CUDA_TRY(cudaStreamWaitEvent(s, fin.ev_done, 0));  // another slot layout
+            Control *fctl = (Control *)fin.ctl.p;
+            tl.root_list = (const uint32_t *)fin.roots.p;
+            tl.root_begin = 0;
+            tl.count_dev = &fctl->list_n;
+            tl.next_root = &fctl->next_root;
+            count = pe - pb;  // a bound: the kernel reads the listed count
+            listed = true;
+            list_h.clear();
+        } else if (split) {
             CUDA_TRY(launch_split_trivial(tl, pb, pe - pb, (uint32_t *)b_roots.p, &ctl->list_n, s));
             ++launches;
             CUDA_TRY(cudaMemcpyAsync(&list_n, &ctl->list_n, 4, cudaMemcpyDeviceToHost, s));
@@ -762,8 +812,68 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
                     ++launches;
                 }
             } else if (lt.offsets) {
+                // the next phase's first trees fill this launch's tail (see Filler)
+                const uint64_t nx = std::min<uint64_t>(
+                    std::max<uint64_t>(uint64_t(pe) * 2, uint64_t(pe) + uint64_t(P.slots) * 2), re);
+                const bool filler = overlap && first && !small && use_lt && pe < re;
+                Filler &fo = fill[ph & 1];
+                if (filler) {
+                    if (!s2) {
+                        CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+                        for (Filler &f : fill) {
+                            CUDA_TRY(cudaEventCreateWithFlags(&f.ev_clear, cudaEventDisableTiming));
+                            CUDA_TRY(cudaEventCreateWithFlags(&f.ev_split, cudaEventDisableTiming));
+                            CUDA_TRY(cudaEventCreateWithFlags(&f.ev_done, cudaEventDisableTiming));
+                        }
+                    }
+                    if (!fo.ctl.p) {
+                        fo.ctl.s = fo.fail.s = fo.roots.s = fo.ov.s = fo.oh.s = fo.od.s = fo.op.s = fo.stop.s = s;
+                        fo.roots_cap = re - rb + 1;
+                        // labels of the trees that fit: a tree that does not fit is built again later
+                        fo.cap = std::min<uint64_t>(cap, uint64_t(32) << 20) + fo.roots_cap;
+                        CUDA_TRY(dmalloc(&fo.ctl.p, sizeof(Control), s));
+                        CUDA_TRY(dmalloc(&fo.fail.p, size_t(fo.roots_cap) * 4, s));
+                        CUDA_TRY(dmalloc(&fo.roots.p, size_t(fo.roots_cap) * 4, s));
+                        CUDA_TRY(dmalloc(&fo.ov.p, fo.cap * 4, s));
+                        CUDA_TRY(dmalloc(&fo.oh.p, fo.cap * 4, s));
+                        CUDA_TRY(dmalloc(&fo.od.p, fo.cap * 4, s));
+                        if (parents) CUDA_TRY(dmalloc(&fo.op.p, fo.cap * 4, s));
+                        CUDA_TRY(dmalloc(&fo.stop.p, sizeof(int), s));
+                    }
+                    CUDA_TRY(cudaMemsetAsync(fo.stop.p, 0, sizeof(int), s));
+                    CUDA_TRY(cudaMemsetAsync(fo.ctl.p, 0, sizeof(Control), s));
+                    CUDA_TRY(cudaEventRecord(fo.ev_clear, s));
+                }
                 CUDA_TRY(launch_plant_trees(tl, small ? P.tpt_sm : P.tpt_lt, small ? P.slots_sm : P.slots_lt, s));
                 ++launches;
+                if (filler) {
+                    // stop claiming once this launch is done (ordered after it on s)
+                    CUDA_TRY(cudaMemsetAsync(fo.stop.p, 1, sizeof(int), s));
+                    Control *fctl = (Control *)fo.ctl.p;
+                    TreeLaunch tf = tl;  // this phase's table and launch shape
+                    tf.out_v = (uint32_t *)fo.ov.p;
+                    tf.out_h = (uint32_t *)fo.oh.p;
+                    tf.out_d = (uint32_t *)fo.od.p;
+                    tf.out_p = (uint32_t *)fo.op.p;
+                    tf.out_cap = fo.cap;
+                    bind_control(tf, fctl);
+                    tf.failed = (uint32_t *)fo.fail.p;
+                    tf.stop = (const int *)fo.stop.p;
+                    CUDA_TRY(cudaStreamWaitEvent(s2, fo.ev_clear, 0));
+                    CUDA_TRY(launch_split_trivial(tf, pe, uint32_t(nx - pe), (uint32_t *)fo.roots.p,
+                                                  &fctl->list_n, s2));
+                    CUDA_TRY(cudaEventRecord(fo.ev_split, s2));
+                    tf.root_list = (const uint32_t *)fo.roots.p;
+                    tf.root_begin = 0;
+                    tf.root_count = uint32_t(nx - pe);
+                    tf.count_dev = &fctl->list_n;
+                    CUDA_TRY(launch_plant_trees(tf, P.tpt_lt, P.slots_lt, s2));
+                    CUDA_TRY(cudaEventRecord(fo.ev_done, s2));
+                    launches += 2;
+                    fo.active = true;
+                    fo.pb = pe;
+                    fo.pe = uint32_t(nx);
+                }
             } else {
                 CUDA_TRY(launch_plant_trees(tl, P.tpt, P.slots, s));
                 ++launches;
@@ -785,17 +895,69 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             goto done;
         }
         T = records_kept(hc);
-        if (!hc.flags[1]) break;  // every root of this attempt fit
+        std::vector<uint32_t> ffailed;  // the filler's trees that did not fit its buffer
+        if (first && from_filler && !filler_merged) {
+            // the filler's trees are this phase's too: wait for them, then take
+            // their statistics, append their labels after this launch's, and
+            // count the shared claim counter and root list as this attempt's
+            CUDA_TRY(cudaEventSynchronize(fin.ev_done));
+            CUDA_TRY(cudaMemcpy(&fin.hc, fin.ctl.p, sizeof(Control), cudaMemcpyDeviceToHost));
+            for (int k = 0; k < 7; ++k) agg[k] += fin.hc.stats[k];
+            if (fin.hc.flags[0] == ERR_DIST_OVERFLOW) {
+                st = set_error(CHL_EOVERFLOW, "a shortest distance reaches UINT32_MAX");
+                goto done;
+            }
+            if (fin.hc.flags[0]) {
+                st = set_error(CHL_ETIMEOUT, "a tree exceeded its round limit or a staging wait (code %d)",
+                               fin.hc.flags[0]);
+                goto done;
+            }
+            const uint64_t Tf = records_kept(fin.hc);
+            if (Tf) {
+                if (cap < T + Tf) {
+                    uint64_t ncap = cap;
+                    while (ncap < T + Tf) ncap *= 2;
+                    void *bufs[4] = {b_ov.p, b_oh.p, b_od.p, b_op.p};
+                    CUDA_TRY(grow_records(bufs, parents ? 4 : 3, T, ncap, s));
+                    b_ov.p = bufs[0];
+                    b_oh.p = bufs[1];
+                    b_od.p = bufs[2];
+                    b_op.p = bufs[3];
+                    cap = ncap;
+                }
+                CUDA_TRY(cudaMemcpyAsync((uint32_t *)b_ov.p + T, fin.ov.p, Tf * 4, cudaMemcpyDeviceToDevice, s));
+                CUDA_TRY(cudaMemcpyAsync((uint32_t *)b_oh.p + T, fin.oh.p, Tf * 4, cudaMemcpyDeviceToDevice, s));
+                CUDA_TRY(cudaMemcpyAsync((uint32_t *)b_od.p + T, fin.od.p, Tf * 4, cudaMemcpyDeviceToDevice, s));
+                if (parents)
+                    CUDA_TRY(cudaMemcpyAsync((uint32_t *)b_op.p + T, fin.op.p, Tf * 4, cudaMemcpyDeviceToDevice, s));
+                T += Tf;
+            }
+            ffailed.resize(fin.hc.failed_count);
+            if (!ffailed.empty())
+                CUDA_TRY(cudaMemcpy(ffailed.data(), fin.fail.p, ffailed.size() * 4, cudaMemcpyDeviceToHost));
+            hc.next_root = fin.hc.next_root;
+            count = fin.hc.list_n;
+            filler_merged = true;
+            fin.active = false;
+            free_table(fin.old, s);
+        }
+        if (!hc.flags[1] && ffailed.empty()) break;  // every root of this attempt fit
         // collect roots that failed or were never claimed, grow the buffer, go again
         {
             std::vector<uint32_t> failed(hc.failed_count);
             if (hc.failed_count)
                 CUDA_TRY(cudaMemcpyAsync(failed.data(), b_fail.p, size_t(hc.failed_count) * 4,
                                          cudaMemcpyDeviceToHost, s));
+            failed.insert(failed.end(), ffailed.begin(), ffailed.end());
             if (split) {
                 list_h.resize(count);
                 if (count)
                     CUDA_TRY(cudaMemcpyAsync(list_h.data(), b_roots.p, size_t(count) * 4,
+                                             cudaMemcpyDeviceToHost, s));
+            } else if (filler_merged && first) {
+                list_h.resize(count);
+                if (count)
+                    CUDA_TRY(cudaMemcpyAsync(list_h.data(), fin.roots.p, size_t(count) * 4,
                                              cudaMemcpyDeviceToHost, s));
             }
             CUDA_TRY(cudaStreamSynchronize(s));
@@ -893,7 +1055,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
         else
             CUDA_TRY(grow_table(n, lt, lt_records, T, (const uint32_t *)b_ov.p,
                                 (const uint32_t *)b_oh.p, (const uint32_t *)b_od.p, rg.pos_of, min_hub,
-                                s, &launches));
+                                s, &launches, fill[ph & 1].active ? &fill[ph & 1].old : nullptr));
         lt_records = T;
     }
     if (trace) {
@@ -974,6 +1136,16 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     csr = LabelCSR{};
     *out = L;
 done:
+    if (s2) {
+        // the fillers' trees read buffers freed below on s
+        cudaStreamSynchronize(s2);
+        cudaStreamDestroy(s2);
+    }
+    for (Filler &f : fill) {
+        free_table(f.old, s);
+        for (cudaEvent_t e : {f.ev_clear, f.ev_split, f.ev_done})
+            if (e) cudaEventDestroy(e);
+    }
     free_table(lt, s);
     if (csr_parent) cudaFreeAsync(csr_parent, s);
     if (csr.offsets) cudaFreeAsync(csr.offsets, s);

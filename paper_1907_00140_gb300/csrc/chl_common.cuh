@@ -48,6 +48,8 @@ struct TreeLaunch {
     const uint32_t *root_list;
     uint32_t root_begin;
     uint32_t root_count;
+    const uint32_t *count_dev;  // non-null: the root count is read here (written by an earlier kernel)
+    const int *stop;            // non-null: no root is claimed once *stop != 0
     // search parameters
     uint32_t delta;
     int delta_shift;    // log2(delta) when delta is a power of two, else -1
@@ -82,7 +84,9 @@ struct TreeLaunch {
     int key_bytes;      // 4 (distances provably < 2^31 - 1) or 8
     uint32_t *rtag;     // per slot: round id that last listed the vertex in nxt
     uint32_t *lists;    // per slot: round lists l0, l1, far, touched, then nwin bucket lists
-    uint32_t *slot_ctr; // [slot][4] persistent instance counters
+    uint32_t *slot_ctr; // [slot][4] persistent per-slot words: [0] round id, [1] held by a CTA
+    int dyn_slots;      // 1: a CTA takes any free slot of [0, nslots) (launches may overlap), 0: slot = CTA
+    uint32_t nslots;    // slots of the launch (its grid size)
     // label output (structure of arrays)
     uint32_t *out_v;    // caller vertex id of the labelled vertex
     uint32_t *out_h;    // hub pos id
@@ -152,10 +156,11 @@ cudaError_t assemble_table(uint32_t n, uint64_t T, const uint32_t *in_v, const u
                            LabelTable &out, cudaStream_t s, int *launches);
 
 // a table from assemble_table of records [0, T0) grown by records [T0, T):
-// each vertex keeps its old entries first (lt is replaced; freed on success)
+// each vertex keeps its old entries first (lt is replaced; on success the old
+// arrays are freed on s, or handed to *keep_old when that is non-null)
 cudaError_t grow_table(uint32_t n, LabelTable &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
                        const uint32_t *in_h, const uint32_t *in_d, const uint32_t *pos_of,
-                       uint32_t min_hub, cudaStream_t s, int *launches);
+                       uint32_t min_hub, cudaStream_t s, int *launches, LabelTable *keep_old = nullptr);
 void free_table(LabelTable &t, cudaStream_t s);
 
 // parents of label records into the slots of the assembled CSR (parent[T])

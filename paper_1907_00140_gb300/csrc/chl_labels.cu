@@ -374,7 +374,7 @@ done:
 
 cudaError_t grow_table(uint32_t n, LabelTable &lt, uint64_t T0, uint64_t T, const uint32_t *in_v,
                        const uint32_t *in_h, const uint32_t *in_d, const uint32_t *pos_of,
-                       uint32_t min_hub, cudaStream_t s, int *launches) {
+                       uint32_t min_hub, cudaStream_t s, int *launches, LabelTable *keep_old) {
     cudaError_t e = cudaSuccess;
     uint64_t *cnt = nullptr;
     LabelTable out;
@@ -411,8 +411,12 @@ done:
         if (out.e) cudaFreeAsync(out.e, s);
         return e;
     }
-    cudaFreeAsync(lt.offsets, s);
-    cudaFreeAsync(lt.e, s);
+    if (keep_old) {
+        *keep_old = lt;  // still read by trees on another stream: the caller frees it after them
+    } else {
+        cudaFreeAsync(lt.offsets, s);
+        cudaFreeAsync(lt.e, s);
+    }
     lt = out;
     return e;
 }

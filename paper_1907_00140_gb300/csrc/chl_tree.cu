@@ -148,6 +148,7 @@ struct Shared {
     uint32_t lth_val[LTH_SLOTS];
     unsigned long long base;
     uint32_t sub_n[NWIN_MAX];
+    uint32_t slot;         // the tree slot this CTA holds
     // launch statistics of this CTA, reported once at exit (kept here, not in
     // registers, which the arc pass needs)
     unsigned long long n_exp, n_arcs, n_pruned, n_rounds, n_buckets;
@@ -622,7 +623,7 @@ __device__ void lt_answer(const TreeLaunch &p, Shared &S, Frontier<TPB, K> &F, u
     constexpr int NW = TPB / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t t = threadIdx.x;
-    const uint32_t *rootd = S.lt_dense == 1 ? p.lt_root + size_t(blockIdx.x) * p.n
+    const uint32_t *rootd = S.lt_dense == 1 ? p.lt_root + size_t(S.slot) * p.n
                             : S.lt_dense == 2 ? reinterpret_cast<const uint32_t *>(stage)
                                               : nullptr;
     // the batch's staged queries; the staging keys are free during stage A
@@ -975,7 +976,28 @@ __global__ void __launch_bounds__(TPB, TPB >= 64 ? 1024 / TPB : 16) plant_trees_
     __shared__ Shared S;
     __shared__ Frontier<TPB, K> F;
     const uint32_t n = p.n;
-    const size_t so = size_t(blockIdx.x) * n;
+    // The CTA's tree slot: its own index, or (when launches share the slots)
+    // any slot no running CTA holds. A CTA becomes resident only once another
+    // has left its SM, and every CTA gives its slot back before it exits, so
+    // a free slot exists; a CTA that finds none leaves its roots to the others.
+    if (threadIdx.x == 0) {
+        uint32_t got = NONE;
+        if (p.dyn_slots) {
+            for (uint32_t i = 0; i < p.nslots; ++i) {
+                const uint32_t c = (blockIdx.x + i) % p.nslots;
+                if (atomicCAS(&p.slot_ctr[c * 4 + 1], 0u, 1u) == 0u) {
+                    got = c;
+                    break;
+                }
+            }
+        } else {
+            got = blockIdx.x;
+        }
+        S.slot = got;
+    }
+    __syncthreads();
+    if (S.slot == NONE) return;
+    const size_t so = size_t(S.slot) * n;
     Slot<K> sl;
     sl.key = (typename K::T *)p.key + so;
     sl.rtag = p.rtag + so;
@@ -985,7 +1007,7 @@ __global__ void __launch_bounds__(TPB, TPB >= 64 ? 1024 / TPB : 16) plant_trees_
     uint8_t *stage = reinterpret_cast<uint8_t *>(fin_bitmap) + stage_offset(p.fin_words);
     uint32_t parity = 0;  // phase of S.mbar the next staging batch completes
     if (threadIdx.x == 0) {
-        S.rid = p.slot_ctr[blockIdx.x * 4 + 0];
+        S.rid = p.slot_ctr[S.slot * 4 + 0];
         mbar_init(&S.mbar, TPB);
         S.n_exp = S.n_arcs = S.n_pruned = S.n_rounds = S.n_buckets = 0;
         S.n_trees = S.n_trivial = 0;
@@ -994,9 +1016,10 @@ __global__ void __launch_bounds__(TPB, TPB >= 64 ? 1024 / TPB : 16) plant_trees_
     for (;;) {
         if (threadIdx.x == 0) {
             uint32_t r = NONE;
-            if (!p.flags[1] && !p.flags[0]) {
+            if (!p.flags[1] && !p.flags[0] && !(p.stop && *(volatile const int *)p.stop)) {
+                const uint32_t cnt = p.count_dev ? *(volatile const uint32_t *)p.count_dev : p.root_count;
                 const uint32_t i = atomicAdd(p.next_root, 1u);
-                if (i < p.root_count) r = p.root_list ? p.root_list[i] : p.root_begin + i;
+                if (i < cnt) r = p.root_list ? p.root_list[i] : p.root_begin + i;
             }
             S.root = r;
         }
@@ -1266,7 +1289,12 @@ __global__ void __launch_bounds__(TPB, TPB >= 64 ? 1024 / TPB : 16) plant_trees_
         atomicAdd(&p.stats[3], (unsigned long long)S.n_trees);
         atomicAdd(&p.stats[4], S.n_rounds);
         atomicAdd(&p.stats[5], S.n_buckets);
-        p.slot_ctr[blockIdx.x * 4 + 0] = S.rid;
+        p.slot_ctr[S.slot * 4 + 0] = S.rid;
+        if (p.dyn_slots) {
+            // the slot is idle again (every key and root array entry reset)
+            __threadfence();
+            atomicExch(&p.slot_ctr[S.slot * 4 + 1], 0u);
+        }
     }
 }
 
@@ -1364,7 +1392,9 @@ uint32_t dyn_budget_t() {
 
 }  // namespace
 
-cudaError_t launch_plant_trees(const TreeLaunch &p, int tpt, int slots, cudaStream_t s) {
+cudaError_t launch_plant_trees(const TreeLaunch &pl, int tpt, int slots, cudaStream_t s) {
+    TreeLaunch p = pl;
+    p.nslots = uint32_t(slots);
     if (p.nwin < 2 || p.nwin > NWIN_MAX) return cudaErrorInvalidValue;
     // the staging copies read the label table in 16-byte units
     if (p.lt_off && ((reinterpret_cast<uintptr_t>(p.lt_e) & 15) || (p.stage_bytes & 15)))

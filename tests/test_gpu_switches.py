@@ -1,8 +1,10 @@
 """GPU parity across the hybrid's switch points (Sec. 5.2): wherever the
 first-phase switch (labels per arc, switch_ratio), the Psi switch
 (psi_threshold), the small-tree switch (small_tree_expansions) and the
-narrow bucket width after big trees (big_tree_bucket_delta) fire, the
-labels are the canonical ones, bit-exact with the CPU oracle. Only the amount
+narrow bucket width after big trees (big_tree_bucket_delta) fire, and with or
+without the next phase's first trees overlapped with a phase's tail
+(overlap_phases), the labels are the canonical ones, bit-exact with the CPU
+oracle. Only the amount
 of work changes: the label table of earlier phases covers a rank-closed hub
 set whenever it is used (Sec. 5.3), and the small-tree launch runs the same
 search in smaller blocks. Each build's statistics show which switch fired.
@@ -72,6 +74,14 @@ SWEEP = [
     (dict(switch_ratio=1e6, big_tree_bucket_delta=-1), None),
     (dict(switch_ratio=1e6, big_tree_bucket_delta=1), None),
     (dict(switch_ratio=1e6, big_tree_bucket_delta=3, pruned_bucket_delta=4096), None),
+    # the next phase's first trees in a phase's tail (second stream, older
+    # table): off; in every label-pruned phase; with a label buffer so small
+    # that their trees overflow it and are built again by their own phase
+    (dict(switch_ratio=1e6, overlap_phases=-1), None),
+    (dict(switch_ratio=1e6, small_tree_expansions=NEVER_SMALL), lambda s: s["small_tree_phases"] == 0),
+    (dict(switch_ratio=1e6, small_tree_expansions=NEVER_SMALL, label_capacity=1000), None),
+    (dict(switch_ratio=1e6, small_tree_expansions=NEVER_SMALL, threads_per_tree=256, flags=chl.CHL_FLAG_PARENTS),
+     None),
     # both switches with the other block sizes and bucket widths
     (dict(threads_per_tree=256, switch_ratio=1e6, small_tree_expansions=ALWAYS_SMALL,
           pruned_bucket_delta=1), None),
