@@ -255,6 +255,9 @@ typedef struct {
  *                  earlier ones (0: the switch threshold was never passed)
  *   small_tree_phases  label-pruned phases run with the small-tree launch
  *                  (the switch on small_tree_expansions; 0: it never fired)
+ *   overlapped_trees  trees built in an earlier phase's tail on the second
+ *                  stream (overlap_phases; trivial roots included), all of
+ *                  whose labels were kept
  */
 typedef struct {
     uint64_t trees;
@@ -273,6 +276,7 @@ typedef struct {
     uint64_t phases;
     uint64_t label_table_phases;
     uint64_t small_tree_phases;
+    uint64_t overlapped_trees;
 } chl_build_stats;
 
 /*

@@ -133,7 +133,8 @@ class chl_build_stats(C.Structure):
                 ("tree_ms", C.c_double), ("sort_ms", C.c_double), ("launches", C.c_uint64),
                 ("rounds", C.c_uint64), ("buckets", C.c_uint64), ("pruned", C.c_uint64),
                 ("table_ms", C.c_double), ("phases", C.c_uint64),
-                ("label_table_phases", C.c_uint64), ("small_tree_phases", C.c_uint64)]
+                ("label_table_phases", C.c_uint64), ("small_tree_phases", C.c_uint64),
+                ("overlapped_trees", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -556,7 +556,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     bool use_lt = false, hybrid = false, hybrid_off = false;
     bool small = false;  // later label-pruned phases run the small-tree launch
     bool big = false;    // the previous phase's trees were big (BIG_TREE_COVER)
-    uint64_t lt_phases = 0, small_phases = 0;
+    uint64_t lt_phases = 0, small_phases = 0, overlapped = 0;
     uint64_t lt_records = 0;  // output records the label table holds
     const double psi_th = o.psi_threshold > 0.0f ? double(o.psi_threshold) : PSI_TH;
     uint32_t claimed_upto = 0;
@@ -903,6 +903,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
             CUDA_TRY(cudaEventSynchronize(fin.ev_done));
             CUDA_TRY(cudaMemcpy(&fin.hc, fin.ctl.p, sizeof(Control), cudaMemcpyDeviceToHost));
             for (int k = 0; k < 7; ++k) agg[k] += fin.hc.stats[k];
+            overlapped += fin.hc.stats[3] - fin.hc.failed_count;
             if (fin.hc.flags[0] == ERR_DIST_OVERFLOW) {
                 st = set_error(CHL_EOVERFLOW, "a shortest distance reaches UINT32_MAX");
                 goto done;
@@ -1132,6 +1133,7 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     L->stats.phases = phases.size();
     L->stats.label_table_phases = lt_phases;
     L->stats.small_tree_phases = small_phases;
+    L->stats.overlapped_trees = overlapped;
     L->stats.launches = uint64_t(launches);
     csr = LabelCSR{};
     *out = L;
