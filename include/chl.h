@@ -311,15 +311,16 @@ chl_status chl_build(const chl_csr *g, const uint32_t *rank, const chl_build_opt
  * hybrid phases prune later trees far below the sample's sizes, and then the
  * phases' switch points, each by whole builds: the first-phase switch
  * (switch_ratio default or off), the frontier size of the small-tree switch
- * (small_tree_expansions 2048, 8192 or 32768) and the narrow bucket width
- * after big trees (big_tree_bucket_delta default or off).
+ * (small_tree_expansions 2048, 8192 or 32768), the narrow bucket width
+ * after big trees (big_tree_bucket_delta default or off) and, for a build with
+ * label-pruned phases, the Common Label Table's size (common_hubs 16, 8 or 4).
  *   g, rank, stream   as for chl_build
  *   base              fields set (non-zero) are kept fixed; NULL = tune all
  *   best              receives base with threads_per_tree, bucket_delta and
  *                     window_buckets filled in (and, for a whole build,
- *                     switch_ratio, small_tree_expansions and
- *                     big_tree_bucket_delta when base left them 0); pass it
- *                     to chl_build
+ *                     switch_ratio, small_tree_expansions,
+ *                     big_tree_bucket_delta and common_hubs when base left
+ *                     them 0); pass it to chl_build
  *   report            optional: trials run, sample size, best trial time
  * Errors: as chl_build.
  */

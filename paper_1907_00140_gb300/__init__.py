@@ -440,7 +440,7 @@ def tune(g, rank, stream: int | None = None, **fixed):
     base = _build_opts(**fixed)
     best, rep = chl_tune(csr, rkp, base, _current_stream() if stream is None else stream)
     out = {k: getattr(best, k) for k in ("threads_per_tree", "bucket_delta", "window_buckets")}
-    for k in ("switch_ratio", "small_tree_expansions", "big_tree_bucket_delta"):
+    for k in ("switch_ratio", "small_tree_expansions", "big_tree_bucket_delta", "common_hubs"):
         if getattr(best, k):
             out[k] = getattr(best, k)
     out.update(fixed)

@@ -1700,11 +1700,13 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
     // at a time.
     if (!o.root_begin && !o.root_end && !(o.flags & CHL_FLAG_NO_HYBRID)) {
         double best_build = -1.0;
+        bool pruned_phases = false;  // the last whole build ran label-pruned phases
         auto whole = [&](const chl_build_opts &q, double *ms) -> chl_status {
             chl_labels *Lt = nullptr;
             const chl_status r = chl_build(g, rank, &q, stream, &Lt);
             if (r != CHL_OK) return r;
             *ms = Lt->stats.tree_ms;
+            pruned_phases = Lt->stats.label_table_phases > 0;
             chl_labels_free(Lt);
             ++trials;
             return CHL_OK;
@@ -1746,6 +1748,25 @@ extern "C" chl_status chl_tune(const chl_csr *g, const uint32_t *rank, const chl
             double ms = 0;
             if ((st = whole(q, &ms)) != CHL_OK) goto done;
             if (ms < best_build) { best_build = ms; best->big_tree_bucket_delta = -1; }
+        }
+        // The Common Label Table's size (the paper's eta = 16) where the build
+        // prunes with the label table too: every hub left out of the dense
+        // table is still in the label table, so a smaller one costs a shorter
+        // row per expanded vertex and may prune as well
+        if (!o.common_hubs) {
+            chl_build_opts q = *best;
+            double ms = 0;
+            if ((st = whole(q, &ms)) != CHL_OK) goto done;
+            if (ms < best_build) best_build = ms;
+            if (pruned_phases) {
+                int best_eta = 0;
+                for (int e : {8, 4}) {
+                    q.common_hubs = e;
+                    if ((st = whole(q, &ms)) != CHL_OK) goto done;
+                    if (ms < best_build) { best_build = ms; best_eta = e; }
+                }
+                best->common_hubs = best_eta;
+            }
         }
     }
     if (report) {

@@ -82,6 +82,10 @@ SWEEP = [
     (dict(switch_ratio=1e6, small_tree_expansions=NEVER_SMALL, label_capacity=1000), None),
     (dict(switch_ratio=1e6, small_tree_expansions=NEVER_SMALL, threads_per_tree=256, flags=chl.CHL_FLAG_PARENTS),
      None),
+    # smaller Common Label Tables (the tuner's candidates; the label table
+    # holds the hubs left out)
+    (dict(switch_ratio=1e6, common_hubs=8), None),
+    (dict(switch_ratio=1e6, common_hubs=4, small_tree_expansions=NEVER_SMALL), None),
     # both switches with the other block sizes and bucket widths
     (dict(threads_per_tree=256, switch_ratio=1e6, small_tree_expansions=ALWAYS_SMALL,
           pruned_bucket_delta=1), None),
@@ -109,7 +113,7 @@ def test_tuned_switch_points_are_exact(family):
     name, g, rank, ref, G, R = family
     opts, rep = chl.tune(G, R)
     assert rep["trials"] >= 3
-    for k in ("switch_ratio", "small_tree_expansions", "big_tree_bucket_delta"):
+    for k in ("switch_ratio", "small_tree_expansions", "big_tree_bucket_delta", "common_hubs"):
         assert k not in opts or opts[k] != 0
     L = chl.build_labels(G, R, **opts)
     assert_same(ref, *L.to_numpy())
