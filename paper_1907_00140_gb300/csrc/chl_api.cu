@@ -1030,12 +1030,16 @@ extern "C" chl_status chl_build(const chl_csr *g, const uint32_t *rank, const ch
     }
     // The next phase is one more wave of trees after the first (the table's
     // pruning share decides the switch), doubles while the label table is
-    // used, so that it stays fresh, and grows fourfold before.
+    // used, so that it stays fresh, and grows fourfold before; after a phase
+    // that ran the small-tree launch, it grows fourfold again (those trees are
+    // tiny: a phase's fixed cost of table growth and host round trip outweighs
+    // the table's freshness). A phase that did not run it doubles, which the
+    // next phase's overlapped first trees (launched during it) rely on.
     if (hybrid && pe < re) {
         const uint64_t step_min = uint64_t(P.slots) * 2;
         const uint64_t nx = hybrid_off ? re
                             : ph == 0 ? uint64_t(pe) + P.slots
-                                      : std::max<uint64_t>(uint64_t(pe) * (use_lt ? 2 : 4), pe + step_min);
+                                      : std::max<uint64_t>(uint64_t(pe) * (use_lt && !ph_small ? 2 : 4), pe + step_min);
         phases.push_back({pe, uint32_t(std::min<uint64_t>(nx, re))});
     }
     double t_tree = trace ? now_ms() - t_ph : 0;
